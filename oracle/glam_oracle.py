@@ -1,0 +1,443 @@
+"""FP64 CPU oracle of the GD-PG penalized GLAM solver -- TEST INFRASTRUCTURE ONLY.
+
+Only the test suite, `__graft_entry__.smoke()` and the CPU-baseline leg of `bench.py` may
+import this module.  The product path (the CUDA library and its Python binding) never
+calls it, and shares no code with it.
+
+It is plain, slow, obviously-correct float64 numpy, written in the paper's notation
+(Lund, Vincent & Hansen, "Penalized estimation in large-scale generalized linear array
+models"):
+  * arrays are indexed as in the paper, A[i1, i2, ..., id], and flattened by `vec`
+    (App. A, Eq. index: column-major, i1 fastest);
+  * rho, H and G follow App. A and Eqs. (eighteen)/(nineteen) of Sec. 6.1, with c = 1;
+  * the family quantities follow App. B, Eqs. (four), (weights)/(nine) and (tennew);
+  * the inner PG (FISTA) loop follows Sec. 3.2 with h and grad h of Eqs.
+    (twentyfour)/(twentyfive); the step size is Prop. 1 (Eq. nineteennew);
+  * the outer loop is Algorithm 1 (GD-PG) with the Armijo rule of Sec. 5;
+  * lambda_max and the warm-started path follow Sec. 6.4.
+
+Library primitives used as steps: numpy tensordot (the contraction inside rho), np.kron
+(the explicit tensor-product design, Eq. fivenew), np.linalg.eigvalsh (spectral radius).
+
+Readings where the paper is silent or ambiguous (each also listed in the design notes):
+  R1  1/n scaling: F = -(1/n) l + lambda J throughout (the inner problem, Eq. eleven, and the
+      Lipschitz constant, Eq. lip, carry 1/n); n counts every cell, masked ones included.
+  R2  The IRLS weight includes the observation weight: w_i = a_i theta'(eta_i)(g^-1)'(eta_i),
+      z_i = W^-1 u_i + eta_i, and z_i = eta_i where a_i = 0.  The fixed point of the outer
+      loop (the PMLE) does not depend on this choice (Sec. 5, remark after the Corollary).
+  R3  Gaussian loss f = (1/2n) sum a_i (y_i - eta_i)^2, i.e. -(1/n) l plus the constant
+      sum a_i y_i^2 / (2n); Poisson loss f = (1/n) sum a_i (exp(eta_i) - y_i eta_i), i.e.
+      -(1/n) l with the constant sum a_i log(y_i!) dropped.
+  R4  lambda path: lambda_k = lambda_max * ratio^(k/(K-1)) (log spacing).
+  R5  Armijo constants alpha0 = 1, b = 0.5, v = 0.1 (the rule of Sec. 5 leaves them free).
+  R6  Inner stop: ||x(l+1) - x(l)||_inf <= tol_inner * max(1, ||x(l)||_inf); outer stop:
+      KKT residual <= tol (definition in `kkt_residual`).  The paper gives no criterion.
+  R7  Step size delta = 1/L_hat (the package's nu = 1: no inner backtracking).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+GAUSSIAN = 0
+POISSON = 1
+
+
+# --------------------------------------------------------------------------------------
+# App. A: the vec map and rho
+# --------------------------------------------------------------------------------------
+
+def vec(A) -> np.ndarray:
+    """vec of App. A (Eq. index): column-major flattening, i1 fastest."""
+    return np.asarray(A, dtype=np.float64).reshape(-1, order="F")
+
+
+def unvec(v, shape) -> np.ndarray:
+    """Inverse of `vec` for an array of the given paper shape (n1, ..., nd)."""
+    return np.asarray(v, dtype=np.float64).reshape(shape, order="F")
+
+
+def rho(X, A) -> np.ndarray:
+    """The rotated H-transform of App. A.
+
+    X is an r x n1 matrix and A an n1 x n2 x ... x nd array; the result is the
+    n2 x ... x nd x r array with rho(X, A)[i1, ..., id] = sum_j X[id, j] A[j, i1, ..., i(d-1)]:
+    the first mode is contracted with X and the new mode goes last.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    A = np.asarray(A, dtype=np.float64)
+    if X.ndim != 2 or X.shape[1] != A.shape[0]:
+        raise ValueError(f"rho: X {X.shape} does not match the first mode of A {A.shape}")
+    T = np.tensordot(X, A, axes=([1], [0]))   # T[r, i2, ..., id]
+    return np.moveaxis(T, 0, -1)               # rotate: new mode last
+
+
+def H(Xs: Sequence[np.ndarray], Theta) -> np.ndarray:
+    """Eq. (eighteen), c = 1: H(<X_j>, Theta) = rho(X_d, ..., rho(X_2, rho(X_1, Theta))).
+
+    Xs[j] is the n_j x p_j marginal design; Theta is p1 x ... x pd; the result is the
+    n1 x ... x nd array whose vec is the linear predictor X theta (Eq. seventeen)."""
+    A = np.asarray(Theta, dtype=np.float64)
+    for X in Xs:
+        A = rho(X, A)
+    return A
+
+
+def G(Xs: Sequence[np.ndarray], U) -> np.ndarray:
+    """Eq. (nineteen), c = 1: G(<X_j>, U) = rho(X_d^T, ..., rho(X_1^T, U)); vec(G) = X^T vec(U)."""
+    A = np.asarray(U, dtype=np.float64)
+    for X in Xs:
+        A = rho(np.asarray(X).T, A)
+    return A
+
+
+def kron_design(Xs: Sequence[np.ndarray]) -> np.ndarray:
+    """The explicit tensor-product design X = X_d (x) ... (x) X_1 of Eq. (fivenew) (tiny sizes)."""
+    Phi = np.asarray(Xs[0], dtype=np.float64)
+    for X in Xs[1:]:
+        Phi = np.kron(np.asarray(X, dtype=np.float64), Phi)
+    return Phi
+
+
+# --------------------------------------------------------------------------------------
+# App. B: exponential-family quantities (canonical links only: theta(eta) = eta)
+# --------------------------------------------------------------------------------------
+
+def _canonical_derivative(family, eta):
+    """theta'(eta): 1 for the canonical Gaussian-identity and Poisson-log links."""
+    return np.ones_like(eta)
+
+
+def _mean(family, eta):
+    """g^{-1}(eta)."""
+    if family == GAUSSIAN:
+        return eta.copy()
+    if family == POISSON:
+        return np.exp(eta)
+    raise ValueError(family)
+
+
+def _mean_derivative(family, eta):
+    """(g^{-1})'(eta)."""
+    if family == GAUSSIAN:
+        return np.ones_like(eta)
+    if family == POISSON:
+        return np.exp(eta)
+    raise ValueError(family)
+
+
+def _link_derivative(family, mu):
+    """g'(mu)."""
+    if family == GAUSSIAN:
+        return np.ones_like(mu)
+    if family == POISSON:
+        return 1.0 / mu
+    raise ValueError(family)
+
+
+def _b(family, th):
+    """Log-normaliser b(theta) of the density in App. B."""
+    if family == GAUSSIAN:
+        return 0.5 * th * th
+    if family == POISSON:
+        return np.exp(th)
+    raise ValueError(family)
+
+
+def score(family, eta, y, a):
+    """u_i = a_i theta'(eta_i) (y_i - g^{-1}(eta_i)), Eq. (four)."""
+    return a * _canonical_derivative(family, eta) * (y - _mean(family, eta))
+
+
+def irls_weight(family, eta, a):
+    """w_i = a_i theta'(eta_i) (g^{-1})'(eta_i): Eq. (weights)/(nine) times a_i (reading R2)."""
+    return a * _canonical_derivative(family, eta) * _mean_derivative(family, eta)
+
+
+def working_response(family, eta, y, a):
+    """z = W^{-1} u + eta (Eq. ten); with w from `irls_weight` this is the a-free form of
+    Eq. (tennew), z_i = (y_i - mu_i) g'(mu_i) + eta_i; z_i = eta_i where a_i = 0 (R2)."""
+    mu = _mean(family, eta)
+    z = (y - mu) * _link_derivative(family, mu) + eta
+    return np.where(a > 0, z, eta)
+
+
+def loglik(family, eta, y, a):
+    """l(eta) = sum_i a_i (y_i theta(eta_i) - b(theta(eta_i))), Eq. (two) (canonical link)."""
+    th = eta
+    return float(np.sum(a * (y * th - _b(family, th))))
+
+
+def loss(family, eta, y, a) -> float:
+    """f(eta) = -(1/n) l(eta) + c, with c = sum a y^2/(2n) for the Gaussian family (reading R3)."""
+    n = np.asarray(eta).size
+    f = -loglik(family, eta, y, a) / n
+    if family == GAUSSIAN:
+        f += float(np.sum(a * y * y)) / (2.0 * n)
+    return f
+
+
+# --------------------------------------------------------------------------------------
+# Penalty and proximal operator (Sec. 6.3)
+# --------------------------------------------------------------------------------------
+
+def penalty(theta, pen_w) -> float:
+    """J(theta) = sum_m omega_m |theta_m| (weighted l1)."""
+    return float(np.sum(pen_w * np.abs(theta)))
+
+
+def soft_threshold(z, gamma):
+    """prox of gamma*|.|: (|z| - gamma)_+ sign(z) (Sec. 6.3); gamma may be per coordinate."""
+    return np.maximum(np.abs(z) - gamma, 0.0) * np.sign(z)
+
+
+# --------------------------------------------------------------------------------------
+# Step size (Prop. 1) and the exact Lipschitz constant (Eq. lip, tiny sizes only)
+# --------------------------------------------------------------------------------------
+
+def spectral_radius_gram(X) -> float:
+    """varrho(X^T X) for a marginal design X (n_j x p_j)."""
+    X = np.asarray(X, dtype=np.float64)
+    return float(np.max(np.abs(np.linalg.eigvalsh(X.T @ X))))
+
+
+def lipschitz_bound(Xs, w) -> float:
+    """L_hat = max(w)/n * prod_j varrho(X_j^T X_j), Prop. 1 (Eq. nineteennew) with c = 1."""
+    n = np.asarray(w).size
+    return float(np.max(w)) / n * math.prod(spectral_radius_gram(X) for X in Xs)
+
+
+def lipschitz_exact(Xs, w) -> float:
+    """L = ||X^T W X||_2 / n, Eq. (lip), from the explicit design (tiny sizes only)."""
+    Phi = kron_design(Xs)
+    M = Phi.T @ (vec(w)[:, None] * Phi)
+    return float(np.linalg.norm(M, 2)) / Phi.shape[0]
+
+
+# --------------------------------------------------------------------------------------
+# Problem container in paper layout
+# --------------------------------------------------------------------------------------
+
+def paper_array(c_arr) -> np.ndarray:
+    """A C-order (n3, n2, n1) array as the paper's n1 x n2 x n3 array (same memory order)."""
+    return np.asarray(c_arr, dtype=np.float64).transpose(2, 1, 0)
+
+
+def c_array(paper_arr) -> np.ndarray:
+    """Inverse of `paper_array`: a C-contiguous (n3, n2, n1) array."""
+    return np.ascontiguousarray(np.asarray(paper_arr).transpose(2, 1, 0))
+
+
+@dataclass
+class GlamData:
+    """A GLAM fitting problem in paper layout: Xs[j] is n_j x p_j, Y and a are n1 x n2 x n3,
+    pen_w is p1 x p2 x p3."""
+    family: int
+    Xs: List[np.ndarray]
+    Y: np.ndarray
+    a: np.ndarray
+    pen_w: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return int(self.Y.size)
+
+    @property
+    def pshape(self):
+        return tuple(X.shape[1] for X in self.Xs)
+
+    @classmethod
+    def from_c(cls, family, XT, Y, W, pen_w):
+        """Build from the C-order layout of the library: XT[j] is (p_j, n_j), Y/W are
+        (n3, n2, n1), pen_w is (p3, p2, p1)."""
+        return cls(int(family), [np.asarray(x, dtype=np.float64).T for x in XT], paper_array(Y),
+                   paper_array(W), paper_array(pen_w))
+
+
+def objective(data: GlamData, theta, lam) -> float:
+    """F(theta) = f(eta(theta)) + lambda J(theta), Eq. (five) with the 1/n scaling of R1."""
+    eta = H(data.Xs, theta)
+    return loss(data.family, eta, data.Y, data.a) + lam * penalty(theta, data.pen_w)
+
+
+def gradient(data: GlamData, theta) -> np.ndarray:
+    """grad f(theta) = -(1/n) X^T u(eta(theta)) (Eq. three), via G (Eq. nineteen)."""
+    eta = H(data.Xs, theta)
+    u = score(data.family, eta, data.Y, data.a)
+    return -G(data.Xs, u) / data.n
+
+
+def lambda_max(data: GlamData) -> float:
+    """The smallest lambda whose solution is zero (Sec. 6.4): max_m |g_m(0)| / omega_m with
+    g(0) the gradient of f at theta = 0 (the KKT condition of Eq. five at zero)."""
+    g0 = gradient(data, np.zeros(data.pshape))
+    return float(np.max(np.abs(g0) / data.pen_w))
+
+
+def lambda_sequence(lmax, nlambda, ratio) -> np.ndarray:
+    """lambda_k = lambda_max * ratio^(k/(K-1)), k = 0..K-1 (reading R4)."""
+    if nlambda == 1:
+        return np.array([lmax])
+    return lmax * ratio ** (np.arange(nlambda) / (nlambda - 1))
+
+
+def kkt_residual(data: GlamData, theta, lam, lmax, grad=None) -> float:
+    """Scaled lasso KKT residual of Eq. (five): r = max_m r_m / lambda_max with
+    r_m = |g_m + lambda omega_m sign(theta_m)| if theta_m != 0 and
+    r_m = max(0, |g_m| - lambda omega_m) if theta_m = 0, g = grad f(theta)."""
+    g = gradient(data, theta) if grad is None else grad
+    thr = lam * data.pen_w
+    r = np.where(theta != 0, np.abs(g + thr * np.sign(theta)), np.maximum(0.0, np.abs(g) - thr))
+    return float(np.max(r)) / lmax
+
+
+# --------------------------------------------------------------------------------------
+# Inner PG loop (Sec. 3.2) on the quadratic model h of Eq. (twentyfour)
+# --------------------------------------------------------------------------------------
+
+@dataclass
+class InnerResult:
+    x: np.ndarray
+    iters: int
+    history: Optional[list] = None
+
+
+def inner_pg(data: GlamData, V, Z, theta0, delta, lam, tol=1e-12, max_iter=100000,
+             keep_history=False) -> InnerResult:
+    """Accelerated proximal gradient on h(x) + lambda J(x), h(x) = (1/2n)||sqrt(W)(Xx - z)||^2.
+
+    x(0) = x(1) = theta0, omega_l = (l-1)/(l+2), y = x(l) + omega_l (x(l) - x(l-1)),
+    x(l+1) = prox_{delta lambda}(y - delta grad h(y)) with grad h(y) = (1/n) X^T W (X y - z),
+    evaluated as (G(V (.) H(y)) - G(V (.) Z)) / n (Eqs. twentyeight and twentysixnew)."""
+    n = data.n
+    b = G(data.Xs, V * Z)
+    x_prev = np.array(theta0, dtype=np.float64)
+    x = x_prev.copy()
+    hist = [x.copy()] if keep_history else None
+    thr = delta * lam * data.pen_w
+    it = 0
+    for l in range(1, max_iter + 1):
+        it = l
+        omega = (l - 1.0) / (l + 2.0)
+        y = x + omega * (x - x_prev)
+        grad_h = (G(data.Xs, V * H(data.Xs, y)) - b) / n
+        x_new = soft_threshold(y - delta * grad_h, thr)
+        step = float(np.max(np.abs(x_new - x))) if x.size else 0.0
+        scale = max(1.0, float(np.max(np.abs(x))) if x.size else 0.0)
+        x_prev, x = x, x_new
+        if keep_history:
+            hist.append(x.copy())
+        if step <= tol * scale:
+            break
+    return InnerResult(x, it, hist)
+
+
+# --------------------------------------------------------------------------------------
+# Algorithm 1 (GD-PG) with the Armijo rule of Sec. 5
+# --------------------------------------------------------------------------------------
+
+@dataclass
+class FitStats:
+    outer_iters: int = 0
+    inner_iters: int = 0
+    armijo_backtracks: int = 0
+    objective: float = float("nan")
+    kkt: float = float("nan")
+    converged: bool = False
+    objective_trace: list = field(default_factory=list)
+
+
+def gdpg(data: GlamData, lam, theta0, lmax, tol=1e-9, tol_inner=1e-12, max_outer=100,
+         max_inner=100000, alpha0=1.0, b=0.5, v=0.1, max_ls=60, weights="exact"):
+    """Algorithm 1 (GD-PG) for one lambda.  weights='exact' uses the IRLS weights of App. B
+    (times a, R2); weights='one' uses w_i = a_i (any positive weights keep the fixed point,
+    Sec. 5).  Returns (theta, FitStats)."""
+    fam = data.family
+    n = data.n
+    rho_prod = math.prod(spectral_radius_gram(X) for X in data.Xs)
+    theta = np.array(theta0, dtype=np.float64)
+    st = FitStats()
+    eta = H(data.Xs, theta)
+    F = loss(fam, eta, data.Y, data.a) + lam * penalty(theta, data.pen_w)
+    st.objective_trace.append(F)
+    for k in range(max_outer):
+        # Step 2: U, V and Z at theta(k)
+        u = score(fam, eta, data.Y, data.a)
+        if weights == "exact":
+            w = irls_weight(fam, eta, data.a)
+            z = working_response(fam, eta, data.Y, data.a)
+        else:
+            w = data.a.astype(np.float64)
+            z = np.where(w > 0, u / np.where(w > 0, w, 1.0) + eta, eta)
+        # Step 3: delta = 1 / L_hat (Prop. 1)
+        Lhat = float(np.max(w)) / n * rho_prod
+        if Lhat <= 0:
+            break
+        delta = 1.0 / Lhat
+        # Step 4: inner PG loop
+        inner = inner_pg(data, w, z, theta, delta, lam, tol=tol_inner, max_iter=max_inner)
+        st.inner_iters += inner.iters
+        theta_t = inner.x
+        # Step 5: Armijo line search along d = theta~ - theta
+        d = theta_t - theta
+        eta_t = H(data.Xs, theta_t)
+        Delta = -float(np.sum(u * (eta_t - eta))) / n + lam * (penalty(theta_t, data.pen_w)
+                                                               - penalty(theta, data.pen_w))
+        alpha = alpha0
+        accepted = False
+        for j in range(max_ls):
+            th = theta + alpha * d
+            eta_j = H(data.Xs, th)
+            F_j = loss(fam, eta_j, data.Y, data.a) + lam * penalty(th, data.pen_w)
+            if F_j <= F + alpha * v * Delta:
+                accepted = True
+                break
+            alpha *= b
+            st.armijo_backtracks += 1
+        st.outer_iters = k + 1
+        if not accepted:
+            break
+        theta, eta, F = th, eta_j, F_j
+        st.objective_trace.append(F)
+        # Step 6: convergence test
+        r = kkt_residual(data, theta, lam, lmax)
+        st.kkt = r
+        if r <= tol:
+            st.converged = True
+            break
+    st.objective = F
+    if not st.converged:
+        st.kkt = kkt_residual(data, theta, lam, lmax)
+        st.converged = st.kkt <= tol
+    return theta, st
+
+
+def fit_path(data: GlamData, nlambda=10, ratio=1e-3, lambdas=None, theta0=None, **kw):
+    """Warm-started lambda path (Sec. 6.4): lambda_max down to ratio*lambda_max, each fit
+    started from the previous solution.  Returns (lambdas, thetas[K, p1, .., pd], stats)."""
+    lmax = lambda_max(data)
+    lams = lambda_sequence(lmax, nlambda, ratio) if lambdas is None else np.asarray(lambdas, float)
+    theta = np.zeros(data.pshape) if theta0 is None else np.array(theta0, dtype=np.float64)
+    thetas, stats = [], []
+    for lam in lams:
+        theta, st = gdpg(data, lam, theta, lmax, **kw)
+        thetas.append(theta.copy())
+        stats.append(st)
+    return lams, np.array(thetas), stats, lmax
+
+
+# --------------------------------------------------------------------------------------
+# C-order conveniences (same layout as the library's arguments)
+# --------------------------------------------------------------------------------------
+
+def predict_c(XT, theta_c) -> np.ndarray:
+    """eta = H(Theta) for C-order inputs: XT[j] (p_j, n_j), theta (p3, p2, p1) -> (n3, n2, n1)."""
+    return c_array(H([np.asarray(x).T for x in XT], paper_array(theta_c)))
+
+
+def G_c(XT, U_c) -> np.ndarray:
+    """G(U) for C-order inputs: U (n3, n2, n1) -> (p3, p2, p1)."""
+    return c_array(G([np.asarray(x).T for x in XT], paper_array(U_c)))
