@@ -1,0 +1,196 @@
+/*
+ * glam.h -- C ABI of libglam: the GD-PG penalized GLAM solver on one GB300 GPU (sm_103a).
+ *
+ * Method: Lund, Vincent & Hansen, "Penalized estimation in large-scale generalized linear
+ * array models".  The design matrix X = X_3 (x) X_2 (x) X_1 (Sec. 2, Eq. fivenew) is never
+ * formed: the linear predictor is the array transform H (Sec. 6.1, Eq. eighteen, built from
+ * the rotated H-transform rho of App. A) and the gradient uses its transpose G (Eq. nineteen).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Arrays.  A paper array of size n1 x n2 x n3 is stored flattened by the vec map of App. A
+ *   (Eq. index: column-major, i1 fastest), which is a C-order (n3, n2, n1) array.  The
+ *   parameter array Theta (p1 x p2 x p3) is a C-order (p3, p2, p1) array.  A marginal design
+ *   X_j (n_j x p_j) is stored column-major, as R stores it: element (i, k) sits at
+ *   X[j][k * n_j + i] (a C-order (p_j, n_j) array).
+ * Element type.  double for a GLAM_FP64 plan; float (IEEE binary32) for the GLAM_FP32,
+ *   GLAM_TF32 and GLAM_BF16 plans (the precision names the arithmetic of the mode products,
+ *   not the storage).  Scalars marked "double" are always double.
+ * Memory.  Every array argument is a DEVICE pointer owned by the caller, unless marked HOST.
+ *   The library never frees caller memory.  All workspace lives in the opaque plan, allocated
+ *   by glam_plan_create and released by glam_plan_destroy.
+ * Streams.  Work is enqueued on the plan's stream (glam_plan_create / glam_plan_set_stream).
+ *   Calls that return only device results are asynchronous; calls that fill HOST outputs
+ *   (glam_fit_path) synchronize the stream before returning.
+ * Errors.  Every function returns a status (GLAM_OK = 0).  No exception crosses the ABI.
+ *   On failure glam_last_error(plan) returns a message (for glam_plan_create failures, and
+ *   for calls given a NULL plan, use glam_last_error(NULL): the calling thread's last error).
+ * Families.  GLAM_GAUSSIAN_IDENTITY and GLAM_POISSON_LOG (App. B; canonical links).
+ * Objective.  F(theta) = f(theta) + lambda * sum_m w_m |theta_m| with f = -(1/n) l, l the
+ *   weighted log-likelihood of Sec. 2, Eq. (two), n = n1 n2 n3 counting every cell (masked
+ *   ones included).  Constants: Gaussian f = (1/2n) sum a_i (y_i - eta_i)^2; Poisson
+ *   f = (1/n) sum a_i (exp(eta_i) - y_i eta_i) (the sum of a_i log y_i! is dropped).
+ * Observation weights W (the paper's a_i, Sec. 6.4 "Weights") are >= 0; a_i = 0 masks a cell
+ *   (Sec. 4.3).  Penalty weights pen_w (omega_m) must be > 0.
+ */
+#ifndef GLAM_H
+#define GLAM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define GLAM_OK 0
+#define GLAM_EINVAL 1     /* bad argument: NULL pointer, bad dims, bad enum, unsupported combination */
+#define GLAM_ENOMEM 2     /* device or host allocation failed */
+#define GLAM_ECUDA 3      /* a CUDA runtime call failed; the message names it */
+#define GLAM_ENONFINITE 4 /* non-finite input, or a non-finite accepted iterate (Poisson overflow) */
+#define GLAM_ENOCONV 5    /* an iteration cap was reached before the KKT tolerance */
+#define GLAM_ETIMEOUT 6   /* a bounded device-side wait gave up */
+
+/* ---- families (App. B) ---- */
+#define GLAM_GAUSSIAN_IDENTITY 0
+#define GLAM_POISSON_LOG 1
+
+/* ---- arithmetic of the mode products ---- */
+#define GLAM_FP64 0
+#define GLAM_FP32 1
+#define GLAM_TF32 2
+#define GLAM_BF16 3
+
+typedef struct glam_plan glam_plan;
+
+/* Grid and basis sizes.  d = 3, or d = 2 with n[2] = p[2] = 1 (then X[2] may be NULL). */
+typedef struct {
+  int32_t d;
+  int64_t n[3]; /* n1, n2, n3: grid points per dimension */
+  int64_t p[3]; /* p1, p2, p3: basis functions per dimension */
+} glam_dims;
+
+/* The quadratic model h of Sec. 3.2, Eq. (twentyfour), at an anchor Theta_k (Alg. 1, step 2-3).
+ * Caller-owned device buffers, filled by glam_quad_build:
+ *   V    n elements: IRLS weights w_i = a_i theta'(eta_i) (g^-1)'(eta_i) (App. B, Eq. weights,
+ *        times the observation weight a_i);
+ *   VZ   n elements: V (.) Z, Z the working response of Eq. (ten);
+ *   b    p elements: G(V (.) Z) = X^T W z (Sec. 6.1, Eq. twentyeight);
+ *   Lhat 1 double:   the Lipschitz bound max(w)/n * prod_j rho(X_j^T X_j) (Prop. 1). */
+typedef struct {
+  void* V;
+  void* VZ;
+  void* b;
+  double* Lhat;
+} glam_quad;
+
+/* Options of glam_fit_path.  glam_opts_default fills the defaults given below. */
+typedef struct {
+  double tol;              /* KKT residual target per lambda (default 1e-6), see glam_stats.kkt */
+  double lambda_min_ratio; /* auto path: lambda_min = ratio * lambda_max (default 1e-3) */
+  double inner_forcing;    /* inner PG stop: max_m |x+_m - y_m| / delta <= s * lambda_max with
+                              s = max(inner_floor * tol, inner_forcing * r_k), r_k the KKT residual
+                              at the outer iterate (defaults 1e-2 and 0.1) */
+  double inner_floor;
+  double armijo_alpha0;    /* Armijo rule of Sec. 5: alpha = alpha0 * b^j (default 1) */
+  double armijo_b;         /* (default 0.5) */
+  double armijo_v;         /* (default 0.1) */
+  int32_t max_inner;       /* inner FISTA iterations per outer iteration (default 50000) */
+  int32_t max_outer;       /* outer GD iterations per lambda (default 50) */
+  int32_t max_linesearch;  /* Armijo trials per outer iteration (default 30) */
+  int32_t check_every;     /* inner iterations per captured CUDA graph chunk, i.e. between host
+                              reads of the device stop flag (default 32, rounded up to even) */
+  int32_t reserved[6];
+} glam_opts;
+
+/* Per-lambda record written by glam_fit_path (HOST array of nlambda entries). */
+typedef struct {
+  double lambda;
+  double objective;        /* F at the returned Theta, FP64 */
+  double kkt;              /* max_m r_m / lambda_max, FP64; r_m = |g_m + lambda w_m sign theta_m|
+                              if theta_m != 0, else max(0, |g_m| - lambda w_m), g = grad f */
+  double time_ms;
+  int32_t outer_iters;     /* outer GD iterations (inner solves) */
+  int32_t inner_iters;     /* inner PG iterations, total */
+  int32_t fp64_passes;     /* FP64 gradient / KKT passes (outer_iters + 1 when converged) */
+  int32_t armijo_backtracks;
+  int32_t nnz;
+  int32_t status;          /* GLAM_OK or GLAM_ENOCONV / GLAM_ENONFINITE for this lambda */
+} glam_stats;
+
+/* Fill *opts with the defaults listed in glam_opts.  Returns GLAM_EINVAL for NULL. */
+int glam_opts_default(glam_opts* opts);
+
+/* Create a plan for one problem shape.  dims: HOST pointer (copied).  family: GLAM_GAUSSIAN_IDENTITY
+ * or GLAM_POISSON_LOG.  precision: GLAM_FP64 or GLAM_FP32 (GLAM_TF32 / GLAM_BF16 return
+ * GLAM_EINVAL until built).  stream: a cudaStream_t (NULL = legacy default stream) on the
+ * current device.  *out receives the plan.  Allocates the workspace on the current device. */
+int glam_plan_create(const glam_dims* dims, int family, int precision, void* stream, glam_plan** out);
+
+/* Release the plan and its workspace (synchronizes its stream first).  NULL is a no-op. */
+int glam_plan_destroy(glam_plan* plan);
+
+/* Enqueue later calls on another stream of the plan's device. */
+int glam_plan_set_stream(glam_plan* plan, void* stream);
+
+/* Message of the last failure on this plan ("" if none); NULL plan: the calling thread's last
+ * failure.  The string is owned by the library and valid until the next call on the plan. */
+const char* glam_last_error(const glam_plan* plan);
+
+/* eta = H(<X_j>, Theta): the linear predictor X theta of Sec. 2 computed by three chained rho
+ * transforms (Sec. 6.1, Eq. eighteen; App. A).  X: HOST array of 3 device pointers (X[2] may be
+ * NULL when d = 2).  Theta: p elements.  eta: n elements (written). */
+int glam_predict(glam_plan* plan, const void* const X[3], const void* Theta, void* eta);
+
+/* grad = grad f(Theta) = -(1/n) X^T u(eta(Theta)) (Sec. 2, Eq. three), u the score of App. B,
+ * Eq. (four), X^T computed by G (Eq. nineteen).  Y, W: n elements.  grad: p elements (written).
+ * loss_or_null: if not NULL, a DEVICE double receiving f(Theta) (FP64 accumulation). */
+int glam_gradient(glam_plan* plan, const void* const X[3], const void* Theta, const void* Y,
+                  const void* W, void* grad, double* loss_or_null);
+
+/* *out = f(Theta) = -(1/n) l(eta(Theta)) (Sec. 2, Eq. two; constants as stated above), computed
+ * with FP64 accumulation.  out: DEVICE double. */
+int glam_loss(glam_plan* plan, const void* const X[3], const void* Theta, const void* Y,
+              const void* W, double* out);
+
+/* Build the quadratic model at Theta_k (Alg. 1 steps 2-3; Sec. 6.1 step 2 and Eq. twentyeight):
+ * eta = H(Theta_k), then V, V (.) Z, b = G(V (.) Z) and Lhat (Prop. 1).  q: HOST struct of
+ * caller-owned device buffers (see glam_quad). */
+int glam_quad_build(glam_plan* plan, const void* const X[3], const void* Theta_k, const void* Y,
+                    const void* W, const glam_quad* q);
+
+/* One inner PG iteration of Sec. 3.2 on the model q:
+ *   y = x + omega (x - x_prev);  grad h(y) = (G(V (.) H(y)) - b) / n  (Eqs. twentyfive, twentysixnew);
+ *   x_next = prox_{delta lambda}(y - delta grad h(y)), the weighted soft threshold of Sec. 6.3
+ *   with per-coordinate threshold delta * lambda * pen_w[m].
+ * delta <= 0 means delta = 1 / *q->Lhat (read on the device).  x, x_prev, pen_w, x_next: p
+ * elements; x_next must not alias x or x_prev. */
+int glam_prox_step(glam_plan* plan, const void* const X[3], const glam_quad* q, const void* x,
+                   const void* x_prev, double omega, double delta, double lambda, const void* pen_w,
+                   void* x_next);
+
+/* Warm-started lambda path of GD-PG (Alg. 1; lambda_max and warm starts of Sec. 6.4).
+ * X, Y, W: the plan's element type, as for the other calls.
+ * pen_w, Theta0, Theta_path: DOUBLE for every plan (the p-space state of the solver is FP64 in
+ *   every precision: the mode products of a GLAM_FP32 plan run in FP32 on corrections only, and
+ *   each outer iteration recomputes grad f and the KKT residual in FP64, so the returned Theta
+ *   carries FP64 accuracy).
+ * lambda: HOST array of nlambda doubles.  If lambda[0] < 0 the path is automatic,
+ *   lambda_k = lambda_max * ratio^(k/(nlambda-1)) (ratio = opts->lambda_min_ratio), and the used
+ *   values are written back; otherwise the given values are used in order.
+ * opts: HOST, NULL for defaults.  Theta0: p doubles or NULL (start from zero).
+ * Theta_path: nlambda * p doubles (written; row k is the solution at lambda[k]).
+ * stats: HOST array of nlambda records or NULL.  nfit: HOST, number of completed lambdas.
+ * Each lambda stops when its FP64 KKT residual is <= opts->tol.  Returns GLAM_ENOCONV (with
+ * *nfit = the number of lambdas that met the tolerance, and rows up to the failing one written)
+ * when an iteration cap is hit, as the paper's package does; GLAM_ENONFINITE on non-finite
+ * input or a non-finite iterate. */
+int glam_fit_path(glam_plan* plan, const void* const X[3], const void* Y, const void* W,
+                  const void* pen_w, int nlambda, double* lambda, const glam_opts* opts,
+                  const double* Theta0, double* Theta_path, glam_stats* stats, int* nfit);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GLAM_H */

@@ -102,6 +102,24 @@ def kron_design(Xs: Sequence[np.ndarray]) -> np.ndarray:
     return Phi
 
 
+def design_row(Xs, idx) -> np.ndarray:
+    """Row [i1, .., id] of X = X_d (x) ... (x) X_1 (Eq. fivenew) as a p1 x .. x pd array, so that
+    eta[idx] = sum(design_row * Theta) (one entry of Eq. seventeen without the full product)."""
+    r = np.asarray(Xs[0][idx[0]], dtype=np.float64)
+    for j in range(1, len(Xs)):
+        r = np.kron(np.asarray(Xs[j][idx[j]], dtype=np.float64), r)
+    return unvec(r, tuple(X.shape[1] for X in Xs))
+
+
+def design_col(Xs, midx) -> np.ndarray:
+    """Column [j1, .., jd] of X = X_d (x) ... (x) X_1 as an n1 x .. x nd array, so that
+    G(U)[midx] = sum(design_col * U)."""
+    c = np.asarray(Xs[0][:, midx[0]], dtype=np.float64)
+    for j in range(1, len(Xs)):
+        c = np.kron(np.asarray(Xs[j][:, midx[j]], dtype=np.float64), c)
+    return unvec(c, tuple(X.shape[0] for X in Xs))
+
+
 # --------------------------------------------------------------------------------------
 # App. B: exponential-family quantities (canonical links only: theta(eta) = eta)
 # --------------------------------------------------------------------------------------

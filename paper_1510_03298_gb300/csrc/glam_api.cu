@@ -1,0 +1,900 @@
+// C ABI of libglam (include/glam.h): plans, the array transforms H and G, the standalone
+// entry points and the warm-started GD-PG lambda path (Alg. 1, Sec. 3; Sec. 6.1 and 6.4).
+//
+// Mode order (the Kronecker algebra of App. A leaves it free): H contracts mode 3, then mode 1,
+// then mode 2; G runs the reverse.  Mode 2 is the fused mode of the bottleneck kernel.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "glam_internal.cuh"
+
+using namespace glam;
+
+namespace {
+
+thread_local std::string g_thread_err;
+
+template <typename T>
+struct Work {
+  T *Ta = nullptr, *Tb = nullptr, *Sb = nullptr, *Qpart = nullptr;
+  T *eta = nullptr, *eta_bar = nullptr, *V = nullptr, *VZ = nullptr, *U = nullptr;
+  T *x0 = nullptr, *x1 = nullptr, *theta = nullptr, *theta_t = nullptr, *b = nullptr,
+    *grad = nullptr;
+  T* Xc[3] = {nullptr, nullptr, nullptr};  // converted copies of the marginal designs
+  T *Yc = nullptr, *Wc = nullptr, *penc = nullptr;
+  T* one = nullptr;                        // the 1 x 1 design of a d = 2 problem
+  bool ready = false;
+};
+
+}  // namespace
+
+struct glam_plan {
+  int device = 0;
+  cudaStream_t stream = nullptr;   // caller's stream
+  cudaStream_t work = nullptr;     // private stream (graph capture needs a capturable stream)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  glam_dims dims{};
+  int family = 0, precision = 0;
+  int64_t n1 = 1, n2 = 1, n3 = 1, p1 = 1, p2 = 1, p3 = 1, n = 1, p = 1;
+  int ksplit = 1;
+  bool fused[2] = {false, false};  // [float, double]
+  std::string err;
+  Work<float> wf;
+  Work<double> wd;
+  // p-space state of the fit path, always FP64: theta, the two FISTA buffers, grad f(theta_k),
+  // the penalty weights and a scratch vector
+  double *th = nullptr, *x0 = nullptr, *x1 = nullptr, *gk = nullptr, *pen = nullptr, *ptmp = nullptr;
+  InnerCtl* ctl = nullptr;
+  DevScalars* sc = nullptr;
+  RedScratch red{};
+  InnerCtl* h_ctl = nullptr;
+  DevScalars* h_sc = nullptr;
+  double* h_gram = nullptr;
+  double* d_gram = nullptr;        // p_j x p_j Gram scratch (p_j <= 64)
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+int fail(glam_plan* pl, int code, const std::string& msg) {
+  if (pl)
+    pl->err = msg;
+  else
+    g_thread_err = msg;
+  return code;
+}
+
+#define CK(...)                                                                             \
+  do {                                                                                      \
+    cudaError_t e_ = (__VA_ARGS__);                                                         \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail(pl, GLAM_ECUDA, std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define CKS(call)                                 \
+  do {                                            \
+    int s_ = (call);                              \
+    if (s_ != GLAM_OK) return s_;                 \
+  } while (0)
+
+template <typename T>
+int dalloc(glam_plan* pl, T** ptr, size_t count) {
+  if (count == 0) count = 1;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(pl, GLAM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  pl->allocs.push_back(p);
+  *ptr = static_cast<T*>(p);
+  return GLAM_OK;
+}
+
+// ---------------------------------------------------------------- GEMM descriptors (rho)
+GemmDesc mk(int M, int N, int K, int batch, int ksplit, int64_t sAb, int64_t sAm, int64_t sAk,
+            int64_t sBb, int64_t sBk, int64_t sBn, int64_t sCb, int64_t sCm, int64_t sCn,
+            int64_t sCs) {
+  GemmDesc d;
+  d.M = M; d.N = N; d.K = K; d.batch = batch; d.ksplit = ksplit;
+  d.sAb = sAb; d.sAm = sAm; d.sAk = sAk;
+  d.sBb = sBb; d.sBk = sBk; d.sBn = sBn;
+  d.sCb = sCb; d.sCm = sCm; d.sCn = sCn; d.sCsplit = sCs;
+  return d;
+}
+// H stage 1: T_a (n3 x p2p1) = X_3 (n3 x p3) . Theta (p3 x p2p1)
+GemmDesc d_mode3_fwd(const glam_plan* pl) {
+  const int64_t P21 = pl->p2 * pl->p1;
+  return mk((int)pl->n3, (int)P21, (int)pl->p3, 1, 1, 0, 1, pl->n3, 0, P21, 1, 0, P21, 1, 0);
+}
+// H stage 2: T_b (n3 p2 x n1) = T_a (n3 p2 x p1) . X_1^T (p1 x n1)
+GemmDesc d_mode1_fwd(const glam_plan* pl) {
+  return mk((int)(pl->n3 * pl->p2), (int)pl->n1, (int)pl->p1, 1, 1, 0, pl->p1, 1, 0, pl->n1, 1, 0,
+            pl->n1, 1, 0);
+}
+// H stage 3: eta[i3] (n2 x n1) = X_2 (n2 x p2) . T_b[i3] (p2 x n1)
+GemmDesc d_mode2_fwd(const glam_plan* pl) {
+  return mk((int)pl->n2, (int)pl->n1, (int)pl->p2, (int)pl->n3, 1, 0, 1, pl->n2, pl->p2 * pl->n1,
+            pl->n1, 1, pl->n2 * pl->n1, pl->n1, 1, 0);
+}
+// G stage 1: S[i3] (p2 x n1) = X_2^T (p2 x n2) . U[i3] (n2 x n1)
+GemmDesc d_mode2_adj(const glam_plan* pl) {
+  return mk((int)pl->p2, (int)pl->n1, (int)pl->n2, (int)pl->n3, 1, 0, pl->n2, 1, pl->n2 * pl->n1,
+            pl->n1, 1, pl->p2 * pl->n1, pl->n1, 1, 0);
+}
+// G stage 2: S_b (n3 p2 x p1) = S (n3 p2 x n1) . X_1 (n1 x p1)
+GemmDesc d_mode1_adj(const glam_plan* pl) {
+  return mk((int)(pl->n3 * pl->p2), (int)pl->p1, (int)pl->n1, 1, 1, 0, pl->n1, 1, 0, 1, pl->n1, 0,
+            pl->p1, 1, 0);
+}
+// G stage 3: Q (p3 x p2p1) = X_3^T (p3 x n3) . S_b (n3 x p2p1), optionally split over i3
+GemmDesc d_mode3_adj(const glam_plan* pl, int ksplit) {
+  const int64_t P21 = pl->p2 * pl->p1;
+  return mk((int)pl->p3, (int)P21, (int)pl->n3, 1, ksplit, 0, pl->n3, 1, 0, P21, 1, 0, P21, 1,
+            pl->p3 * P21);
+}
+
+template <typename T>
+Work<T>& work_of(glam_plan* pl);
+template <>
+Work<float>& work_of<float>(glam_plan* pl) { return pl->wf; }
+template <>
+Work<double>& work_of<double>(glam_plan* pl) { return pl->wd; }
+
+template <typename T>
+struct Ops {
+  glam_plan* pl;
+  Work<T>& w;
+  cudaStream_t s;
+  const T* X[3];
+
+  Ops(glam_plan* p, cudaStream_t st, const void* const Xin[3])
+      : pl(p), w(work_of<T>(p)), s(st) {
+    for (int j = 0; j < 3; ++j) X[j] = static_cast<const T*>(Xin[j]);
+    if (X[2] == nullptr) X[2] = w.one;
+  }
+
+  // eta = H(<X_j>, Theta)   (Sec. 6.1, Eq. eighteen)
+  int H(const T* theta, T* eta) {
+    CK(launch_gemm<T, T>(d_mode3_fwd(pl), X[2], theta, w.Ta, s));
+    CK(launch_gemm<T, T>(d_mode1_fwd(pl), w.Ta, X[0], w.Tb, s));
+    CK(launch_gemm<T, T>(d_mode2_fwd(pl), X[1], w.Tb, eta, s));
+    return GLAM_OK;
+  }
+  // out = G(<X_j>, U)   (Sec. 6.1, Eq. nineteen)
+  int G(const T* U, T* out) {
+    CK(launch_gemm<T, T>(d_mode2_adj(pl), X[1], U, w.Tb, s));
+    CK(launch_gemm<T, T>(d_mode1_adj(pl), w.Tb, X[0], w.Sb, s));
+    CK(launch_gemm<T, T>(d_mode3_adj(pl, 1), X[2], w.Sb, out, s));
+    return GLAM_OK;
+  }
+  // eta = H(<X_j>, x - sub) for a parameter array held in TB (the correction of a refinement)
+  template <typename TB>
+  int H_diff(const TB* x, const TB* sub, T* eta) {
+    CK(launch_gemm<T, TB>(d_mode3_fwd(pl), X[2], x, w.Ta, s, nullptr, sub, nullptr, 0.0, nullptr));
+    CK(launch_gemm<T, T>(d_mode1_fwd(pl), w.Ta, X[0], w.Tb, s));
+    CK(launch_gemm<T, T>(d_mode2_fwd(pl), X[1], w.Tb, eta, s));
+    return GLAM_OK;
+  }
+  // Qpart = partial sums of G(V (.) H(y - sub)), y = x + omega (x - x_prev)  (Eq. twentysixnew)
+  template <typename TB>
+  int XtWX(const TB* x, const TB* xp, const TB* sub, const T* V, const InnerCtl* ctl,
+           double omega, const int* skip) {
+    CK(launch_gemm<T, TB>(d_mode3_fwd(pl), X[2], x, w.Ta, s, xp, sub, ctl, omega, skip));
+    if (pl->fused[sizeof(T) == 8 ? 1 : 0]) {
+      CK(launch_fused_slab<T>((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2,
+                              X[0], X[1], w.Ta, V, w.Sb, s, skip));
+    } else {
+      T* tmp = w.eta_bar;
+      CK(launch_gemm<T, T>(d_mode1_fwd(pl), w.Ta, X[0], w.Tb, s, nullptr, nullptr, nullptr, 0.0, skip));
+      CK(launch_gemm<T, T>(d_mode2_fwd(pl), X[1], w.Tb, tmp, s, nullptr, nullptr, nullptr, 0.0, skip));
+      CK(launch_vmul<T>(pl->n, V, tmp, skip, s));
+      CK(launch_gemm<T, T>(d_mode2_adj(pl), X[1], tmp, w.Tb, s, nullptr, nullptr, nullptr, 0.0, skip));
+      CK(launch_gemm<T, T>(d_mode1_adj(pl), w.Tb, X[0], w.Sb, s, nullptr, nullptr, nullptr, 0.0, skip));
+    }
+    CK(launch_gemm<T, T>(d_mode3_adj(pl, pl->ksplit), X[2], w.Sb, w.Qpart, s, nullptr, nullptr,
+                         nullptr, 0.0, skip));
+    return GLAM_OK;
+  }
+};
+
+template <typename T>
+int alloc_work(glam_plan* pl, Work<T>& w, bool full) {
+  const int64_t n = pl->n, p = pl->p;
+  const int64_t ta = pl->n3 * pl->p2 * pl->p1;
+  const int64_t tb = pl->n3 * pl->p2 * pl->n1;
+  CKS(dalloc(pl, &w.Ta, ta));
+  CKS(dalloc(pl, &w.Tb, tb));
+  CKS(dalloc(pl, &w.Sb, ta));
+  CKS(dalloc(pl, &w.Qpart, (size_t)pl->ksplit * p));
+  CKS(dalloc(pl, &w.eta, n));
+  CKS(dalloc(pl, &w.U, n));
+  CKS(dalloc(pl, &w.theta, p));
+  CKS(dalloc(pl, &w.grad, p));
+  CKS(dalloc(pl, &w.one, 1));
+  const T one = T(1);
+  CK(cudaMemcpy(w.one, &one, sizeof(T), cudaMemcpyHostToDevice));
+  if (full) {
+    CKS(dalloc(pl, &w.eta_bar, n));
+    CKS(dalloc(pl, &w.V, n));
+    CKS(dalloc(pl, &w.VZ, n));
+    CKS(dalloc(pl, &w.x0, p));
+    CKS(dalloc(pl, &w.x1, p));
+    CKS(dalloc(pl, &w.theta_t, p));
+    CKS(dalloc(pl, &w.b, p));
+  }
+  w.ready = true;
+  return GLAM_OK;
+}
+
+// Largest eigenvalue magnitude of a symmetric matrix by the cyclic Jacobi method.
+double jacobi_spectral_radius(std::vector<double> A, int m) {
+  auto at = [&](int i, int j) -> double& { return A[(size_t)i * m + j]; };
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int i = 0; i < m; ++i) {
+      diag += at(i, i) * at(i, i);
+      for (int j = i + 1; j < m; ++j) off += at(i, j) * at(i, j);
+    }
+    if (off <= 1e-30 * (diag + 1e-300)) break;
+    for (int p = 0; p < m - 1; ++p) {
+      for (int q = p + 1; q < m; ++q) {
+        const double apq = at(p, q);
+        if (apq == 0.0) continue;
+        const double theta = (at(q, q) - at(p, p)) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < m; ++k) {
+          const double akp = at(k, p), akq = at(k, q);
+          at(k, p) = c * akp - s * akq;
+          at(k, q) = s * akp + c * akq;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double apk = at(p, k), aqk = at(q, k);
+          at(p, k) = c * apk - s * aqk;
+          at(q, k) = s * apk + c * aqk;
+        }
+      }
+    }
+  }
+  double r = 0.0;
+  for (int i = 0; i < m; ++i) r = std::fmax(r, std::fabs(at(i, i)));
+  return r;
+}
+
+int validate_X(glam_plan* pl, const void* const X[3]) {
+  if (X == nullptr || X[0] == nullptr || X[1] == nullptr)
+    return fail(pl, GLAM_EINVAL, "X: NULL design pointer");
+  if (pl->dims.d == 3 && X[2] == nullptr) return fail(pl, GLAM_EINVAL, "X[2] is NULL with d = 3");
+  return GLAM_OK;
+}
+
+int check_plan(glam_plan* pl) {
+  if (pl == nullptr) return fail(nullptr, GLAM_EINVAL, "NULL plan");
+  pl->err.clear();
+  return GLAM_OK;
+}
+
+}  // namespace
+
+// ======================================================================== ABI
+// (every entry point is declared extern "C" in glam.h, so these definitions have C linkage)
+
+int glam_opts_default(glam_opts* o) {
+  if (o == nullptr) return fail(nullptr, GLAM_EINVAL, "glam_opts_default: NULL");
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-6;
+  o->lambda_min_ratio = 1e-3;
+  o->inner_forcing = 1e-2;
+  o->inner_floor = 0.1;
+  o->armijo_alpha0 = 1.0;
+  o->armijo_b = 0.5;
+  o->armijo_v = 0.1;
+  o->max_inner = 50000;
+  o->max_outer = 50;
+  o->max_linesearch = 30;
+  o->check_every = 32;
+  return GLAM_OK;
+}
+
+int glam_plan_create(const glam_dims* dims, int family, int precision, void* stream,
+                     glam_plan** out) {
+  glam_plan* pl = nullptr;
+  if (out == nullptr || dims == nullptr) return fail(nullptr, GLAM_EINVAL, "glam_plan_create: NULL argument");
+  *out = nullptr;
+  if (!(dims->d == 2 || dims->d == 3)) return fail(nullptr, GLAM_EINVAL, "dims.d must be 2 or 3");
+  for (int j = 0; j < 3; ++j)
+    if (dims->n[j] < 1 || dims->p[j] < 1)
+      return fail(nullptr, GLAM_EINVAL, "dims: every n_j and p_j must be >= 1");
+  if (dims->d == 2 && (dims->n[2] != 1 || dims->p[2] != 1))
+    return fail(nullptr, GLAM_EINVAL, "dims: d = 2 needs n3 = p3 = 1");
+  if (family != GLAM_GAUSSIAN_IDENTITY && family != GLAM_POISSON_LOG)
+    return fail(nullptr, GLAM_EINVAL, "unknown family");
+  if (precision != GLAM_FP64 && precision != GLAM_FP32)
+    return fail(nullptr, GLAM_EINVAL, "precision: only GLAM_FP64 and GLAM_FP32 are available");
+  const int64_t n = dims->n[0] * dims->n[1] * dims->n[2];
+  const int64_t p = dims->p[0] * dims->p[1] * dims->p[2];
+  if (n > (int64_t)1 << 40 || dims->n[2] * dims->p[1] > 65535LL * 64 || dims->n[2] > 65535)
+    return fail(nullptr, GLAM_EINVAL, "dims too large");
+  pl = new (std::nothrow) glam_plan();
+  if (pl == nullptr) return fail(nullptr, GLAM_ENOMEM, "host allocation failed");
+  pl->dims = *dims;
+  pl->family = family;
+  pl->precision = precision;
+  pl->stream = static_cast<cudaStream_t>(stream);
+  pl->n1 = dims->n[0]; pl->n2 = dims->n[1]; pl->n3 = dims->n[2];
+  pl->p1 = dims->p[0]; pl->p2 = dims->p[1]; pl->p3 = dims->p[2];
+  pl->n = n;
+  pl->p = p;
+  auto bail = [&](int code) {
+    std::string m = pl->err;
+    glam_plan_destroy(pl);
+    g_thread_err = m;
+    return code;
+  };
+  if (cudaGetDevice(&pl->device) != cudaSuccess) { pl->err = "cudaGetDevice failed"; return bail(GLAM_ECUDA); }
+  if (fused_prepare() != cudaSuccess) { pl->err = "cudaFuncSetAttribute failed"; return bail(GLAM_ECUDA); }
+  // split of the last G stage over i3 so that the small p3 x p2p1 output still fills the GPU
+  {
+    const int64_t tiles = ((pl->p3 + 63) / 64) * ((pl->p2 * pl->p1 + 63) / 64);
+    int64_t ks = (2 * num_sms() + tiles - 1) / tiles;
+    if (ks > pl->n3 / 16) ks = pl->n3 / 16;
+    if (ks < 1) ks = 1;
+    if (ks > 64) ks = 64;
+    pl->ksplit = (int)ks;
+  }
+  pl->fused[0] = fused_slab_supported((int)pl->n1, (int)pl->n2, (int)pl->p1, (int)pl->p2, 4) != 0;
+  pl->fused[1] = fused_slab_supported((int)pl->n1, (int)pl->n2, (int)pl->p1, (int)pl->p2, 8) != 0;
+  int st;
+  if (precision == GLAM_FP64) {
+    if ((st = alloc_work<double>(pl, pl->wd, true)) != GLAM_OK) return bail(st);
+  } else {
+    if ((st = alloc_work<float>(pl, pl->wf, true)) != GLAM_OK) return bail(st);
+    if ((st = alloc_work<double>(pl, pl->wd, true)) != GLAM_OK) return bail(st);
+    for (int j = 0; j < 3; ++j)
+      if ((st = dalloc(pl, &pl->wd.Xc[j], (size_t)dims->n[j] * dims->p[j])) != GLAM_OK) return bail(st);
+    if ((st = dalloc(pl, &pl->wd.Yc, n)) != GLAM_OK) return bail(st);
+    if ((st = dalloc(pl, &pl->wd.Wc, n)) != GLAM_OK) return bail(st);
+  }
+  for (double** v : {&pl->th, &pl->x0, &pl->x1, &pl->gk, &pl->pen, &pl->ptmp})
+    if ((st = dalloc(pl, v, p)) != GLAM_OK) return bail(st);
+  if ((st = dalloc(pl, &pl->d_gram, 4096)) != GLAM_OK) return bail(st);
+  if ((st = dalloc(pl, &pl->ctl, 1)) != GLAM_OK) return bail(st);
+  if ((st = dalloc(pl, &pl->sc, 1)) != GLAM_OK) return bail(st);
+  if ((st = dalloc(pl, &pl->red.partial, (size_t)kMaxRedBlocks * kRedSlots)) != GLAM_OK) return bail(st);
+  if ((st = dalloc(pl, &pl->red.counter, 1)) != GLAM_OK) return bail(st);
+  if (cudaMemset(pl->red.counter, 0, sizeof(unsigned int)) != cudaSuccess ||
+      cudaMemset(pl->ctl, 0, sizeof(InnerCtl)) != cudaSuccess ||
+      cudaMemset(pl->sc, 0, sizeof(DevScalars)) != cudaSuccess) {
+    pl->err = "cudaMemset failed";
+    return bail(GLAM_ECUDA);
+  }
+  if (cudaMallocHost(&pl->h_ctl, sizeof(InnerCtl)) != cudaSuccess ||
+      cudaMallocHost(&pl->h_sc, sizeof(DevScalars)) != cudaSuccess ||
+      cudaMallocHost(&pl->h_gram, sizeof(double) * 3 * 4096) != cudaSuccess) {
+    pl->err = "cudaMallocHost failed";
+    return bail(GLAM_ENOMEM);
+  }
+  if (cudaStreamCreateWithFlags(&pl->work, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&pl->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&pl->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    pl->err = "stream/event creation failed";
+    return bail(GLAM_ECUDA);
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) { pl->err = "cudaDeviceSynchronize failed"; return bail(GLAM_ECUDA); }
+  *out = pl;
+  return GLAM_OK;
+}
+
+int glam_plan_destroy(glam_plan* pl) {
+  if (pl == nullptr) return GLAM_OK;
+  if (pl->stream) cudaStreamSynchronize(pl->stream);
+  if (pl->work) cudaStreamSynchronize(pl->work);
+  for (void* p : pl->allocs) cudaFree(p);
+  if (pl->h_ctl) cudaFreeHost(pl->h_ctl);
+  if (pl->h_sc) cudaFreeHost(pl->h_sc);
+  if (pl->h_gram) cudaFreeHost(pl->h_gram);
+  if (pl->ev_in) cudaEventDestroy(pl->ev_in);
+  if (pl->ev_out) cudaEventDestroy(pl->ev_out);
+  if (pl->work) cudaStreamDestroy(pl->work);
+  delete pl;
+  return GLAM_OK;
+}
+
+int glam_plan_set_stream(glam_plan* pl, void* stream) {
+  CKS(check_plan(pl));
+  pl->stream = static_cast<cudaStream_t>(stream);
+  return GLAM_OK;
+}
+
+const char* glam_last_error(const glam_plan* pl) {
+  return pl ? pl->err.c_str() : g_thread_err.c_str();
+}
+
+int glam_predict(glam_plan* pl, const void* const X[3], const void* Theta, void* eta) {
+  CKS(check_plan(pl));
+  CKS(validate_X(pl, X));
+  if (Theta == nullptr || eta == nullptr) return fail(pl, GLAM_EINVAL, "glam_predict: NULL array");
+  if (pl->precision == GLAM_FP64) {
+    Ops<double> op(pl, pl->stream, X);
+    return op.H(static_cast<const double*>(Theta), static_cast<double*>(eta));
+  }
+  Ops<float> op(pl, pl->stream, X);
+  return op.H(static_cast<const float*>(Theta), static_cast<float*>(eta));
+}
+
+namespace {
+template <typename T>
+int gradient_impl(glam_plan* pl, const void* const X[3], const T* Theta, const T* Y, const T* W,
+                  T* grad, double* loss) {
+  Ops<T> op(pl, pl->stream, X);
+  CKS(op.H(Theta, op.w.eta));
+  CK(launch_family<T, T>(pl->family, pl->n, op.w.eta, Y, W, nullptr, nullptr, op.w.U, 1.0, pl->sc,
+                         pl->red, pl->stream));
+  CKS(op.G(op.w.U, op.w.grad));
+  CK(launch_scale<T>(pl->p, op.w.grad, grad, -1.0 / (double)pl->n, pl->stream));
+  if (loss != nullptr)
+    CK(cudaMemcpyAsync(loss, &pl->sc->loss, sizeof(double), cudaMemcpyDeviceToDevice, pl->stream));
+  return GLAM_OK;
+}
+}  // namespace
+
+int glam_gradient(glam_plan* pl, const void* const X[3], const void* Theta, const void* Y,
+                  const void* W, void* grad, double* loss_or_null) {
+  CKS(check_plan(pl));
+  CKS(validate_X(pl, X));
+  if (!Theta || !Y || !W || !grad) return fail(pl, GLAM_EINVAL, "glam_gradient: NULL array");
+  if (pl->precision == GLAM_FP64)
+    return gradient_impl<double>(pl, X, (const double*)Theta, (const double*)Y, (const double*)W,
+                                 (double*)grad, loss_or_null);
+  return gradient_impl<float>(pl, X, (const float*)Theta, (const float*)Y, (const float*)W,
+                              (float*)grad, loss_or_null);
+}
+
+namespace {
+template <typename T>
+int loss_impl(glam_plan* pl, const void* const X[3], const T* Theta, const T* Y, const T* W,
+              double* out) {
+  Ops<T> op(pl, pl->stream, X);
+  CKS(op.H(Theta, op.w.eta));
+  CK(launch_loss_only<T>(pl->family, pl->n, op.w.eta, Y, W, out, pl->red, pl->stream));
+  return GLAM_OK;
+}
+}  // namespace
+
+int glam_loss(glam_plan* pl, const void* const X[3], const void* Theta, const void* Y,
+              const void* W, double* out) {
+  CKS(check_plan(pl));
+  CKS(validate_X(pl, X));
+  if (!Theta || !Y || !W || !out) return fail(pl, GLAM_EINVAL, "glam_loss: NULL array");
+  if (pl->precision == GLAM_FP64)
+    return loss_impl<double>(pl, X, (const double*)Theta, (const double*)Y, (const double*)W, out);
+  return loss_impl<float>(pl, X, (const float*)Theta, (const float*)Y, (const float*)W, out);
+}
+
+namespace {
+
+
+template <typename T>
+int quad_impl(glam_plan* pl, const void* const X[3], const T* Theta, const T* Y, const T* W,
+              const glam_quad* q, double rho_prod) {
+  Ops<T> op(pl, pl->stream, X);
+  CKS(op.H(Theta, op.w.eta));
+  CK(launch_family<T, T>(pl->family, pl->n, op.w.eta, Y, W, (T*)q->V, (T*)q->VZ, nullptr, rho_prod,
+                         pl->sc, pl->red, pl->stream));
+  CKS(op.G((const T*)q->VZ, (T*)q->b));
+  CK(cudaMemcpyAsync(q->Lhat, &pl->sc->Lhat, sizeof(double), cudaMemcpyDeviceToDevice, pl->stream));
+  return GLAM_OK;
+}
+
+// prod_j varrho(X_j^T X_j) (Prop. 1): FP64 Gram matrices on the device, eigenvalues on the host.
+template <typename T>
+int rho_product_from(glam_plan* pl, const T* const X[3], cudaStream_t s, double& out) {
+  double prod = 1.0;
+  const int d = pl->dims.d;
+  for (int j = 0; j < d; ++j) {
+    const int nj = (int)pl->dims.n[j], pj = (int)pl->dims.p[j];
+    if ((int64_t)pj * pj > 4096) return fail(pl, GLAM_EINVAL, "p_j > 64 is not supported by the step-size setup");
+    const double* X64;
+    if (sizeof(T) == 8) {
+      X64 = reinterpret_cast<const double*>(X[j]);
+    } else {
+      CK(launch_convert<float, double>((int64_t)nj * pj, reinterpret_cast<const float*>(X[j]),
+                                       pl->wd.Xc[j], s));
+      X64 = pl->wd.Xc[j];
+    }
+    CK(launch_gram(nj, pj, X64, pl->d_gram, s));
+    CK(cudaMemcpyAsync(pl->h_gram, pl->d_gram, sizeof(double) * pj * pj, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<double> A(pl->h_gram, pl->h_gram + (size_t)pj * pj);
+    prod *= jacobi_spectral_radius(A, pj);
+  }
+  out = prod;
+  return GLAM_OK;
+}
+
+}  // namespace
+
+int glam_quad_build(glam_plan* pl, const void* const X[3], const void* Theta_k, const void* Y,
+                    const void* W, const glam_quad* q) {
+  CKS(check_plan(pl));
+  CKS(validate_X(pl, X));
+  if (!Theta_k || !Y || !W || !q || !q->V || !q->VZ || !q->b || !q->Lhat)
+    return fail(pl, GLAM_EINVAL, "glam_quad_build: NULL argument");
+  double rp = 1.0;
+  if (pl->precision == GLAM_FP64) {
+    const double* Xd[3] = {(const double*)X[0], (const double*)X[1], (const double*)X[2]};
+    if (Xd[2] == nullptr) Xd[2] = pl->wd.one;
+    CKS(rho_product_from<double>(pl, Xd, pl->stream, rp));
+    return quad_impl<double>(pl, X, (const double*)Theta_k, (const double*)Y, (const double*)W, q, rp);
+  }
+  const float* Xf[3] = {(const float*)X[0], (const float*)X[1], (const float*)X[2]};
+  if (Xf[2] == nullptr) Xf[2] = pl->wf.one;
+  CKS(rho_product_from<float>(pl, Xf, pl->stream, rp));
+  return quad_impl<float>(pl, X, (const float*)Theta_k, (const float*)Y, (const float*)W, q, rp);
+}
+
+namespace {
+template <typename T>
+int prox_impl(glam_plan* pl, const void* const X[3], const glam_quad* q, const T* x, const T* xp,
+              double omega, double delta, double lambda, const T* pen_w, T* x_next) {
+  Ops<T> op(pl, pl->stream, X);
+  CKS(op.template XtWX<T>(x, xp, nullptr, (const T*)q->V, nullptr, omega, nullptr));
+  CK(launch_prox<T, T>(pl->p, pl->ksplit, op.w.Qpart, (const T*)q->b, -1.0 / (double)pl->n, x, xp,
+                       pen_w, x_next, 1.0 / (double)pl->n, nullptr, omega, delta, lambda, q->Lhat,
+                       pl->stream));
+  return GLAM_OK;
+}
+}  // namespace
+
+int glam_prox_step(glam_plan* pl, const void* const X[3], const glam_quad* q, const void* x,
+                   const void* x_prev, double omega, double delta, double lambda, const void* pen_w,
+                   void* x_next) {
+  CKS(check_plan(pl));
+  CKS(validate_X(pl, X));
+  if (!q || !q->V || !q->b || !q->Lhat || !x || !x_prev || !pen_w || !x_next)
+    return fail(pl, GLAM_EINVAL, "glam_prox_step: NULL argument");
+  if (x_next == x || x_next == x_prev) return fail(pl, GLAM_EINVAL, "glam_prox_step: x_next aliases an input");
+  if (pl->precision == GLAM_FP64)
+    return prox_impl<double>(pl, X, q, (const double*)x, (const double*)x_prev, omega, delta,
+                             lambda, (const double*)pen_w, (double*)x_next);
+  return prox_impl<float>(pl, X, q, (const float*)x, (const float*)x_prev, omega, delta, lambda,
+                          (const float*)pen_w, (float*)x_next);
+}
+
+
+// ======================================================================== fit path
+//
+// Mixed-precision refinement form of Alg. 1.  Per outer iteration k:
+//   FP64 pass:  eta = H(theta_k), u, w (App. B), g_k = grad f(theta_k) = -(1/n) G(u), the KKT
+//               residual (the convergence test of step 6) and F(theta_k), all in FP64;
+//               V = w is written in the plan's working precision;
+//   inner loop: FISTA (Sec. 3.2) on the quadratic model h with
+//               grad h(y) = g_k + (1/n) X^T W X (y - theta_k)        (= Eq. twentyfive)
+//               p-space vectors in FP64, mode products in the working precision acting on the
+//               correction y - theta_k only;
+//   line search: Armijo rule (Sec. 5) on d = theta~ - theta_k with eta(theta_k + alpha d) =
+//               eta + alpha H(d) (linearity of H), all trial steps evaluated in one pass.
+// The mode products only ever see corrections, so their rounding error shrinks with the
+// correction and the iteration converges to FP64 accuracy in theta and in the KKT residual.
+namespace {
+
+__global__ void ctl_init_kernel(InnerCtl* ctl, const DevScalars* sc, double lambda, double stop_rel,
+                                int max_iter) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double delta = 1.0 / sc->Lhat;  // step 3 of Alg. 1: delta = 1 / L_hat (nu = 1)
+  ctl->l = 1;
+  ctl->done = 0;
+  ctl->max_iter = max_iter;
+  ctl->iters_run = 0;
+  ctl->counter = 0u;
+  ctl->stop_reason = 0;
+  ctl->crit_bits = 0ull;
+  ctl->delta = delta;
+  ctl->lambda = lambda;
+  ctl->stop_abs = stop_rel * sc->lmax * delta;
+  ctl->crit = 0.0;
+}
+
+__global__ void objective_kernel(DevScalars* sc, double lambda) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) sc->F = sc->loss + lambda * sc->pen;
+}
+
+template <typename T>
+struct Fit {
+  glam_plan* pl = nullptr;
+  glam_opts o{};
+  cudaStream_t s = nullptr;
+  double rho_prod = 1.0;
+  double lmax = 0.0;
+  const void* Xw[3] = {nullptr, nullptr, nullptr};   // designs in the working precision
+  const void* X64[3] = {nullptr, nullptr, nullptr};  // designs in FP64
+  const double* Y64 = nullptr;
+  const double* W64 = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  ~Fit() {
+    if (graph) cudaGraphExecDestroy(graph);
+  }
+};
+
+// The FP64 pass at theta (see above).  Fills r (scaled KKT residual), F, nnz.
+template <typename T>
+int fp64_pass(Fit<T>& f, double lambda, double& r, double& F, int& nnz, bool& nonfinite) {
+  glam_plan* pl = f.pl;
+  Ops<double> op(pl, f.s, f.X64);
+  Work<T>& w = work_of<T>(pl);
+  CKS(op.H(pl->th, pl->wd.eta));
+  CK(launch_family<double, T>(pl->family, pl->n, pl->wd.eta, f.Y64, f.W64, w.V, nullptr, pl->wd.U,
+                              f.rho_prod, pl->sc, pl->red, f.s));
+  CKS(op.G(pl->wd.U, pl->gk));
+  CK(launch_scale<double>(pl->p, pl->gk, pl->gk, -1.0 / (double)pl->n, f.s));
+  CK(launch_kkt<double>(pl->p, pl->gk, pl->th, pl->pen, lambda, pl->sc, pl->red, f.s));
+  objective_kernel<<<1, 32, 0, f.s>>>(pl->sc, lambda);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(pl->h_sc, pl->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, f.s));
+  CK(cudaStreamSynchronize(f.s));
+  r = pl->h_sc->kkt_max / f.lmax;
+  F = pl->h_sc->F;
+  nnz = pl->h_sc->nnz;
+  nonfinite = pl->h_sc->nonfinite != 0 || !std::isfinite(F) || !std::isfinite(r);
+  return GLAM_OK;
+}
+
+template <typename T>
+int capture_chunk(Fit<T>& f) {
+  glam_plan* pl = f.pl;
+  Ops<T> op(pl, f.s, f.Xw);
+  const int C = f.o.check_every;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(f.s, cudaStreamCaptureModeThreadLocal));
+  int st = GLAM_OK;
+  for (int it = 0; it < C && st == GLAM_OK; ++it) {
+    double* x = (it % 2 == 0) ? pl->x0 : pl->x1;
+    double* xp = (it % 2 == 0) ? pl->x1 : pl->x0;
+    st = op.template XtWX<double>(x, xp, pl->th, op.w.V, pl->ctl, 0.0, &pl->ctl->done);
+    if (st == GLAM_OK) {
+      cudaError_t e = launch_prox<T, double>(pl->p, pl->ksplit, op.w.Qpart, pl->gk, 1.0, x, xp,
+                                             pl->pen, xp, 1.0 / (double)pl->n, pl->ctl, 0.0, 0.0,
+                                             0.0, nullptr, f.s);
+      if (e != cudaSuccess) st = fail(pl, GLAM_ECUDA, std::string("prox launch: ") + cudaGetErrorString(e));
+    }
+  }
+  cudaError_t e = cudaStreamEndCapture(f.s, &g);
+  if (st != GLAM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(pl, GLAM_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&f.graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(pl, GLAM_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  return GLAM_OK;
+}
+
+// Inner PG loop of Sec. 3.2 from x(0) = x(1) = theta_k; *xout receives the last iterate.
+template <typename T>
+int run_inner(Fit<T>& f, double lambda, double stop_rel, int max_iter, double** xout, int& iters,
+              int& reason) {
+  glam_plan* pl = f.pl;
+  CK(cudaMemcpyAsync(pl->x0, pl->th, sizeof(double) * pl->p, cudaMemcpyDeviceToDevice, f.s));
+  CK(cudaMemcpyAsync(pl->x1, pl->th, sizeof(double) * pl->p, cudaMemcpyDeviceToDevice, f.s));
+  ctl_init_kernel<<<1, 32, 0, f.s>>>(pl->ctl, pl->sc, lambda, stop_rel, max_iter);
+  CK(cudaGetLastError());
+  if (f.graph == nullptr) CKS(capture_chunk<T>(f));
+  const int C = f.o.check_every;
+  const int max_chunks = max_iter / C + 2;
+  bool done = false;
+  for (int c = 0; c < max_chunks && !done; ++c) {
+    CK(cudaGraphLaunch(f.graph, f.s));
+    CK(cudaMemcpyAsync(pl->h_ctl, pl->ctl, sizeof(InnerCtl), cudaMemcpyDeviceToHost, f.s));
+    CK(cudaStreamSynchronize(f.s));
+    done = pl->h_ctl->done != 0;
+  }
+  if (!done) return fail(pl, GLAM_ETIMEOUT, "inner loop did not stop within its iteration cap");
+  iters = pl->h_ctl->iters_run;
+  reason = pl->h_ctl->stop_reason;
+  *xout = (iters % 2 == 1) ? pl->x1 : pl->x0;
+  return GLAM_OK;
+}
+
+struct LamOut {
+  int outer = 0, inner = 0, passes = 0, backtracks = 0, nnz = 0;
+  double kkt = 1e300, F = 0.0;
+  bool converged = false, nonfinite = false;
+};
+
+template <typename T>
+int solve_lambda(Fit<T>& f, double lambda, LamOut& lo) {
+  glam_plan* pl = f.pl;
+  Ops<T> op(pl, f.s, f.Xw);
+  Work<T>& w = op.w;
+  for (int k = 0;; ++k) {
+    double r = 0.0, F = 0.0;
+    int nnz = 0;
+    bool nonfinite = false;
+    CKS(fp64_pass<T>(f, lambda, r, F, nnz, nonfinite));
+    lo.passes += 1;
+    lo.kkt = r;
+    lo.F = F;
+    lo.nnz = nnz;
+    if (nonfinite) {
+      lo.nonfinite = true;
+      return GLAM_OK;
+    }
+    if (r <= f.o.tol) {
+      lo.converged = true;
+      return GLAM_OK;
+    }
+    if (k >= f.o.max_outer) return GLAM_OK;
+    // inner PG loop, solved to a fraction of the current residual (floor: inner_floor * tol)
+    double stop_rel = f.o.inner_forcing * r;
+    if (stop_rel < f.o.inner_floor * f.o.tol) stop_rel = f.o.inner_floor * f.o.tol;
+    double* xt = nullptr;
+    int iters = 0, reason = 0;
+    CKS(run_inner<T>(f, lambda, stop_rel, f.o.max_inner, &xt, iters, reason));
+    lo.inner += iters;
+    lo.outer += 1;
+    // Armijo rule along d = theta~ - theta_k
+    CKS(op.template H_diff<double>(xt, pl->th, w.eta_bar));
+    int accepted = -1;
+    for (int j0 = 0; j0 < f.o.max_linesearch && accepted < 0; j0 += kTrials) {
+      CK(launch_armijo_stream<double, T>(pl->family, pl->n, pl->wd.eta, w.eta_bar, f.Y64, f.W64,
+                                         f.o.armijo_alpha0, f.o.armijo_b, j0, pl->sc, pl->red, f.s));
+      CK(launch_armijo_penalty<double>(pl->p, pl->th, xt, pl->pen, f.o.armijo_alpha0, f.o.armijo_b,
+                                       j0, pl->sc, pl->red, f.s));
+      CK(launch_armijo_select(lambda, f.o.armijo_v, f.o.armijo_alpha0, f.o.armijo_b, j0, pl->sc, f.s));
+      CK(cudaMemcpyAsync(pl->h_sc, pl->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, f.s));
+      CK(cudaStreamSynchronize(f.s));
+      accepted = pl->h_sc->accepted;
+    }
+    if (accepted < 0) return GLAM_OK;  // no descent left: report the current residual
+    lo.backtracks += accepted;
+    CK(launch_armijo_update<double>(pl->p, pl->th, xt, pl->sc, f.s));
+  }
+}
+
+template <typename T>
+int fit_impl(glam_plan* pl, const void* const X[3], const T* Y, const T* W, const double* pen,
+             int nlambda, double* lambda, const glam_opts& o, const double* Theta0, double* path,
+             glam_stats* stats, int* nfit) {
+  Fit<T> f;
+  f.pl = pl;
+  f.o = o;
+  f.s = pl->work;
+  CK(cudaEventRecord(pl->ev_in, pl->stream));
+  CK(cudaStreamWaitEvent(f.s, pl->ev_in, 0));
+  for (int j = 0; j < 3; ++j) f.Xw[j] = X[j];
+  if (sizeof(T) == 8) {
+    for (int j = 0; j < 3; ++j) f.X64[j] = X[j];
+    f.Y64 = (const double*)Y;
+    f.W64 = (const double*)W;
+  } else {
+    for (int j = 0; j < 3; ++j) {
+      if (X[j] == nullptr) continue;
+      CK(launch_convert<float, double>(pl->dims.n[j] * pl->dims.p[j], (const float*)X[j], pl->wd.Xc[j], f.s));
+      f.X64[j] = pl->wd.Xc[j];
+    }
+    CK(launch_convert<float, double>(pl->n, (const float*)Y, pl->wd.Yc, f.s));
+    CK(launch_convert<float, double>(pl->n, (const float*)W, pl->wd.Wc, f.s));
+    f.Y64 = pl->wd.Yc;
+    f.W64 = pl->wd.Wc;
+  }
+  CK(cudaMemcpyAsync(pl->pen, pen, sizeof(double) * pl->p, cudaMemcpyDeviceToDevice, f.s));
+  // input checks
+  CK(cudaMemsetAsync(&pl->sc->nonfinite, 0, sizeof(int), f.s));
+  CK(launch_check_finite<double>(pl->n, f.Y64, pl->sc, f.s));
+  CK(launch_check_finite<double>(pl->n, f.W64, pl->sc, f.s));
+  CK(launch_check_finite<double>(pl->p, pl->pen, pl->sc, f.s));
+  if (Theta0) CK(launch_check_finite<double>(pl->p, Theta0, pl->sc, f.s));
+  CK(cudaMemcpyAsync(pl->h_sc, pl->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, f.s));
+  CK(cudaStreamSynchronize(f.s));
+  if (pl->h_sc->nonfinite) return fail(pl, GLAM_ENONFINITE, "non-finite value in Y, W, pen_w or Theta0");
+  // Prop. 1: prod_j varrho(X_j^T X_j)
+  {
+    const double* Xd[3] = {(const double*)f.X64[0], (const double*)f.X64[1], (const double*)f.X64[2]};
+    if (Xd[2] == nullptr) Xd[2] = pl->wd.one;
+    CKS(rho_product_from<double>(pl, Xd, f.s, f.rho_prod));
+  }
+  // lambda_max (Sec. 6.4): g(0) = -(1/n) G(U(eta = 0)), in FP64
+  {
+    Ops<double> op(pl, f.s, f.X64);
+    CK(cudaMemsetAsync(pl->wd.eta, 0, sizeof(double) * pl->n, f.s));
+    CK(launch_family<double, double>(pl->family, pl->n, pl->wd.eta, f.Y64, f.W64, nullptr, nullptr,
+                                     pl->wd.U, 1.0, pl->sc, pl->red, f.s));
+    CKS(op.G(pl->wd.U, pl->ptmp));
+    CK(launch_scale<double>(pl->p, pl->ptmp, pl->ptmp, -1.0 / (double)pl->n, f.s));
+    CK(launch_lambda_max<double>(pl->p, pl->ptmp, pl->pen, pl->sc, pl->red, f.s));
+    CK(cudaMemcpyAsync(pl->h_sc, pl->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, f.s));
+    CK(cudaStreamSynchronize(f.s));
+    f.lmax = pl->h_sc->lmax;
+  }
+  if (!(f.lmax > 0.0)) return fail(pl, GLAM_EINVAL, "lambda_max is zero: the zero fit is exact");
+  CK(cudaMemcpyAsync(&pl->sc->lmax, &f.lmax, sizeof(double), cudaMemcpyHostToDevice, f.s));
+  std::vector<double> lams(nlambda);
+  if (lambda[0] < 0) {
+    for (int k = 0; k < nlambda; ++k)
+      lams[k] = nlambda == 1 ? f.lmax : f.lmax * std::pow(o.lambda_min_ratio, (double)k / (nlambda - 1));
+    for (int k = 0; k < nlambda; ++k) lambda[k] = lams[k];
+  } else {
+    for (int k = 0; k < nlambda; ++k) lams[k] = lambda[k];
+  }
+  if (Theta0)
+    CK(cudaMemcpyAsync(pl->th, Theta0, sizeof(double) * pl->p, cudaMemcpyDeviceToDevice, f.s));
+  else
+    CK(cudaMemsetAsync(pl->th, 0, sizeof(double) * pl->p, f.s));
+  int status = GLAM_OK;
+  *nfit = 0;
+  for (int k = 0; k < nlambda; ++k) {
+    const auto t0 = std::chrono::steady_clock::now();
+    LamOut lo;
+    CK(cudaMemsetAsync(&pl->sc->nonfinite, 0, sizeof(int), f.s));
+    CKS(solve_lambda<T>(f, lams[k], lo));
+    CK(cudaMemcpyAsync(path + (size_t)k * pl->p, pl->th, sizeof(double) * pl->p, cudaMemcpyDeviceToDevice, f.s));
+    CK(cudaStreamSynchronize(f.s));
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    const int lam_status = lo.converged ? GLAM_OK : (lo.nonfinite ? GLAM_ENONFINITE : GLAM_ENOCONV);
+    if (stats) {
+      glam_stats& s = stats[k];
+      s.lambda = lams[k];
+      s.objective = lo.F;
+      s.kkt = lo.kkt;
+      s.time_ms = ms;
+      s.outer_iters = lo.outer;
+      s.inner_iters = lo.inner;
+      s.fp64_passes = lo.passes;
+      s.armijo_backtracks = lo.backtracks;
+      s.nnz = lo.nnz;
+      s.status = lam_status;
+    }
+    if (lam_status != GLAM_OK) {
+      status = lam_status;
+      char buf[160];
+      std::snprintf(buf, sizeof(buf), "lambda %d (%.6g): %s, KKT %.3g", k, lams[k],
+                    lo.nonfinite ? "non-finite iterate" : "no convergence", lo.kkt);
+      fail(pl, status, buf);
+      break;
+    }
+    *nfit = k + 1;
+  }
+  CK(cudaEventRecord(pl->ev_out, f.s));
+  CK(cudaStreamWaitEvent(pl->stream, pl->ev_out, 0));
+  return status;
+}
+
+}  // namespace
+
+int glam_fit_path(glam_plan* pl, const void* const X[3], const void* Y, const void* W,
+                  const void* pen_w, int nlambda, double* lambda, const glam_opts* opts,
+                  const double* Theta0, double* Theta_path, glam_stats* stats, int* nfit) {
+  CKS(check_plan(pl));
+  CKS(validate_X(pl, X));
+  if (!Y || !W || !pen_w || !lambda || !Theta_path || !nfit)
+    return fail(pl, GLAM_EINVAL, "glam_fit_path: NULL argument");
+  if (nlambda < 1) return fail(pl, GLAM_EINVAL, "glam_fit_path: nlambda must be >= 1");
+  glam_opts o;
+  if (opts)
+    o = *opts;
+  else
+    glam_opts_default(&o);
+  if (o.check_every < 2) o.check_every = 2;
+  if (o.check_every % 2) o.check_every += 1;
+  if (o.max_inner < 1 || o.max_outer < 1 || o.max_linesearch < 1 || !(o.tol > 0) ||
+      !(o.inner_forcing > 0) || !(o.inner_floor > 0) || !(o.armijo_b > 0 && o.armijo_b < 1) ||
+      !(o.armijo_v > 0 && o.armijo_v < 1) || !(o.armijo_alpha0 > 0))
+    return fail(pl, GLAM_EINVAL, "glam_fit_path: bad options");
+  if (lambda[0] >= 0)
+    for (int k = 0; k < nlambda; ++k)
+      if (!(lambda[k] >= 0)) return fail(pl, GLAM_EINVAL, "glam_fit_path: negative lambda");
+  if (pl->precision == GLAM_FP64)
+    return fit_impl<double>(pl, X, (const double*)Y, (const double*)W, (const double*)pen_w, nlambda,
+                            lambda, o, Theta0, Theta_path, stats, nfit);
+  return fit_impl<float>(pl, X, (const float*)Y, (const float*)W, (const double*)pen_w, nlambda,
+                         lambda, o, Theta0, Theta_path, stats, nfit);
+}

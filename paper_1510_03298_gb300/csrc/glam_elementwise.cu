@@ -1,0 +1,741 @@
+// Entrywise steps and reductions of GD-PG.
+//
+//  * family pass (Sec. 6.1 step 2; App. B Eqs. four, weights, tennew): from eta, Y and the
+//    observation weights a it writes V = w, V (.) Z = u + w eta and optionally U, and reduces the
+//    loss f(eta) (FP64 accumulation) and max(w) (for the step size of Prop. 1);
+//  * proximal step (Sec. 3.2, Sec. 6.3): y = x + omega (x - x_prev), g = (Q - b)/n,
+//    x+ = soft(y - delta g, delta lambda w_m), with the inner stopping reduction;
+//  * Armijo rule (Sec. 5): Delta_k and the loss change at several trial steps in one pass over
+//    the cells, using eta(theta + alpha d) = eta + alpha (eta~ - eta) (linearity of H);
+//  * KKT residual, lambda_max (Sec. 6.4), penalty, conversions, Gram matrices (Prop. 1).
+//
+// Reductions: per-thread partials in the working precision over a few elements, FP64 across
+// threads and blocks, and a deterministic final sum in block order by the last block to finish
+// (no floating-point atomics, so every run gives the same bits).
+#include <cfloat>
+
+#include "glam_internal.cuh"
+
+namespace glam {
+namespace {
+
+constexpr int kEPT = 8;  // elements per thread per tile of a streaming reduction
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide sums of NV values; result valid in thread 0.
+template <int NV>
+__device__ void block_sum(double (&v)[NV]) {
+  __shared__ double sh[NV][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[k][warp] = v[k];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double t = lane < nw ? sh[k][lane] : 0.0;
+      v[k] = warp_sum(t);
+    }
+  }
+  __syncthreads();
+}
+
+__device__ double block_max(double v) {
+  __shared__ double sh[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_max(v);
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    double t = lane < nw ? sh[lane] : 0.0;
+    v = warp_max(t);
+  }
+  __syncthreads();
+  return v;
+}
+
+// Last-block-done: returns true in every thread of the block that finished last.  Partials
+// written before the call are visible to that block (threadfence before the ticket).
+__device__ bool last_block(unsigned int* counter) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int ticket = atomicAdd(counter, 1u);
+    is_last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  return is_last;
+}
+
+template <typename T>
+__device__ __forceinline__ T poisson_clamp();
+template <>
+__device__ __forceinline__ float poisson_clamp<float>() {
+  return 80.0f;  // exp(80) ~ 5.5e34 < FLT_MAX
+}
+template <>
+__device__ __forceinline__ double poisson_clamp<double>() {
+  return 700.0;
+}
+
+template <typename T>
+__device__ __forceinline__ T t_exp(T x);
+template <>
+__device__ __forceinline__ float t_exp<float>(float x) {
+  return expf(x);
+}
+template <>
+__device__ __forceinline__ double t_exp<double>(double x) {
+  return exp(x);
+}
+template <typename T>
+__device__ __forceinline__ T t_expm1(T x);
+template <>
+__device__ __forceinline__ float t_expm1<float>(float x) {
+  return expm1f(x);
+}
+template <>
+__device__ __forceinline__ double t_expm1<double>(double x) {
+  return expm1(x);
+}
+
+int red_blocks(int64_t n, int per_thread) {
+  const int64_t per_block = (int64_t)kThreads * per_thread;
+  int64_t b = (n + per_block - 1) / per_block;
+  const int cap = 4 * num_sms();
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  if (b > kMaxRedBlocks) b = kMaxRedBlocks;
+  return (int)b;
+}
+
+// ---------------------------------------------------------------- family pass
+template <typename T, typename TV>
+__global__ void __launch_bounds__(kThreads)
+family_kernel(int family, int64_t n, const T* __restrict__ eta, const T* __restrict__ Y,
+              const T* __restrict__ A, TV* __restrict__ V, T* __restrict__ VZ, T* __restrict__ U,
+              double rho_prod, DevScalars* sc, RedScratch red) {
+  double lsum = 0.0, wmax = 0.0;
+  int bad = 0;
+  const int64_t tile = (int64_t)gridDim.x * blockDim.x * kEPT;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kEPT; base < n; base += tile) {
+    T lpart = T(0);
+#pragma unroll
+    for (int k = 0; k < kEPT; ++k) {
+      const int64_t i = base + (int64_t)k * blockDim.x + threadIdx.x;
+      if (i >= n) break;
+      const T e = eta[i], y = Y[i], a = A[i];
+      T u, w, l;
+      if (family == GLAM_GAUSSIAN_IDENTITY) {
+        const T r = y - e;          // identity link: mu = eta
+        u = a * r;                  // Eq. (four)
+        w = a;                      // theta' = (g^-1)' = 1
+        l = T(0.5) * a * r * r;
+      } else {
+        T ec = e;
+        if (ec > poisson_clamp<T>()) {
+          ec = poisson_clamp<T>();
+          bad = 1;
+        }
+        const T mu = t_exp<T>(ec);  // log link: mu = exp(eta)
+        u = a * (y - mu);
+        w = a * mu;                 // (g^-1)' = exp(eta)
+        l = a * (mu - y * e);
+      }
+      if (!(isfinite(e) && isfinite(y) && isfinite(a))) bad = 1;
+      if (V != nullptr) V[i] = TV(w);
+      if (VZ != nullptr) VZ[i] = u + w * e;  // V (.) Z with Z = W^-1 u + eta (Eq. ten)
+      if (U != nullptr) U[i] = u;
+      lpart += l;
+      wmax = fmax(wmax, (double)w);
+    }
+    lsum += (double)lpart;
+  }
+  double v[1] = {lsum};
+  block_sum<1>(v);
+  const double m = block_max(wmax);
+  if (threadIdx.x == 0) {
+    red.partial[blockIdx.x * 2 + 0] = v[0];
+    red.partial[blockIdx.x * 2 + 1] = m;
+    if (bad) atomicOr(&sc->nonfinite, 1);
+  }
+  if (last_block(red.counter)) {
+    if (threadIdx.x == 0) {
+      double s = 0.0, mx = 0.0;
+      for (unsigned int b = 0; b < gridDim.x; ++b) {
+        s += __ldcg(&red.partial[b * 2 + 0]);
+        mx = fmax(mx, __ldcg(&red.partial[b * 2 + 1]));
+      }
+      sc->loss = s / (double)n;
+      sc->maxw = mx;
+      sc->Lhat = mx / (double)n * rho_prod;  // Prop. 1, Eq. (nineteennew), c = 1
+      *red.counter = 0u;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- loss only
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+loss_kernel(int family, int64_t n, const T* __restrict__ eta, const T* __restrict__ Y,
+            const T* __restrict__ A, double* out, RedScratch red) {
+  double lsum = 0.0;
+  const int64_t tile = (int64_t)gridDim.x * blockDim.x * kEPT;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kEPT; base < n; base += tile) {
+    T lpart = T(0);
+#pragma unroll
+    for (int k = 0; k < kEPT; ++k) {
+      const int64_t i = base + (int64_t)k * blockDim.x + threadIdx.x;
+      if (i >= n) break;
+      const T e = eta[i], y = Y[i], a = A[i];
+      if (family == GLAM_GAUSSIAN_IDENTITY) {
+        const T r = y - e;
+        lpart += T(0.5) * a * r * r;
+      } else {
+        lpart += a * (t_exp<T>(e) - y * e);
+      }
+    }
+    lsum += (double)lpart;
+  }
+  double v[1] = {lsum};
+  block_sum<1>(v);
+  if (threadIdx.x == 0) red.partial[blockIdx.x] = v[0];
+  if (last_block(red.counter)) {
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (unsigned int b = 0; b < gridDim.x; ++b) s += __ldcg(&red.partial[b]);
+      *out = s / (double)n;
+      *red.counter = 0u;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- scale / convert / finite
+template <typename T>
+__global__ void scale_kernel(int64_t n, const T* __restrict__ in, T* __restrict__ out, T scale) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[i] * scale;
+}
+
+template <typename TI, typename TO>
+__global__ void convert_kernel(int64_t n, const TI* __restrict__ in, TO* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (TO)in[i];
+}
+
+template <typename T>
+__global__ void vmul_kernel(int64_t n, const T* __restrict__ V, T* x, const int* skip) {
+  if (skip != nullptr && *skip) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = V[i] * x[i];
+}
+
+template <typename T>
+__global__ void finite_kernel(int64_t n, const T* __restrict__ x, DevScalars* sc) {
+  int bad = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite(x[i])) bad = 1;
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&sc->nonfinite, 1);
+}
+
+// ---------------------------------------------------------------- proximal step
+// out[m] = soft(y_m - delta g_m, delta lambda w_m), y = x + omega (x - x_prev) (Sec. 3.2, 6.3),
+// with the gradient of the quadratic model written as g = lin_scale * lin[m] + (sum_s Qpart[s]) / n:
+//   lin = b = X^T W z, lin_scale = -1/n:   g = (X^T W X y - X^T W z) / n     (Eq. twentyfive)
+//   lin = grad f(theta_k), lin_scale = 1:  g = grad f(theta_k) + X^T W X (y - theta_k) / n
+// (the same function of y; the second form needs the products only for the correction).
+// With a control block, omega, delta and lambda come from it, the kernel reduces
+// max_m |x+_m - y_m| and the last block decides whether the inner loop stops.
+template <typename Tq, typename TP>
+__global__ void __launch_bounds__(kThreads)
+prox_kernel(int64_t p, int ksplit, const Tq* __restrict__ Qpart, const TP* __restrict__ lin,
+            TP lin_scale, const TP* __restrict__ x, const TP* xprev, const TP* __restrict__ pen_w,
+            TP* out, TP inv_n, InnerCtl* ctl, TP omega_h, TP delta_h, TP lambda_h, const double* Lhat) {
+  TP omega, delta, lam;
+  if (ctl != nullptr) {
+    if (ctl->done) return;
+    const int l = ctl->l;
+    omega = TP(l - 1) / TP(l + 2);
+    delta = TP(ctl->delta);
+    lam = TP(ctl->lambda);
+  } else {
+    omega = omega_h;
+    delta = delta_h > TP(0) ? delta_h : TP(1.0 / *Lhat);
+    lam = lambda_h;
+  }
+  double crit = 0.0;
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < p;
+       m += (int64_t)gridDim.x * blockDim.x) {
+    TP q = TP(0);
+    for (int s = 0; s < ksplit; ++s) q += TP(Qpart[(int64_t)s * p + m]);
+    const TP g = lin_scale * lin[m] + q * inv_n;
+    const TP xm = x[m];
+    const TP y = xm + omega * (xm - xprev[m]);   // extrapolation, Sec. 3.2
+    const TP z = y - delta * g;
+    const TP thr = delta * lam * pen_w[m];
+    const TP az = fabs(z) - thr;                 // soft threshold, Sec. 6.3
+    const TP xn = az > TP(0) ? copysign(az, z) : TP(0);
+    out[m] = xn;
+    crit = fmax(crit, (double)fabs(xn - y));
+  }
+  if (ctl == nullptr) return;
+  const double bm = block_max(crit);
+  if (threadIdx.x == 0) atomicMax(&ctl->crit_bits, (unsigned long long)__double_as_longlong(bm));
+  if (last_block(&ctl->counter)) {
+    if (threadIdx.x == 0) {
+      const double c = __longlong_as_double((long long)atomicAdd(&ctl->crit_bits, 0ull));
+      ctl->crit = c;
+      ctl->iters_run += 1;
+      if (c <= ctl->stop_abs) {
+        ctl->done = 1;
+        ctl->stop_reason = 1;
+      } else if (ctl->l >= ctl->max_iter) {
+        ctl->done = 1;
+        ctl->stop_reason = 2;
+      }
+      ctl->l += 1;
+      ctl->crit_bits = 0ull;
+      ctl->counter = 0u;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- Armijo (Sec. 5)
+// sums[0] = sum_i u_i d_i;  sums[1 + j] = sum_i a_i (l_i(eta + alpha_j d) - l_i(eta)), d = eta~ - eta
+// with l_i the per-cell loss, written as a difference so that small steps keep their digits:
+//   Gaussian: t (t/2 - (y - eta)),  Poisson: exp(eta) expm1(t) - y t,   t = alpha_j (eta~ - eta).
+template <typename TE, typename T>
+__global__ void __launch_bounds__(kThreads)
+armijo_stream_kernel(int family, int64_t n, const TE* __restrict__ eta, const T* __restrict__ deta,
+                     const TE* __restrict__ Y, const TE* __restrict__ A, double alpha0, double bfac,
+                     int j0, DevScalars* sc, RedScratch red) {
+  double acc[kTrials + 1];
+#pragma unroll
+  for (int k = 0; k <= kTrials; ++k) acc[k] = 0.0;
+  T alpha[kTrials];
+  {
+    double a = alpha0;
+    for (int j = 0; j < j0; ++j) a *= bfac;
+#pragma unroll
+    for (int j = 0; j < kTrials; ++j) {
+      alpha[j] = T(a);
+      a *= bfac;
+    }
+  }
+  const int64_t tile = (int64_t)gridDim.x * blockDim.x * kEPT;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kEPT; base < n; base += tile) {
+    T part[kTrials + 1];
+#pragma unroll
+    for (int k = 0; k <= kTrials; ++k) part[k] = T(0);
+#pragma unroll 2
+    for (int k = 0; k < kEPT; ++k) {
+      const int64_t i = base + (int64_t)k * blockDim.x + threadIdx.x;
+      if (i >= n) break;
+      const T e = T(eta[i]), y = T(Y[i]), a = T(A[i]);
+      const T d = deta[i];  // eta(theta~) - eta(theta) = H(theta~ - theta)
+      if (family == GLAM_GAUSSIAN_IDENTITY) {
+        const T r = T(Y[i] - eta[i]);
+        part[0] += a * r * d;
+#pragma unroll
+        for (int j = 0; j < kTrials; ++j) {
+          const T t = alpha[j] * d;
+          part[1 + j] += a * (t * (T(0.5) * t - r));
+        }
+      } else {
+        const T mu = t_exp<T>(e);
+        part[0] += a * (y - mu) * d;
+#pragma unroll
+        for (int j = 0; j < kTrials; ++j) {
+          const T t = alpha[j] * d;
+          part[1 + j] += a * (mu * t_expm1<T>(t) - y * t);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k <= kTrials; ++k) acc[k] += (double)part[k];
+  }
+  block_sum<kTrials + 1>(acc);
+  if (threadIdx.x == 0)
+    for (int k = 0; k <= kTrials; ++k) red.partial[blockIdx.x * (kTrials + 1) + k] = acc[k];
+  if (last_block(red.counter)) {
+    if (threadIdx.x < kTrials + 1) {
+      const int k = threadIdx.x;
+      double s = 0.0;
+      for (unsigned int b = 0; b < gridDim.x; ++b) s += __ldcg(&red.partial[b * (kTrials + 1) + k]);
+      if (k == 0)
+        sc->dir = -s / (double)n;
+      else
+        sc->data_diff[k - 1] = s / (double)n;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *red.counter = 0u;
+  }
+}
+
+// pen_diff[j] = J(theta + alpha_j d) - J(theta); pen_tilde_diff = J(theta~) - J(theta);
+// pen = J(theta).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+armijo_penalty_kernel(int64_t p, const T* __restrict__ th, const T* __restrict__ tt,
+                      const T* __restrict__ pw, double alpha0, double bfac, int j0, DevScalars* sc,
+                      RedScratch red) {
+  constexpr int NV = kTrials + 2;
+  double acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+  double alpha[kTrials];
+  {
+    double a = alpha0;
+    for (int j = 0; j < j0; ++j) a *= bfac;
+    for (int j = 0; j < kTrials; ++j) {
+      alpha[j] = a;
+      a *= bfac;
+    }
+  }
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < p;
+       m += (int64_t)gridDim.x * blockDim.x) {
+    const double t0 = (double)th[m], t1 = (double)tt[m], w = (double)pw[m];
+    const double d = t1 - t0;
+    const double a0 = fabs(t0);
+    acc[0] += w * a0;
+    acc[1] += w * (fabs(t1) - a0);
+#pragma unroll
+    for (int j = 0; j < kTrials; ++j) acc[2 + j] += w * (fabs(t0 + alpha[j] * d) - a0);
+  }
+  block_sum<NV>(acc);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < NV; ++k) red.partial[blockIdx.x * NV + k] = acc[k];
+  if (last_block(red.counter)) {
+    if (threadIdx.x < NV) {
+      const int k = threadIdx.x;
+      double s = 0.0;
+      for (unsigned int b = 0; b < gridDim.x; ++b) s += __ldcg(&red.partial[b * NV + k]);
+      if (k == 0)
+        sc->pen = s;
+      else if (k == 1)
+        sc->pen_tilde_diff = s;
+      else
+        sc->pen_diff[k - 2] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *red.counter = 0u;
+  }
+}
+
+// Smallest j with F(theta + alpha_j d) - F(theta) <= alpha_j v Delta_k, where
+// Delta_k = -(1/n) u^T X d + lambda (J(theta~) - J(theta)).
+__global__ void armijo_select_kernel(double lambda, double v, double alpha0, double bfac, int j0,
+                                     DevScalars* sc) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double Delta = sc->dir + lambda * sc->pen_tilde_diff;
+  double a = alpha0;
+  for (int j = 0; j < j0; ++j) a *= bfac;
+  sc->accepted = -1;
+  for (int j = 0; j < kTrials; ++j) {
+    const double dF = sc->data_diff[j] + lambda * sc->pen_diff[j];
+    if (dF <= a * v * Delta) {
+      sc->accepted = j0 + j;
+      sc->alpha = a;
+      sc->F_new = sc->F + dF;
+      return;
+    }
+    a *= bfac;
+  }
+  sc->alpha = 0.0;
+}
+
+template <typename T>
+__global__ void armijo_update_kernel(int64_t p, T* __restrict__ th, const T* __restrict__ tt,
+                                     const DevScalars* __restrict__ sc) {
+  if (sc->accepted < 0) return;
+  const double alpha = sc->alpha;
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < p;
+       m += (int64_t)gridDim.x * blockDim.x) {
+    if (alpha == 1.0)
+      th[m] = tt[m];
+    else
+      th[m] = T((double)th[m] + alpha * ((double)tt[m] - (double)th[m]));
+  }
+}
+
+// ---------------------------------------------------------------- KKT / penalty / lambda_max
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+kkt_kernel(int64_t p, const double* __restrict__ g, const T* __restrict__ th,
+           const T* __restrict__ pw, double lambda, DevScalars* sc, RedScratch red) {
+  double rmax = 0.0;
+  double acc[2] = {0.0, 0.0};  // J(theta), nnz
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < p;
+       m += (int64_t)gridDim.x * blockDim.x) {
+    const double t = (double)th[m], thr = lambda * (double)pw[m], gm = g[m];
+    double r;
+    if (t != 0.0) {
+      r = fabs(gm + copysign(thr, t));
+      acc[1] += 1.0;
+    } else {
+      r = fmax(0.0, fabs(gm) - thr);
+    }
+    rmax = fmax(rmax, r);
+    acc[0] += (double)pw[m] * fabs(t);
+  }
+  block_sum<2>(acc);
+  const double bm = block_max(rmax);
+  if (threadIdx.x == 0) {
+    red.partial[blockIdx.x * 3 + 0] = bm;
+    red.partial[blockIdx.x * 3 + 1] = acc[0];
+    red.partial[blockIdx.x * 3 + 2] = acc[1];
+  }
+  if (last_block(red.counter)) {
+    if (threadIdx.x == 0) {
+      double mx = 0.0, pen = 0.0, nnz = 0.0;
+      for (unsigned int b = 0; b < gridDim.x; ++b) {
+        mx = fmax(mx, __ldcg(&red.partial[b * 3 + 0]));
+        pen += __ldcg(&red.partial[b * 3 + 1]);
+        nnz += __ldcg(&red.partial[b * 3 + 2]);
+      }
+      sc->kkt_max = mx;
+      sc->pen = pen;
+      sc->nnz = (int)nnz;
+      *red.counter = 0u;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+lmax_kernel(int64_t p, const double* __restrict__ g0, const T* __restrict__ pw, DevScalars* sc,
+            RedScratch red) {
+  double mx = 0.0;
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < p;
+       m += (int64_t)gridDim.x * blockDim.x)
+    mx = fmax(mx, fabs(g0[m]) / (double)pw[m]);
+  const double bm = block_max(mx);
+  if (threadIdx.x == 0) red.partial[blockIdx.x] = bm;
+  if (last_block(red.counter)) {
+    if (threadIdx.x == 0) {
+      double m2 = 0.0;
+      for (unsigned int b = 0; b < gridDim.x; ++b) m2 = fmax(m2, __ldcg(&red.partial[b]));
+      sc->lmax = m2;
+      *red.counter = 0u;
+    }
+  }
+}
+
+__global__ void gram_kernel(int nj, int pj, const double* __restrict__ XT, double* __restrict__ gram) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= pj * pj) return;
+  const int a = idx / pj, b = idx - a * pj;
+  const double* xa = XT + (int64_t)a * nj;
+  const double* xb = XT + (int64_t)b * nj;
+  double s = 0.0;
+  for (int i = 0; i < nj; ++i) s = fma(xa[i], xb[i], s);
+  gram[idx] = s;
+}
+
+int grid_for(int64_t n) {
+  int64_t b = (n + kThreads - 1) / kThreads;
+  const int cap = 8 * num_sms();
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+
+int num_sms() {
+  static int cached = 0;
+  if (cached == 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+      v = 152;
+    cached = v;
+  }
+  return cached;
+}
+
+template <typename T, typename TV>
+cudaError_t launch_family(int family, int64_t n, const T* eta, const T* Y, const T* A, TV* V, T* VZ,
+                          T* U, double rho_prod, DevScalars* sc, RedScratch red, cudaStream_t s) {
+  family_kernel<T, TV><<<red_blocks(n, kEPT), kThreads, 0, s>>>(family, n, eta, Y, A, V, VZ, U,
+                                                                rho_prod, sc, red);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_loss_only(int family, int64_t n, const T* eta, const T* Y, const T* A,
+                             double* out, RedScratch red, cudaStream_t s) {
+  loss_kernel<T><<<red_blocks(n, kEPT), kThreads, 0, s>>>(family, n, eta, Y, A, out, red);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_scale(int64_t n, const T* in, T* out, double scale, cudaStream_t s) {
+  scale_kernel<T><<<grid_for(n), kThreads, 0, s>>>(n, in, out, T(scale));
+  return cudaGetLastError();
+}
+
+template <typename TI, typename TO>
+cudaError_t launch_convert(int64_t n, const TI* in, TO* out, cudaStream_t s) {
+  convert_kernel<TI, TO><<<grid_for(n), kThreads, 0, s>>>(n, in, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_vmul(int64_t n, const T* V, T* x, const int* skip, cudaStream_t s) {
+  vmul_kernel<T><<<grid_for(n), kThreads, 0, s>>>(n, V, x, skip);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_check_finite(int64_t n, const T* x, DevScalars* sc, cudaStream_t s) {
+  finite_kernel<T><<<grid_for(n), kThreads, 0, s>>>(n, x, sc);
+  return cudaGetLastError();
+}
+
+template <typename Tq, typename TP>
+cudaError_t launch_prox(int64_t p, int ksplit, const Tq* Qpart, const TP* lin, double lin_scale,
+                        const TP* x, const TP* xprev, const TP* pen_w, TP* out, double inv_n,
+                        InnerCtl* ctl, double omega, double delta, double lambda,
+                        const double* Lhat, cudaStream_t s) {
+  int blocks = (int)((p + kThreads - 1) / kThreads);
+  if (blocks < 1) blocks = 1;
+  if (blocks > 4 * num_sms()) blocks = 4 * num_sms();
+  prox_kernel<Tq, TP><<<blocks, kThreads, 0, s>>>(p, ksplit, Qpart, lin, TP(lin_scale), x, xprev,
+                                                  pen_w, out, TP(inv_n), ctl, TP(omega), TP(delta),
+                                                  TP(lambda), Lhat);
+  return cudaGetLastError();
+}
+
+template <typename TE, typename T>
+cudaError_t launch_armijo_stream(int family, int64_t n, const TE* eta, const T* deta, const TE* Y,
+                                 const TE* A, double alpha0, double b, int j0, DevScalars* sc,
+                                 RedScratch red, cudaStream_t s) {
+  armijo_stream_kernel<TE, T><<<red_blocks(n, kEPT), kThreads, 0, s>>>(family, n, eta, deta, Y, A,
+                                                                       alpha0, b, j0, sc, red);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_armijo_penalty(int64_t p, const T* theta, const T* theta_t, const T* pen_w,
+                                  double alpha0, double b, int j0, DevScalars* sc, RedScratch red,
+                                  cudaStream_t s) {
+  armijo_penalty_kernel<T><<<red_blocks(p, 1), kThreads, 0, s>>>(p, theta, theta_t, pen_w, alpha0,
+                                                                 b, j0, sc, red);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_armijo_select(double lambda, double v, double alpha0, double b, int j0,
+                                 DevScalars* sc, cudaStream_t s) {
+  armijo_select_kernel<<<1, 32, 0, s>>>(lambda, v, alpha0, b, j0, sc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_armijo_update(int64_t p, T* theta, const T* theta_t, const DevScalars* sc,
+                                 cudaStream_t s) {
+  armijo_update_kernel<T><<<grid_for(p), kThreads, 0, s>>>(p, theta, theta_t, sc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_kkt(int64_t p, const double* g, const T* theta, const T* pen_w, double lambda,
+                       DevScalars* sc, RedScratch red, cudaStream_t s) {
+  kkt_kernel<T><<<red_blocks(p, 1), kThreads, 0, s>>>(p, g, theta, pen_w, lambda, sc, red);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_penalty(int64_t p, const T* theta, const T* pen_w, DevScalars* sc,
+                           RedScratch red, cudaStream_t s) {
+  // J(theta) only: reuse the Armijo penalty kernel with theta~ = theta.
+  armijo_penalty_kernel<T><<<red_blocks(p, 1), kThreads, 0, s>>>(p, theta, theta, pen_w, 1.0, 0.5,
+                                                                 0, sc, red);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_lambda_max(int64_t p, const double* g0, const T* pen_w, DevScalars* sc,
+                              RedScratch red, cudaStream_t s) {
+  lmax_kernel<T><<<red_blocks(p, 1), kThreads, 0, s>>>(p, g0, pen_w, sc, red);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram(int nj, int pj, const double* XT, double* gram, cudaStream_t s) {
+  const int tot = pj * pj;
+  gram_kernel<<<(tot + kThreads - 1) / kThreads, kThreads, 0, s>>>(nj, pj, XT, gram);
+  return cudaGetLastError();
+}
+
+#define GLAM_INST(T)                                                                              \
+  template cudaError_t launch_loss_only<T>(int, int64_t, const T*, const T*, const T*, double*,   \
+                                           RedScratch, cudaStream_t);                             \
+  template cudaError_t launch_scale<T>(int64_t, const T*, T*, double, cudaStream_t);              \
+  template cudaError_t launch_check_finite<T>(int64_t, const T*, DevScalars*, cudaStream_t);      \
+  template cudaError_t launch_vmul<T>(int64_t, const T*, T*, const int*, cudaStream_t);           \
+  template cudaError_t launch_armijo_penalty<T>(int64_t, const T*, const T*, const T*, double,    \
+                                                double, int, DevScalars*, RedScratch,             \
+                                                cudaStream_t);                                    \
+  template cudaError_t launch_armijo_update<T>(int64_t, T*, const T*, const DevScalars*,          \
+                                               cudaStream_t);                                     \
+  template cudaError_t launch_kkt<T>(int64_t, const double*, const T*, const T*, double,          \
+                                     DevScalars*, RedScratch, cudaStream_t);                      \
+  template cudaError_t launch_penalty<T>(int64_t, const T*, const T*, DevScalars*, RedScratch,    \
+                                         cudaStream_t);                                           \
+  template cudaError_t launch_lambda_max<T>(int64_t, const double*, const T*, DevScalars*,        \
+                                            RedScratch, cudaStream_t);
+
+GLAM_INST(float)
+GLAM_INST(double)
+#undef GLAM_INST
+
+template cudaError_t launch_family<float, float>(int, int64_t, const float*, const float*,
+                                                 const float*, float*, float*, float*, double,
+                                                 DevScalars*, RedScratch, cudaStream_t);
+template cudaError_t launch_family<double, double>(int, int64_t, const double*, const double*,
+                                                   const double*, double*, double*, double*, double,
+                                                   DevScalars*, RedScratch, cudaStream_t);
+template cudaError_t launch_family<double, float>(int, int64_t, const double*, const double*,
+                                                  const double*, float*, double*, double*, double,
+                                                  DevScalars*, RedScratch, cudaStream_t);
+#define GLAM_PROX_INST(Tq, TP)                                                                  \
+  template cudaError_t launch_prox<Tq, TP>(int64_t, int, const Tq*, const TP*, double, const TP*,  \
+                                           const TP*, const TP*, TP*, double, InnerCtl*, double,  \
+                                           double, double, const double*, cudaStream_t);
+GLAM_PROX_INST(float, float)
+GLAM_PROX_INST(double, double)
+GLAM_PROX_INST(float, double)
+#undef GLAM_PROX_INST
+template cudaError_t launch_armijo_stream<double, float>(int, int64_t, const double*, const float*,
+                                                         const double*, const double*, double,
+                                                         double, int, DevScalars*, RedScratch,
+                                                         cudaStream_t);
+template cudaError_t launch_armijo_stream<double, double>(int, int64_t, const double*,
+                                                          const double*, const double*,
+                                                          const double*, double, double, int,
+                                                          DevScalars*, RedScratch, cudaStream_t);
+
+template cudaError_t launch_convert<float, double>(int64_t, const float*, double*, cudaStream_t);
+template cudaError_t launch_convert<double, float>(int64_t, const double*, float*, cudaStream_t);
+template cudaError_t launch_convert<double, double>(int64_t, const double*, double*, cudaStream_t);
+template cudaError_t launch_convert<float, float>(int64_t, const float*, float*, cudaStream_t);
+
+}  // namespace glam

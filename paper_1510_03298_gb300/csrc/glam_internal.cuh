@@ -1,0 +1,159 @@
+// Internal declarations of libglam (not part of the ABI).
+//
+// Layout: paper arrays n1 x n2 x n3 are C-order (n3, n2, n1) buffers (vec of App. A);
+// Theta is (p3, p2, p1); a marginal design X_j is the C-order (p_j, n_j) buffer XT_j
+// (column-major n_j x p_j).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "glam.h"
+
+namespace glam {
+
+constexpr int kThreads = 256;
+constexpr int kTrials = 8;          // Armijo trial step sizes evaluated per n-stream pass
+constexpr int kMaxRedBlocks = 1216; // 8 x 152 SMs: upper bound of blocks in a reduction grid
+constexpr int kRedSlots = 2 * kTrials + 4;
+
+// ------------------------------------------------------------------------------------
+// Device-resident control of the inner PG loop (Sec. 3.2).  One instance per plan; every
+// kernel of an inner iteration reads `done` first and returns when it is set, so a captured
+// chunk of iterations costs nothing after convergence.
+// ------------------------------------------------------------------------------------
+struct InnerCtl {
+  int l;                       // iteration index of the paper (1-based): omega_l = (l-1)/(l+2)
+  int done;                    // nonzero: the loop has stopped
+  int max_iter;                // cap on l
+  int iters_run;               // iterations executed since the last reset
+  unsigned int counter;        // last-block-done counter of the prox kernel
+  int stop_reason;             // 1 converged, 2 cap
+  unsigned long long crit_bits;  // atomicMax accumulator: max_m |x+_m - y_m| (double bits, >= 0)
+  double delta;                // step size
+  double lambda;               // penalty parameter
+  double stop_abs;             // stop when max_m |x+_m - y_m| <= stop_abs
+  double crit;                 // last criterion value
+};
+
+// Scalars produced by reductions and consumed by later kernels (all device-resident).
+struct DevScalars {
+  double loss;                 // f(eta) of the last family pass (already divided by n)
+  double maxw;                 // max_i w_i of the last family pass
+  double Lhat;                 // Prop. 1 bound for the last family pass
+  double pen;                  // J(theta) (weighted l1) of the last penalty pass
+  double F;                    // objective at the current outer iterate
+  double dir;                  // -(1/n) <U, eta_bar - eta>
+  double data_diff[kTrials];   // (1/n) sum a (l(eta + alpha_j d_eta) - l(eta))
+  double pen_diff[kTrials];    // J(theta + alpha_j d) - J(theta)
+  double pen_tilde_diff;       // J(theta~) - J(theta)
+  double alpha;                // accepted Armijo step (0 if none)
+  double F_new;
+  double kkt_max;              // max_m r_m (unscaled)
+  double lmax;                 // lambda_max
+  int accepted;                // index j of the accepted trial, -1 if none in this pass
+  int nnz;
+  int nonfinite;               // set by kernels that meet a non-finite value
+  int pad;
+};
+
+struct RedScratch {
+  double* partial;             // kMaxRedBlocks * kRedSlots doubles
+  unsigned int* counter;       // one counter (reset by the last block)
+};
+
+// ------------------------------------------------------------------------------------
+// Generic strided, batched, split-K SIMT GEMM used for the mode products (App. A rho):
+//   C[b, split][m, n] = sum_{k in split} A[b][m, k] * B[b][k, n]
+// Optional B-operand extrapolation y = x + omega (x - x_prev) (Sec. 3.2) applied on load.
+// ------------------------------------------------------------------------------------
+struct GemmDesc {
+  int M, N, K, batch, ksplit;
+  int64_t sAb, sAm, sAk;
+  int64_t sBb, sBk, sBn;
+  int64_t sCb, sCm, sCn;
+  int64_t sCsplit;
+};
+
+template <typename T, typename TB>
+cudaError_t launch_gemm(const GemmDesc& d, const T* A, const TB* B, T* C, cudaStream_t s,
+                        const TB* Bprev = nullptr, const TB* Bsub = nullptr,
+                        const InnerCtl* ctl = nullptr, double omega = 0.0,
+                        const int* skip = nullptr);
+
+// ------------------------------------------------------------------------------------
+// Fused bottleneck of Sec. 6.2: per slab i3, S_b[i3] = X2^T (V[i3] (.) (X2 (T_a[i3] X1^T))) X1
+// (the last H stage and the first G stage on-chip; eta never reaches memory).
+// ------------------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_fused_slab(int n1, int n2, int n3, int p1, int p2, const T* X1T, const T* X2T,
+                              const T* Ta, const T* V, T* Sb, cudaStream_t s,
+                              const int* skip = nullptr);
+int fused_slab_supported(int n1, int n2, int p1, int p2, int elem_bytes);
+cudaError_t fused_prepare();
+
+// ------------------------------------------------------------------------------------
+// Elementwise / reduction kernels.
+// ------------------------------------------------------------------------------------
+template <typename T, typename TV>
+cudaError_t launch_family(int family, int64_t n, const T* eta, const T* Y, const T* A, TV* V, T* VZ,
+                          T* U, double rho_prod, DevScalars* sc, RedScratch red, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_scale(int64_t n, const T* in, T* out, double scale, cudaStream_t s);
+
+template <typename Tq, typename TP>
+cudaError_t launch_prox(int64_t p, int ksplit, const Tq* Qpart, const TP* lin, double lin_scale,
+                        const TP* x, const TP* xprev, const TP* pen_w, TP* out, double inv_n,
+                        InnerCtl* ctl, double omega, double delta, double lambda,
+                        const double* Lhat, cudaStream_t s);
+
+template <typename TE, typename T>
+cudaError_t launch_armijo_stream(int family, int64_t n, const TE* eta, const T* deta, const TE* Y,
+                                 const TE* A, double alpha0, double b, int j0, DevScalars* sc,
+                                 RedScratch red, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_armijo_penalty(int64_t p, const T* theta, const T* theta_t, const T* pen_w,
+                                  double alpha0, double b, int j0, DevScalars* sc, RedScratch red,
+                                  cudaStream_t s);
+
+cudaError_t launch_armijo_select(double lambda, double v, double alpha0, double b, int j0,
+                                 DevScalars* sc, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_armijo_update(int64_t p, T* theta, const T* theta_t, const DevScalars* sc,
+                                 cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_kkt(int64_t p, const double* g, const T* theta, const T* pen_w, double lambda,
+                       DevScalars* sc, RedScratch red, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_penalty(int64_t p, const T* theta, const T* pen_w, DevScalars* sc,
+                           RedScratch red, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_lambda_max(int64_t p, const double* g0, const T* pen_w, DevScalars* sc,
+                              RedScratch red, cudaStream_t s);
+
+template <typename TI, typename TO>
+cudaError_t launch_convert(int64_t n, const TI* in, TO* out, cudaStream_t s);
+
+cudaError_t launch_gram(int nj, int pj, const double* XT, double* gram, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_vmul(int64_t n, const T* V, T* x, const int* skip, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_check_finite(int64_t n, const T* x, DevScalars* sc, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_loss_only(int family, int64_t n, const T* eta, const T* Y, const T* A,
+                             double* out, RedScratch red, cudaStream_t s);
+
+int num_sms();
+
+}  // namespace glam

@@ -1,0 +1,162 @@
+"""Parity of the GPU lambda path (glam_fit_path) with the oracle.
+
+The target of every lambda is the minimiser of Eq. (five) (the lasso KKT conditions), which the
+oracle reaches by running Algorithm 1 in FP64 to KKT 1e-10.  Parity is judged on the solution's
+objective, its linear predictor, the KKT residual evaluated by the oracle, and the active set
+(exactly, except degenerate coordinates: zero in the oracle with |g_m| within 1e-6 lambda_max of
+the threshold, or |theta_m| <= 1e-9 max|theta|).  The iteration trajectory is not compared.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import gen
+import oracle as O
+from gpu_helpers import dev, dtype_of, gpu_or_skip, host, plan_prec, rel_err
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _active_sets_agree(d, th_gpu, th_ref, lam, lmax, r_tot):
+    """Active sets agree except on degenerate coordinates.  Two points whose KKT residuals sum to
+    r_tot (scaled by lambda_max) can differ by at most r_tot lambda_max / mu_A in theta (mu_A: the
+    smallest eigenvalue of the Hessian on the active set, from the explicit design), so an active
+    coordinate smaller than that bound, or an inactive one whose subgradient slack is below
+    r_tot lambda_max, may legitimately flip."""
+    g = O.gradient(d, th_ref)
+    thr = lam * d.pen_w
+    act = th_ref != 0
+    Phi = O.kron_design(d.Xs)
+    eta = O.H(d.Xs, th_ref)
+    w = O.vec(O.irls_weight(d.family, eta, d.a))
+    ia = np.flatnonzero(O.vec(act))
+    bound = 0.0
+    if ia.size:
+        Hs = Phi[:, ia].T @ (w[:, None] * Phi[:, ia]) / d.n
+        mu = max(np.linalg.eigvalsh(Hs).min(), 1e-300)
+        bound = 10.0 * r_tot * lmax / mu
+    degenerate = (~act & (np.abs(np.abs(g) - thr) <= 10.0 * r_tot * lmax)) | (act & (np.abs(th_ref) <= bound))
+    ok = ~degenerate
+    return np.array_equal((th_gpu != 0)[ok], (th_ref != 0)[ok]), int(degenerate.sum())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_gauss20_path_matches_oracle(prec):
+    torch, g = gpu_or_skip()
+    pr = gen.make_workload(0)
+    gold = np.load(os.path.join(GOLDEN, "gauss20_path.npz"))
+    d = O.GlamData.from_c(pr.family, pr.XT, pr.Y, pr.W, pr.pen_w)
+    dt = dtype_of(prec)
+    plan = g.Plan(pr.n, pr.p, pr.family, plan_prec(g, prec))
+    tol = 1e-9 if prec == "fp64" else 1e-6
+    res = g.glam_fit_path(plan, [dev(x, dt) for x in pr.XT], dev(pr.Y, dt), dev(pr.W, dt),
+                          dev(pr.pen_w, torch.float64), nlambda=10,
+                          opts=g.glam_opts_default(tol=tol, lambda_min_ratio=1e-3))
+    assert res.status == g.GLAM_OK, res.message
+    lmax = float(gold["lmax"])
+    np.testing.assert_allclose(res.lambdas, gold["lambdas"], rtol=1e-12 if prec == "fp64" else 1e-6)
+    path = host(res.path)
+    for k in range(10):
+        th = O.paper_array(path[k])
+        ref = O.paper_array(gold["thetas"][k])
+        lam = res.lambdas[k]
+        # KKT of the returned solution, evaluated by the oracle on the FP64 data
+        r = O.kkt_residual(d, th, lam, lmax)
+        assert r <= (1e-9 if prec == "fp64" else 3e-6), (k, r)
+        F, Fref = O.objective(d, th, lam), float(gold["objective"][k])
+        assert abs(F - Fref) <= (1e-10 if prec == "fp64" else 1e-6) * abs(Fref), (k, F, Fref)
+        assert rel_err(O.H(d.Xs, th), O.H(d.Xs, ref)) <= (1e-6 if prec == "fp64" else 1e-4)
+        same, ndeg = _active_sets_agree(d, th, ref, lam, lmax, r + float(gold["kkt"][k]))
+        assert same, (k, ndeg)
+        assert res.stats[k]["kkt"] <= tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("fam", [gen.GAUSSIAN, gen.POISSON])
+def test_small_masked_path_matches_oracle(prec, fam):
+    torch, g = gpu_or_skip()
+    n, p = (13, 11, 9), (5, 4, 4)
+    pr = gen.random_problem(11, n, p, fam, mask_frac=0.15, basis="normal", pen_w="rand")
+    d = O.GlamData.from_c(pr.family, pr.XT, pr.Y, pr.W, pr.pen_w)
+    lams, thetas, stats, lmax = O.fit_path(d, nlambda=6, ratio=1e-2, tol=1e-10)
+    dt = dtype_of(prec)
+    plan = g.Plan(n, p, fam, plan_prec(g, prec))
+    tol = 1e-9 if prec == "fp64" else 1e-6
+    res = g.glam_fit_path(plan, [dev(x, dt) for x in pr.XT], dev(pr.Y, dt), dev(pr.W, dt),
+                          dev(pr.pen_w, torch.float64), lambdas=list(lams),
+                          opts=g.glam_opts_default(tol=tol))
+    assert res.status == g.GLAM_OK, res.message
+    path = host(res.path)
+    for k in range(len(lams)):
+        th = O.paper_array(path[k])
+        r = O.kkt_residual(d, th, lams[k], lmax)
+        assert r <= (1e-9 if prec == "fp64" else 3e-6)
+        F, Fref = O.objective(d, th, lams[k]), O.objective(d, thetas[k], lams[k])
+        assert abs(F - Fref) <= (1e-10 if prec == "fp64" else 1e-6) * abs(Fref)
+        np.testing.assert_allclose(th, thetas[k], atol=(1e-7 if prec == "fp64" else 1e-4) * max(1, np.abs(thetas[k]).max()))
+        same, ndeg = _active_sets_agree(d, th, thetas[k], lams[k], lmax, r + stats[k].kkt)
+        assert same, (k, ndeg, np.flatnonzero(O.vec(th) != 0), np.flatnonzero(O.vec(thetas[k]) != 0))
+
+
+def test_lambda_max_gives_exact_zero_and_gaussian_needs_no_line_search():
+    torch, g = gpu_or_skip()
+    pr = gen.random_problem(12, (20, 17, 15), (6, 5, 5), gen.GAUSSIAN, mask_frac=0.1, basis="normal")
+    d = O.GlamData.from_c(pr.family, pr.XT, pr.Y, pr.W, pr.pen_w)
+    plan = g.Plan(pr.n, pr.p, pr.family, g.GLAM_FP64)
+    res = g.glam_fit_path(plan, [dev(x, torch.float64) for x in pr.XT], dev(pr.Y, torch.float64),
+                          dev(pr.W, torch.float64), dev(pr.pen_w, torch.float64), nlambda=5,
+                          opts=g.glam_opts_default(lambda_min_ratio=1e-2))
+    assert res.status == g.GLAM_OK
+    assert abs(res.lambdas[0] - O.lambda_max(d)) <= 1e-12 * res.lambdas[0]
+    assert torch.count_nonzero(res.path[0]).item() == 0
+    assert torch.count_nonzero(res.path[1]).item() > 0
+    assert all(s["armijo_backtracks"] == 0 for s in res.stats)
+
+
+def test_iteration_cap_returns_partial_path():
+    torch, g = gpu_or_skip()
+    pr = gen.random_problem(13, (20, 17, 15), (6, 5, 5), gen.POISSON, basis="normal")
+    plan = g.Plan(pr.n, pr.p, pr.family, g.GLAM_FP32)
+    dt = torch.float32
+    res = g.glam_fit_path(plan, [dev(x, dt) for x in pr.XT], dev(pr.Y, dt), dev(pr.W, dt),
+                          dev(pr.pen_w, torch.float64), nlambda=5,
+                          opts=g.glam_opts_default(max_outer=1, max_inner=2, lambda_min_ratio=1e-2))
+    assert res.status == g.GLAM_ENOCONV
+    assert 1 <= res.nfit < 5
+    assert res.stats[res.nfit]["status"] == g.GLAM_ENOCONV
+
+
+def test_nonfinite_input_is_reported():
+    torch, g = gpu_or_skip()
+    pr = gen.random_problem(14, (10, 9, 8), (4, 4, 4), gen.GAUSSIAN, basis="normal")
+    Y = pr.Y.copy()
+    Y[3, 2, 1] = np.nan
+    plan = g.Plan(pr.n, pr.p, pr.family, g.GLAM_FP64)
+    with pytest.raises(g.GlamError) as e:
+        g.glam_fit_path(plan, [dev(x, torch.float64) for x in pr.XT], dev(Y, torch.float64),
+                        dev(pr.W, torch.float64), dev(pr.pen_w, torch.float64), nlambda=3)
+    assert e.value.status == g.GLAM_ENONFINITE
+
+
+def test_resume_from_a_warm_start():
+    """A path split in two, the second half started from the first half's last solution
+    (Theta0), reaches the same solutions as the uninterrupted path."""
+    torch, g = gpu_or_skip()
+    pr = gen.random_problem(15, (16, 14, 12), (5, 5, 4), gen.POISSON, mask_frac=0.1, basis="normal")
+    d = O.GlamData.from_c(pr.family, pr.XT, pr.Y, pr.W, pr.pen_w)
+    plan = g.Plan(pr.n, pr.p, pr.family, g.GLAM_FP64)
+    X = [dev(x, torch.float64) for x in pr.XT]
+    Y, W, pw = dev(pr.Y, torch.float64), dev(pr.W, torch.float64), dev(pr.pen_w, torch.float64)
+    o = g.glam_opts_default(tol=1e-10, lambda_min_ratio=1e-2)
+    full = g.glam_fit_path(plan, X, Y, W, pw, nlambda=6, opts=o)
+    a = g.glam_fit_path(plan, X, Y, W, pw, lambdas=full.lambdas[:3], opts=o)
+    b = g.glam_fit_path(plan, X, Y, W, pw, lambdas=full.lambdas[3:], opts=o, Theta0=a.path[2].contiguous())
+    lmax = O.lambda_max(d)
+    for k in range(3):
+        th_full = O.paper_array(host(full.path[3 + k]))
+        th_res = O.paper_array(host(b.path[k]))
+        lam = full.lambdas[3 + k]
+        assert abs(O.objective(d, th_full, lam) - O.objective(d, th_res, lam)) <= 1e-11 * abs(O.objective(d, th_full, lam))
+        assert O.kkt_residual(d, th_res, lam, lmax) <= 1e-10

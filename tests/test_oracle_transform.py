@@ -120,3 +120,18 @@ def test_planted_transpose_is_caught(monkeypatch):
 
     monkeypatch.setattr(O.glam_oracle, "rho", bad)
     assert not np.allclose(O.vec(O.glam_oracle.H(Xs, Theta)), Phi @ Theta.reshape(-1, order="F"))
+
+
+def test_design_row_and_column_entries():
+    """One row / column of the explicit Kronecker design gives single entries of H and G."""
+    rng = np.random.default_rng(8)
+    n, p = (5, 4, 3), (2, 3, 4)
+    Xs, Theta = _rand(rng, n, p)
+    Phi = np.kron(Xs[2], np.kron(Xs[1], Xs[0]))
+    U = rng.standard_normal(n)
+    for idx in [(0, 0, 0), (4, 3, 2), (2, 1, 0)]:
+        i = idx[0] + n[0] * (idx[1] + n[1] * idx[2])
+        assert np.isclose(np.sum(O.design_row(Xs, idx) * Theta), Phi[i] @ Theta.reshape(-1, order="F"))
+    for midx in [(0, 0, 0), (1, 2, 3), (1, 0, 2)]:
+        m = midx[0] + p[0] * (midx[1] + p[1] * midx[2])
+        assert np.isclose(np.sum(O.design_col(Xs, midx) * U), Phi[:, m] @ U.reshape(-1, order="F"))
