@@ -1,0 +1,381 @@
+#!/usr/bin/env python3
+"""Benchmark of the GD-PG lambda path on the 128 x 128 x 600 Gaussian GLAM workload.
+
+One step = one warm-started 50-lambda path fit (glam_fit_path: lambda_max, inner FISTA loop,
+Armijo line search, FP64 KKT test to 1e-6 at every lambda) on the synthetic workload with
+cubic B-spline bases p = (20, 20, 60), FP32 mode products.  The headline value is prox-grad
+(inner PG) iterations per second over the timed steps; the line also carries the H-transform
+GB/s of glam_predict, the FP64 GPU path on a bounded sample of the same path, the roofline of
+the dominant kernel, the FP64 CPU oracle baseline and an end-to-end figure with host buffers.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --gpus N > 1 (launched by torchrun) every rank fits its own replica of the workload on its
+own GPU (independent fits: no collective on the data path) and value is the sum of iterations
+over all ranks divided by the slowest rank's time (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "prox-grad iters/s & H-transform GB/s on 128x128x600 grid vs FP64 GPU path at KKT 1e-6"
+UNIT = "iters/s"
+WORKLOAD = "gauss-128x128x600 p=(20,20,60) 50-lambda path, ratio 1e-3, KKT 1e-6"
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """Samples nvidia-smi during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f".clocks_{os.getpid()}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------------------------
+# oracle (CPU) legs: the cpu_baseline of our line, and the whole --impl reference arm
+# ------------------------------------------------------------------------------------------
+
+def _oracle_setup():
+    import gen
+    import oracle as O
+    pr = gen.make_workload(1)
+    d = O.GlamData.from_c(pr.family, pr.XT, pr.Y, pr.W, pr.pen_w)
+    lmax = O.lambda_max(d)
+    # the quadratic model of the first outer iteration at theta = 0 (W = 1: V = a, Z = Y)
+    w = O.irls_weight(d.family, np.zeros_like(d.Y), d.a)
+    z = O.working_response(d.family, np.zeros_like(d.Y), d.Y, d.a)
+    Lhat = O.lipschitz_bound(d.Xs, w)
+    return O, d, lmax, w, z, Lhat
+
+
+def _oracle_iters(O, d, lmax, w, z, Lhat, iters):
+    """`iters` inner PG iterations of the oracle (Sec. 3.2) at lambda = 0.1 lambda_max."""
+    t0 = time.perf_counter()
+    res = O.inner_pg(d, w, z, np.zeros(d.pshape), 1.0 / Lhat, 0.1 * lmax, tol=0.0, max_iter=iters)
+    return res.iters, time.perf_counter() - t0
+
+
+def cpu_baseline(budget_s=12.0):
+    O, d, lmax, w, z, Lhat = _oracle_setup()
+    n_it, t = _oracle_iters(O, d, lmax, w, z, Lhat, 1)
+    per = max(t, 1e-3)
+    k = int(max(2, min(200, budget_s / per)))
+    n_it, t = _oracle_iters(O, d, lmax, w, z, Lhat, k)
+    return {"value": n_it / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n_it} inner PG iterations (FP64 numpy, paper's mode order) of the "
+                      f"128x128x600 Gaussian model at lambda = 0.1 lambda_max; {t:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if world > 1 and rank != 0:
+        return 0
+    O, d, lmax, w, z, Lhat = _oracle_setup()
+    per_step = 2
+    for _ in range(args.warmup):
+        _oracle_iters(O, d, lmax, w, z, Lhat, per_step)
+    tot_it, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        it, t = _oracle_iters(O, d, lmax, w, z, Lhat, per_step)
+        tot_it += it
+        tot_t += t
+    v = tot_it / tot_t
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD + " (oracle: inner PG iterations of the same model)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{per_step} inner PG iterations per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import gen
+    import paper_1510_03298_gb300 as g
+    from paper_1510_03298_gb300 import build as gb
+    if not os.path.exists(g.library_path()):
+        gb.build()
+    g.load_library()
+
+    pr = gen.make_workload(1)
+    dev = torch.device("cuda", local)
+    f32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    f64 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    X = [f32(x) for x in pr.XT]
+    Y, W = f32(pr.Y), f32(pr.W)
+    pen = f64(pr.pen_w)
+    plan = g.Plan(pr.n, pr.p, pr.family, g.GLAM_FP32)
+    opts = g.glam_opts_default(tol=1e-6, lambda_min_ratio=1e-3)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def step():
+        flush.fill_(1.0)  # evict L2 between steps
+        return g.glam_fit_path(plan, X, Y, W, pen, nlambda=pr.nlambda, opts=opts)
+
+    for _ in range(args.warmup):
+        r = step()
+    if r.status != g.GLAM_OK:
+        raise SystemExit(f"fit failed: {r.message}")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    clocks = Clocks(local)
+    launches0 = g.glam_launch_count()
+    clocks.start()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    ev0.record()
+    results = [step() for _ in range(args.steps)]
+    ev1.record()
+    barrier()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    launches = g.glam_launch_count() - launches0
+    ms = ev0.elapsed_time(ev1)
+    iters = sum(sum(s["inner_iters"] for s in r.stats) for r in results)
+    ok = all(r.status == g.GLAM_OK for r in results)
+    kkt_max = max(max(s["kkt"] for s in r.stats) for r in results)
+    t_rank = ms / 1e3
+    if dist is not None:
+        tt = torch.tensor([t_rank, float(iters)], dtype=torch.float64, device=dev)
+        tmax = tt.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+        t_job, iters_job = tmax[0].item(), tt[1].item()
+    else:
+        t_job, iters_job = t_rank, float(iters)
+    value = iters_job / t_job
+
+    extra = {}
+    if rank == 0:
+        extra = measure_details(g, torch, pr, plan, X, Y, W, pen, opts, dev, flush, results[-1])
+        extra["e2e"] = measure_e2e(g, torch, pr, plan, opts, dev, args.steps)
+        if world == 1 and not args.no_cpu:
+            extra["cpu_baseline"] = cpu_baseline()
+    if dist is not None:
+        dist.barrier()
+    if rank == 0:
+        st = results[-1].stats
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "grid": [128, 128, 600], "basis": [20, 20, 60],
+                           "nlambda": pr.nlambda, "precision": "fp32 mode products, fp64 refinement",
+                           "l2": "256 MB buffer written between steps",
+                           "parallelism": f"replicas x{world}"},
+                "gpu_launches": int(launches),
+                "clocks": clk,
+                "path": {"converged": ok, "max_kkt": kkt_max, "inner_iters_per_step": iters / args.steps,
+                         "outer_iters": sum(s["outer_iters"] for s in st),
+                         "fp64_passes": sum(s["fp64_passes"] for s in st),
+                         "wall_s_per_step": wall / args.steps}}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_details(g, torch, pr, plan, X, Y, W, pen, opts, dev, flush, last):
+    peaks, src = _peaks()
+    out = {}
+    n1, n2, n3 = pr.n
+    p1, p2, p3 = pr.p
+    n, p = n1 * n2 * n3, p1 * p2 * p3
+    # H-transform (glam_predict) throughput: algorithmic bytes = read Theta and X_j, write eta
+    theta = last.path[-1].float().contiguous()
+    eta = torch.empty((n3, n2, n1), dtype=torch.float32, device=dev)
+    times = []
+    for r in range(60):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.glam_predict(plan, X, theta, eta)
+        b.record()
+        torch.cuda.synchronize()
+        if r >= 10:
+            times.append(a.elapsed_time(b))
+    t_h = statistics.median(times) / 1e3
+    h_bytes = 4 * (n + p + sum(a * b for a, b in zip(pr.n, pr.p)))
+    h_flops = 2 * (n3 * p3 * p2 * p1 + n3 * p2 * p1 * n1 + n3 * n2 * p2 * n1)
+    out["h_transform"] = {"GB/s": h_bytes / t_h / 1e9, "ms": t_h * 1e3, "bytes": h_bytes,
+                          "frac_hbm": h_bytes / t_h / 1e9 / peaks["hbm_gbs"], "peak_src": src,
+                          "tflops": h_flops / t_h / 1e12}
+    # dominant kernel of the inner iteration: the fused slab kernel G(V (.) H(.))
+    q = g.glam_quad_build(plan, X, theta, Y, W)
+    ms = g.glam_time_inner_kernels(plan, X, q, reps=100)
+    per_iter = sum(ms)
+    slab = 2 * p2 * p1 * n1 + 4 * n2 * n1 * p2 + n2 * n1 + 2 * p2 * n1 * p1
+    fl = slab * n3
+    by = 4 * n + 2 * 4 * n3 * p2 * p1 + 4 * (n1 * p1 + n2 * p2)
+    peak_alu = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    t_f = ms[1] / 1e3
+    out["roofline"] = {"bound": "alu", "kernel": "fused_slab_kernel<float,20> (G(V(.)H) per slab)",
+                       "achieved": fl / t_f / 1e12, "peak": peak_alu, "unit": "TFLOP/s",
+                       "frac": fl / t_f / 1e12 / peak_alu, "traffic": None,
+                       "flops_per_launch": fl, "ms_per_launch": ms[1],
+                       "peak_note": "FP32 SIMT: 152 SMs x 128 lanes x 2 FLOP x max SM clock",
+                       "hbm_view": {"bytes_per_launch": by, "GB/s": by / t_f / 1e9,
+                                    "frac": by / t_f / 1e9 / peaks["hbm_gbs"], "peak_src": src}}
+    out["inner_iteration_ms"] = {"mode3_extrap": ms[0], "fused_slab": ms[1], "mode3_adj_split": ms[2],
+                                 "prox": ms[3], "sum": per_iter}
+    # the FP64 GPU path on a bounded sample of the same path (its first 4 lambdas)
+    plan64 = g.Plan(pr.n, pr.p, pr.family, g.GLAM_FP64)
+    X64 = [x.double() for x in X]
+    lams = last.lambdas[:4]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r64 = g.glam_fit_path(plan64, X64, Y.double(), W.double(), pen, lambdas=lams, opts=opts)
+    t64 = time.perf_counter() - t0
+    it64 = sum(s["inner_iters"] for s in r64.stats)
+    it32 = sum(s["inner_iters"] for s in last.stats[:4])
+    t32 = sum(s["time_ms"] for s in last.stats[:4]) / 1e3
+    out["fp64_gpu_path"] = {"iters_per_s": it64 / t64, "sample": "first 4 lambdas of the path",
+                            "time_s": t64, "fp32_time_s_same_lambdas": t32,
+                            "path_speedup_fp32_over_fp64": t64 / max(t32, 1e-9),
+                            "status": r64.status, "max_kkt": max(s["kkt"] for s in r64.stats),
+                            "fp32_iters_same_lambdas": it32, "fp64_iters": it64}
+    plan64.close()
+    return out
+
+
+def measure_e2e(g, torch, pr, plan, opts, dev, steps):
+    """The same metric through the public API with pinned host buffers: every step copies
+    X, Y, W and the penalty weights to the device and the path back to the host."""
+    hX = [torch.tensor(x, dtype=torch.float32).pin_memory() for x in pr.XT]
+    hY = torch.tensor(pr.Y, dtype=torch.float32).pin_memory()
+    hW = torch.tensor(pr.W, dtype=torch.float32).pin_memory()
+    hP = torch.tensor(pr.pen_w, dtype=torch.float64).pin_memory()
+    hout = torch.empty((pr.nlambda,) + tuple(pr.pen_w.shape), dtype=torch.float64).pin_memory()
+    dX = [torch.empty_like(x, device=dev) for x in hX]
+    dY, dW, dP = torch.empty_like(hY, device=dev), torch.empty_like(hW, device=dev), torch.empty_like(hP, device=dev)
+    h2d = sum(x.numel() * 4 for x in hX) + hY.numel() * 4 + hW.numel() * 4 + hP.numel() * 8
+    d2h = hout.numel() * 8
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    iters = 0
+    for _ in range(steps):
+        for a, b in zip(dX, hX):
+            a.copy_(b, non_blocking=True)
+        dY.copy_(hY, non_blocking=True)
+        dW.copy_(hW, non_blocking=True)
+        dP.copy_(hP, non_blocking=True)
+        r = g.glam_fit_path(plan, dX, dY, dW, dP, nlambda=pr.nlambda, opts=opts)
+        hout.copy_(r.path, non_blocking=True)
+        torch.cuda.synchronize()
+        iters += sum(s["inner_iters"] for s in r.stats)
+    t = time.perf_counter() - t0
+    return {"value": iters / t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -189,6 +189,22 @@ int glam_fit_path(glam_plan* plan, const void* const X[3], const void* Y, const 
                   const void* pen_w, int nlambda, double* lambda, const glam_opts* opts,
                   const double* Theta0, double* Theta_path, glam_stats* stats, int* nfit);
 
+/* ---- diagnostics (tracing hooks of this library; the paper has no counterpart) ---- */
+
+/* Number of kernels this process has launched through libglam so far (each replay of a captured
+ * CUDA graph adds its kernel nodes).  Never fails. */
+int64_t glam_launch_count(void);
+
+/* Time the four kernels of one inner PG iteration of glam_fit_path, as the fit launches them, on
+ * the plan's stream with CUDA events: ms[0] the mode-3 product of the extrapolated correction,
+ * ms[1] the fused per-slab G(V (.) H(.)) kernel (0 if the shape uses the unfused chain), ms[2] the
+ * split mode-3 adjoint product, ms[3] the proximal step.  Each kernel runs 2 + reps times back to
+ * back; ms (HOST, 4 doubles) receives the mean of the last reps launches in milliseconds.  Uses
+ * q->V as the weights and the plan's FP64 state of the last fit (values do not change the work).
+ * Synchronizes the plan's stream. */
+int glam_time_inner_kernels(glam_plan* plan, const void* const X[3], const glam_quad* q, int reps,
+                            double* ms);
+
 #ifdef __cplusplus
 }
 #endif

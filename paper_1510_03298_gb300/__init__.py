@@ -24,7 +24,8 @@ __all__ = [
     "GLAM_ETIMEOUT", "GLAM_GAUSSIAN_IDENTITY", "GLAM_POISSON_LOG", "GLAM_FP64", "GLAM_FP32",
     "GLAM_TF32", "GLAM_BF16", "GlamError", "Plan", "Quad", "FitResult", "library_path", "load_library",
     "glam_opts_default", "glam_plan_create", "glam_plan_destroy", "glam_predict", "glam_gradient",
-    "glam_loss", "glam_quad_build", "glam_prox_step", "glam_fit_path",
+    "glam_loss", "glam_quad_build", "glam_prox_step", "glam_fit_path", "glam_launch_count",
+    "glam_time_inner_kernels",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -112,6 +113,9 @@ def load_library():
         "glam_fit_path": (C.c_int, [_VP, _X3, _VP, _VP, _VP, C.c_int, C.POINTER(C.c_double),
                                     C.POINTER(GlamOpts), _VP, _VP, C.POINTER(GlamStats),
                                     C.POINTER(C.c_int)]),
+        "glam_launch_count": (C.c_int64, []),
+        "glam_time_inner_kernels": (C.c_int, [_VP, _X3, C.POINTER(GlamQuadC), C.c_int,
+                                              C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -376,3 +380,19 @@ def _p64(t, shape, name):
     if tuple(t.shape) != tuple(shape) or not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous with shape {tuple(shape)}")
     return t
+
+
+def glam_launch_count() -> int:
+    """Kernels launched through libglam by this process so far (graph nodes included)."""
+    return int(load_library().glam_launch_count())
+
+
+def glam_time_inner_kernels(plan: Plan, X, quad: Quad, reps: int = 50):
+    """Mean CUDA-event time (ms) per launch of the four inner-iteration kernels on the plan's
+    stream: [mode-3 product, fused slab G(V(.)H), split mode-3 adjoint, prox step]."""
+    plan._sync_stream()
+    xs = plan._X(X)
+    ms = (C.c_double * 4)()
+    qc = quad.c()
+    _check(load_library().glam_time_inner_kernels(plan.handle, xs, C.byref(qc), int(reps), ms), plan.handle)
+    return list(ms)

@@ -30,6 +30,7 @@ struct Work {
   T* Xc[3] = {nullptr, nullptr, nullptr};  // converted copies of the marginal designs
   T *Yc = nullptr, *Wc = nullptr, *penc = nullptr;
   T* one = nullptr;                        // the 1 x 1 design of a d = 2 problem
+  T* dn = nullptr;                         // y - theta_k of the next inner iteration (p)
   bool ready = false;
 };
 
@@ -172,7 +173,12 @@ struct Ops {
   int G(const T* U, T* out) {
     CK(launch_gemm<T, T>(d_mode2_adj(pl), X[1], U, w.Tb, s));
     CK(launch_gemm<T, T>(d_mode1_adj(pl), w.Tb, X[0], w.Sb, s));
-    CK(launch_gemm<T, T>(d_mode3_adj(pl, 1), X[2], w.Sb, out, s));
+    if (pl->ksplit > 1) {
+      CK(launch_gemm<T, T>(d_mode3_adj(pl, pl->ksplit), X[2], w.Sb, w.Qpart, s));
+      CK(launch_sum_splits<T>(pl->p, pl->ksplit, w.Qpart, out, s));
+    } else {
+      CK(launch_gemm<T, T>(d_mode3_adj(pl, 1), X[2], w.Sb, out, s));
+    }
     return GLAM_OK;
   }
   // eta = H(<X_j>, x - sub) for a parameter array held in TB (the correction of a refinement)
@@ -183,14 +189,15 @@ struct Ops {
     CK(launch_gemm<T, T>(d_mode2_fwd(pl), X[1], w.Tb, eta, s));
     return GLAM_OK;
   }
-  // Qpart = partial sums of G(V (.) H(y - sub)), y = x + omega (x - x_prev)  (Eq. twentysixnew)
+  // Qpart = partial sums of G(V (.) H(y - sub)), y = x + omega (x - x_prev)  (Eq. twentysixnew);
+  // with xp = sub = nullptr the operand x is used as it is.
   template <typename TB>
   int XtWX(const TB* x, const TB* xp, const TB* sub, const T* V, const InnerCtl* ctl,
            double omega, const int* skip) {
     CK(launch_gemm<T, TB>(d_mode3_fwd(pl), X[2], x, w.Ta, s, xp, sub, ctl, omega, skip));
     if (pl->fused[sizeof(T) == 8 ? 1 : 0]) {
       CK(launch_fused_slab<T>((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2,
-                              X[0], X[1], w.Ta, V, w.Sb, s, skip));
+                              X[0], X[1], w.Ta, V, w.Sb, s, skip, &pl->sc->timeout));
     } else {
       T* tmp = w.eta_bar;
       CK(launch_gemm<T, T>(d_mode1_fwd(pl), w.Ta, X[0], w.Tb, s, nullptr, nullptr, nullptr, 0.0, skip));
@@ -218,6 +225,7 @@ int alloc_work(glam_plan* pl, Work<T>& w, bool full) {
   CKS(dalloc(pl, &w.U, n));
   CKS(dalloc(pl, &w.theta, p));
   CKS(dalloc(pl, &w.grad, p));
+  CKS(dalloc(pl, &w.dn, p));
   CKS(dalloc(pl, &w.one, 1));
   const T one = T(1);
   CK(cudaMemcpy(w.one, &one, sizeof(T), cudaMemcpyHostToDevice));
@@ -340,14 +348,18 @@ int glam_plan_create(const glam_dims* dims, int family, int precision, void* str
     return code;
   };
   if (cudaGetDevice(&pl->device) != cudaSuccess) { pl->err = "cudaGetDevice failed"; return bail(GLAM_ECUDA); }
-  if (fused_prepare() != cudaSuccess) { pl->err = "cudaFuncSetAttribute failed"; return bail(GLAM_ECUDA); }
+  {
+    const cudaError_t e = fused_prepare();
+    if (e != cudaSuccess) {
+      pl->err = std::string("fused kernel set-up (cudaFuncSetAttribute): ") + cudaGetErrorString(e);
+      return bail(GLAM_ECUDA);
+    }
+  }
   // split of the last G stage over i3 so that the small p3 x p2p1 output still fills the GPU
   {
-    const int64_t tiles = ((pl->p3 + 63) / 64) * ((pl->p2 * pl->p1 + 63) / 64);
-    int64_t ks = (2 * num_sms() + tiles - 1) / tiles;
-    if (ks > pl->n3 / 16) ks = pl->n3 / 16;
+    int64_t ks = pl->n3 / 64;  // about 64 rows of i3 per split
     if (ks < 1) ks = 1;
-    if (ks > 64) ks = 64;
+    if (ks > 16) ks = 16;
     pl->ksplit = (int)ks;
   }
   pl->fused[0] = fused_slab_supported((int)pl->n1, (int)pl->n2, (int)pl->p1, (int)pl->p2, 4) != 0;
@@ -619,6 +631,7 @@ struct Fit {
   const double* Y64 = nullptr;
   const double* W64 = nullptr;
   cudaGraphExec_t graph = nullptr;
+  int64_t graph_kernels = 0;
   ~Fit() {
     if (graph) cudaGraphExecDestroy(graph);
   }
@@ -638,6 +651,7 @@ int fp64_pass(Fit<T>& f, double lambda, double& r, double& F, int& nnz, bool& no
   CK(launch_kkt<double>(pl->p, pl->gk, pl->th, pl->pen, lambda, pl->sc, pl->red, f.s));
   objective_kernel<<<1, 32, 0, f.s>>>(pl->sc, lambda);
   CK(cudaGetLastError());
+  count_launches(1);
   CK(cudaMemcpyAsync(pl->h_sc, pl->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, f.s));
   CK(cudaStreamSynchronize(f.s));
   r = pl->h_sc->kkt_max / f.lmax;
@@ -654,24 +668,29 @@ int capture_chunk(Fit<T>& f) {
   const int C = f.o.check_every;
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(f.s, cudaStreamCaptureModeThreadLocal));
+  set_capturing(true);
   int st = GLAM_OK;
   for (int it = 0; it < C && st == GLAM_OK; ++it) {
     double* x = (it % 2 == 0) ? pl->x0 : pl->x1;
     double* xp = (it % 2 == 0) ? pl->x1 : pl->x0;
-    st = op.template XtWX<double>(x, xp, pl->th, op.w.V, pl->ctl, 0.0, &pl->ctl->done);
+    st = op.template XtWX<T>(op.w.dn, nullptr, nullptr, op.w.V, nullptr, 0.0, &pl->ctl->done);
     if (st == GLAM_OK) {
       cudaError_t e = launch_prox<T, double>(pl->p, pl->ksplit, op.w.Qpart, pl->gk, 1.0, x, xp,
                                              pl->pen, xp, 1.0 / (double)pl->n, pl->ctl, 0.0, 0.0,
-                                             0.0, nullptr, f.s);
+                                             0.0, nullptr, f.s, op.w.dn, pl->th);
       if (e != cudaSuccess) st = fail(pl, GLAM_ECUDA, std::string("prox launch: ") + cudaGetErrorString(e));
     }
   }
   cudaError_t e = cudaStreamEndCapture(f.s, &g);
+  set_capturing(false);
   if (st != GLAM_OK) {
     if (g) cudaGraphDestroy(g);
     return st;
   }
   if (e != cudaSuccess) return fail(pl, GLAM_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+  size_t nodes = 0;
+  if (g) cudaGraphGetNodes(g, nullptr, &nodes);
+  f.graph_kernels = (int64_t)nodes;
   e = cudaGraphInstantiate(&f.graph, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return fail(pl, GLAM_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
@@ -685,19 +704,26 @@ int run_inner(Fit<T>& f, double lambda, double stop_rel, int max_iter, double** 
   glam_plan* pl = f.pl;
   CK(cudaMemcpyAsync(pl->x0, pl->th, sizeof(double) * pl->p, cudaMemcpyDeviceToDevice, f.s));
   CK(cudaMemcpyAsync(pl->x1, pl->th, sizeof(double) * pl->p, cudaMemcpyDeviceToDevice, f.s));
+  CK(cudaMemsetAsync(work_of<T>(pl).dn, 0, sizeof(T) * pl->p, f.s));  // y(1) - theta_k = 0
+  CK(cudaMemsetAsync(&pl->sc->timeout, 0, sizeof(int), f.s));
   ctl_init_kernel<<<1, 32, 0, f.s>>>(pl->ctl, pl->sc, lambda, stop_rel, max_iter);
   CK(cudaGetLastError());
+  count_launches(1);
   if (f.graph == nullptr) CKS(capture_chunk<T>(f));
   const int C = f.o.check_every;
   const int max_chunks = max_iter / C + 2;
   bool done = false;
   for (int c = 0; c < max_chunks && !done; ++c) {
     CK(cudaGraphLaunch(f.graph, f.s));
+    count_launches(f.graph_kernels);
     CK(cudaMemcpyAsync(pl->h_ctl, pl->ctl, sizeof(InnerCtl), cudaMemcpyDeviceToHost, f.s));
     CK(cudaStreamSynchronize(f.s));
     done = pl->h_ctl->done != 0;
   }
   if (!done) return fail(pl, GLAM_ETIMEOUT, "inner loop did not stop within its iteration cap");
+  CK(cudaMemcpyAsync(pl->h_sc, pl->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, f.s));
+  CK(cudaStreamSynchronize(f.s));
+  if (pl->h_sc->timeout) return fail(pl, GLAM_ETIMEOUT, "a bounded device-side wait ran out");
   iters = pl->h_ctl->iters_run;
   reason = pl->h_ctl->stop_reason;
   *xout = (iters % 2 == 1) ? pl->x1 : pl->x0;
@@ -897,4 +923,61 @@ int glam_fit_path(glam_plan* pl, const void* const X[3], const void* Y, const vo
                             lambda, o, Theta0, Theta_path, stats, nfit);
   return fit_impl<float>(pl, X, (const float*)Y, (const float*)W, (const double*)pen_w, nlambda,
                          lambda, o, Theta0, Theta_path, stats, nfit);
+}
+
+// ======================================================================== diagnostics
+int64_t glam_launch_count(void) { return launch_count(); }
+
+namespace {
+template <typename T>
+int time_inner_impl(glam_plan* pl, const void* const X[3], const glam_quad* q, int reps, double* ms) {
+  Ops<T> op(pl, pl->stream, X);
+  const T* V = (const T*)q->V;
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  auto timed = [&](int which) -> int {
+    for (int r = -2; r < reps; ++r) {
+      if (r == 0) CK(cudaEventRecord(a, pl->stream));
+      switch (which) {
+        case 0:
+          CK(launch_gemm<T, T>(d_mode3_fwd(pl), op.X[2], op.w.dn, op.w.Ta, pl->stream));
+          break;
+        case 1:
+          if (pl->fused[sizeof(T) == 8 ? 1 : 0])
+            CK(launch_fused_slab<T>((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2,
+                                    op.X[0], op.X[1], op.w.Ta, V, op.w.Sb, pl->stream, nullptr,
+                                    &pl->sc->timeout));
+          break;
+        case 2:
+          CK(launch_gemm<T, T>(d_mode3_adj(pl, pl->ksplit), op.X[2], op.w.Sb, op.w.Qpart, pl->stream));
+          break;
+        default:
+          CK(launch_prox<T, double>(pl->p, pl->ksplit, op.w.Qpart, pl->gk, 1.0, pl->x0, pl->x1,
+                                    pl->pen, pl->ptmp, 1.0 / (double)pl->n, nullptr, 0.5, 1e-3, 0.0,
+                                    nullptr, pl->stream, op.w.grad, pl->th));
+      }
+    }
+    CK(cudaEventRecord(b, pl->stream));
+    CK(cudaEventSynchronize(b));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, a, b));
+    ms[which] = (double)t / reps;
+    return GLAM_OK;
+  };
+  int st = GLAM_OK;
+  for (int k = 0; k < 4 && st == GLAM_OK; ++k) st = timed(k);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return st;
+}
+}  // namespace
+
+int glam_time_inner_kernels(glam_plan* pl, const void* const X[3], const glam_quad* q, int reps,
+                            double* ms) {
+  CKS(check_plan(pl));
+  CKS(validate_X(pl, X));
+  if (!q || !q->V || !ms || reps < 1) return fail(pl, GLAM_EINVAL, "glam_time_inner_kernels: bad argument");
+  if (pl->precision == GLAM_FP64) return time_inner_impl<double>(pl, X, q, reps, ms);
+  return time_inner_impl<float>(pl, X, q, reps, ms);
 }

@@ -12,6 +12,7 @@
 // Reductions: per-thread partials in the working precision over a few elements, FP64 across
 // threads and blocks, and a deterministic final sum in block order by the last block to finish
 // (no floating-point atomics, so every run gives the same bits).
+#include <atomic>
 #include <cfloat>
 
 #include "glam_internal.cuh"
@@ -240,6 +241,16 @@ __global__ void convert_kernel(int64_t n, const TI* __restrict__ in, TO* __restr
 }
 
 template <typename T>
+__global__ void sum_splits_kernel(int64_t p, int ksplit, const T* __restrict__ part, T* __restrict__ out) {
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < p;
+       m += (int64_t)gridDim.x * blockDim.x) {
+    T acc = T(0);
+    for (int s = 0; s < ksplit; ++s) acc += part[(int64_t)s * p + m];
+    out[m] = acc;
+  }
+}
+
+template <typename T>
 __global__ void vmul_kernel(int64_t n, const T* __restrict__ V, T* x, const int* skip) {
   if (skip != nullptr && *skip) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -264,16 +275,20 @@ __global__ void finite_kernel(int64_t n, const T* __restrict__ x, DevScalars* sc
 // (the same function of y; the second form needs the products only for the correction).
 // With a control block, omega, delta and lambda come from it, the kernel reduces
 // max_m |x+_m - y_m| and the last block decides whether the inner loop stops.
+// With dnext, the kernel also writes the operand of the next iteration's first mode product,
+// dnext = y(l+1) - anchor = x+ + omega_{l+1} (x+ - x) - anchor, rounded to Tq.
 template <typename Tq, typename TP>
 __global__ void __launch_bounds__(kThreads)
 prox_kernel(int64_t p, int ksplit, const Tq* __restrict__ Qpart, const TP* __restrict__ lin,
             TP lin_scale, const TP* __restrict__ x, const TP* xprev, const TP* __restrict__ pen_w,
-            TP* out, TP inv_n, InnerCtl* ctl, TP omega_h, TP delta_h, TP lambda_h, const double* Lhat) {
-  TP omega, delta, lam;
+            TP* out, TP inv_n, InnerCtl* ctl, TP omega_h, TP delta_h, TP lambda_h, const double* Lhat,
+            Tq* __restrict__ dnext, const TP* __restrict__ anchor) {
+  TP omega, delta, lam, omega_next = TP(0);
   if (ctl != nullptr) {
     if (ctl->done) return;
     const int l = ctl->l;
     omega = TP(l - 1) / TP(l + 2);
+    omega_next = TP(l) / TP(l + 3);
     delta = TP(ctl->delta);
     lam = TP(ctl->lambda);
   } else {
@@ -294,6 +309,7 @@ prox_kernel(int64_t p, int ksplit, const Tq* __restrict__ Qpart, const TP* __res
     const TP az = fabs(z) - thr;                 // soft threshold, Sec. 6.3
     const TP xn = az > TP(0) ? copysign(az, z) : TP(0);
     out[m] = xn;
+    if (dnext != nullptr) dnext[m] = Tq(xn + omega_next * (xn - xm) - anchor[m]);
     crit = fmax(crit, (double)fabs(xn - y));
   }
   if (ctl == nullptr) return;
@@ -560,6 +576,17 @@ int grid_for(int64_t n) {
 
 }  // namespace
 
+namespace {
+std::atomic<int64_t> g_launches{0};
+std::atomic<int> g_capturing{0};
+}  // namespace
+
+void count_launches(int64_t k) {
+  if (g_capturing.load(std::memory_order_relaxed) == 0) g_launches.fetch_add(k, std::memory_order_relaxed);
+}
+int64_t launch_count() { return g_launches.load(); }
+void set_capturing(bool on) { g_capturing.store(on ? 1 : 0); }
+
 int num_sms() {
   static int cached = 0;
   if (cached == 0) {
@@ -577,6 +604,7 @@ cudaError_t launch_family(int family, int64_t n, const T* eta, const T* Y, const
                           T* U, double rho_prod, DevScalars* sc, RedScratch red, cudaStream_t s) {
   family_kernel<T, TV><<<red_blocks(n, kEPT), kThreads, 0, s>>>(family, n, eta, Y, A, V, VZ, U,
                                                                 rho_prod, sc, red);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -584,30 +612,42 @@ template <typename T>
 cudaError_t launch_loss_only(int family, int64_t n, const T* eta, const T* Y, const T* A,
                              double* out, RedScratch red, cudaStream_t s) {
   loss_kernel<T><<<red_blocks(n, kEPT), kThreads, 0, s>>>(family, n, eta, Y, A, out, red);
+  count_launches(1);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_scale(int64_t n, const T* in, T* out, double scale, cudaStream_t s) {
   scale_kernel<T><<<grid_for(n), kThreads, 0, s>>>(n, in, out, T(scale));
+  count_launches(1);
   return cudaGetLastError();
 }
 
 template <typename TI, typename TO>
 cudaError_t launch_convert(int64_t n, const TI* in, TO* out, cudaStream_t s) {
   convert_kernel<TI, TO><<<grid_for(n), kThreads, 0, s>>>(n, in, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_sum_splits(int64_t p, int ksplit, const T* part, T* out, cudaStream_t s) {
+  sum_splits_kernel<T><<<grid_for(p), kThreads, 0, s>>>(p, ksplit, part, out);
+  count_launches(1);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_vmul(int64_t n, const T* V, T* x, const int* skip, cudaStream_t s) {
   vmul_kernel<T><<<grid_for(n), kThreads, 0, s>>>(n, V, x, skip);
+  count_launches(1);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_check_finite(int64_t n, const T* x, DevScalars* sc, cudaStream_t s) {
   finite_kernel<T><<<grid_for(n), kThreads, 0, s>>>(n, x, sc);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -615,13 +655,14 @@ template <typename Tq, typename TP>
 cudaError_t launch_prox(int64_t p, int ksplit, const Tq* Qpart, const TP* lin, double lin_scale,
                         const TP* x, const TP* xprev, const TP* pen_w, TP* out, double inv_n,
                         InnerCtl* ctl, double omega, double delta, double lambda,
-                        const double* Lhat, cudaStream_t s) {
+                        const double* Lhat, cudaStream_t s, Tq* dnext, const TP* anchor) {
   int blocks = (int)((p + kThreads - 1) / kThreads);
   if (blocks < 1) blocks = 1;
   if (blocks > 4 * num_sms()) blocks = 4 * num_sms();
   prox_kernel<Tq, TP><<<blocks, kThreads, 0, s>>>(p, ksplit, Qpart, lin, TP(lin_scale), x, xprev,
                                                   pen_w, out, TP(inv_n), ctl, TP(omega), TP(delta),
-                                                  TP(lambda), Lhat);
+                                                  TP(lambda), Lhat, dnext, anchor);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -631,6 +672,7 @@ cudaError_t launch_armijo_stream(int family, int64_t n, const TE* eta, const T* 
                                  RedScratch red, cudaStream_t s) {
   armijo_stream_kernel<TE, T><<<red_blocks(n, kEPT), kThreads, 0, s>>>(family, n, eta, deta, Y, A,
                                                                        alpha0, b, j0, sc, red);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -640,12 +682,14 @@ cudaError_t launch_armijo_penalty(int64_t p, const T* theta, const T* theta_t, c
                                   cudaStream_t s) {
   armijo_penalty_kernel<T><<<red_blocks(p, 1), kThreads, 0, s>>>(p, theta, theta_t, pen_w, alpha0,
                                                                  b, j0, sc, red);
+  count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_armijo_select(double lambda, double v, double alpha0, double b, int j0,
                                  DevScalars* sc, cudaStream_t s) {
   armijo_select_kernel<<<1, 32, 0, s>>>(lambda, v, alpha0, b, j0, sc);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -653,6 +697,7 @@ template <typename T>
 cudaError_t launch_armijo_update(int64_t p, T* theta, const T* theta_t, const DevScalars* sc,
                                  cudaStream_t s) {
   armijo_update_kernel<T><<<grid_for(p), kThreads, 0, s>>>(p, theta, theta_t, sc);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -660,6 +705,7 @@ template <typename T>
 cudaError_t launch_kkt(int64_t p, const double* g, const T* theta, const T* pen_w, double lambda,
                        DevScalars* sc, RedScratch red, cudaStream_t s) {
   kkt_kernel<T><<<red_blocks(p, 1), kThreads, 0, s>>>(p, g, theta, pen_w, lambda, sc, red);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -669,6 +715,7 @@ cudaError_t launch_penalty(int64_t p, const T* theta, const T* pen_w, DevScalars
   // J(theta) only: reuse the Armijo penalty kernel with theta~ = theta.
   armijo_penalty_kernel<T><<<red_blocks(p, 1), kThreads, 0, s>>>(p, theta, theta, pen_w, 1.0, 0.5,
                                                                  0, sc, red);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -676,12 +723,14 @@ template <typename T>
 cudaError_t launch_lambda_max(int64_t p, const double* g0, const T* pen_w, DevScalars* sc,
                               RedScratch red, cudaStream_t s) {
   lmax_kernel<T><<<red_blocks(p, 1), kThreads, 0, s>>>(p, g0, pen_w, sc, red);
+  count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gram(int nj, int pj, const double* XT, double* gram, cudaStream_t s) {
   const int tot = pj * pj;
   gram_kernel<<<(tot + kThreads - 1) / kThreads, kThreads, 0, s>>>(nj, pj, XT, gram);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -691,6 +740,7 @@ cudaError_t launch_gram(int nj, int pj, const double* XT, double* gram, cudaStre
   template cudaError_t launch_scale<T>(int64_t, const T*, T*, double, cudaStream_t);              \
   template cudaError_t launch_check_finite<T>(int64_t, const T*, DevScalars*, cudaStream_t);      \
   template cudaError_t launch_vmul<T>(int64_t, const T*, T*, const int*, cudaStream_t);           \
+  template cudaError_t launch_sum_splits<T>(int64_t, int, const T*, T*, cudaStream_t);            \
   template cudaError_t launch_armijo_penalty<T>(int64_t, const T*, const T*, const T*, double,    \
                                                 double, int, DevScalars*, RedScratch,             \
                                                 cudaStream_t);                                    \
@@ -719,7 +769,8 @@ template cudaError_t launch_family<double, float>(int, int64_t, const double*, c
 #define GLAM_PROX_INST(Tq, TP)                                                                  \
   template cudaError_t launch_prox<Tq, TP>(int64_t, int, const Tq*, const TP*, double, const TP*,  \
                                            const TP*, const TP*, TP*, double, InnerCtl*, double,  \
-                                           double, double, const double*, cudaStream_t);
+                                           double, double, const double*, cudaStream_t, Tq*,      \
+                                           const TP*);
 GLAM_PROX_INST(float, float)
 GLAM_PROX_INST(double, double)
 GLAM_PROX_INST(float, double)

@@ -4,18 +4,26 @@
 // Mode order: H contracts mode 3 first (T_a = rho over X_3, computed by the GEMM kernel), then
 // mode 1 and mode 2 inside this kernel; G contracts mode 2, then mode 1 inside this kernel, and
 // mode 3 last (GEMM kernel).  For one slab i3 (a contiguous n2 x n1 block of V):
-//   T_b  (p2 x n1) = T_a[i3] (p2 x p1) . X_1^T        phase 1
-//   eta  (n2 x n1) = X_2 (n2 x p2) . T_b              phase 2 (registers only)
-//   r            = V[i3] (.) eta                      phase 2
-//   S    (p2 x n1) = X_2^T . r                        phase 2 (registers, then shared memory)
-//   S_b[i3] (p2 x p1) = S . X_1                       phase 3
-// eta and r never leave the SM: per inner iteration the kernel streams V once from memory and
-// touches only the small T_a / S_b slabs otherwise.
+//   T_b  (p2 x n1) = T_a[i3] (p2 x p1) . X_1^T        (per thread, registers)
+//   eta  (n2 x n1) = X_2 (n2 x p2) . T_b              (registers only)
+//   r            = V[i3] (.) eta
+//   S    (p2 x n1) = X_2^T . r                        (registers, then shared memory)
+//   S_b[i3] (p2 x p1) = S . X_1                       (shared memory -> global)
+// eta and r never leave the SM: per inner iteration the kernel streams V once and touches only
+// the small T_a / S_b slabs otherwise.
 //
-// Phase 2 mapping: lanes walk the unit-stride index i1 (coalesced V loads), warps split the
-// columns into 32-wide tiles and the rows i2 into RG groups.  Each lane holds its column of T_b
-// and its column of S (P values each) in registers; the X_2 row is read from shared memory with
-// 16-byte broadcast loads and used twice (for eta and for S).
+// Schedule: a persistent grid (one CTA per SM) walks the slabs i3 = blockIdx.x + k gridDim.x.
+// With STAGE, the V slabs are double-buffered in shared memory by 1-D TMA bulk copies
+// (cp.async.bulk with an mbarrier transaction count): slab k + 2 is in flight while slab k is
+// computed.  Every mbarrier wait is bounded (about two seconds of %globaltimer); a wait that
+// runs out sets *err and the CTA leaves the loop together.
+//
+// Thread mapping: lanes walk the unit-stride index i1 (conflict-free shared reads of V and
+// X_1), warps split the columns into 32-wide tiles (CT of them) and the rows i2 into RG groups.
+// Each lane forms its own column of T_b (P values) from T_a and X_1, then for each of its rows
+// loads the X_2 row with 16-byte broadcast reads and uses it twice (for eta and for S).
+#include <cstdint>
+
 #include "glam_internal.cuh"
 
 namespace glam {
@@ -54,112 +62,259 @@ __device__ __forceinline__ void load_row(const T* __restrict__ src, T (&dst)[P])
   }
 }
 
+// ---------------------------------------------------------------- mbarrier / bulk-copy PTX
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // bounded wait: ~2 s
+
+// Bounded wait for phase `parity` of the barrier: true on completion, false on time-out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+
+// Block size cap: 16 warps for FP32; 8 for FP64, whose register arrays take twice the space.
+template <typename T>
+constexpr int max_threads() {
+  return sizeof(T) == 8 ? 256 : 512;
+}
+
 struct SlabShape {
   int n1, n2, n3, p1, p2, CT, RG, LD;
+  uint32_t vbytes;  // n2 * n1 * sizeof(T) (bulk copy size)
 };
 
-template <typename T, int P>
-__global__ void __launch_bounds__(256)
+// Shared-memory layout of one CTA, in elements.  Every section starts on a 32-byte boundary
+// (the 16-byte vector reads of X_2 and T_a rows and the bulk-copy destinations need 16).
+struct SlabLayout {
+  int64_t vbuf, x2, x1, ta, sred, total;
+};
+
+__host__ __device__ inline int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+__host__ __device__ inline SlabLayout slab_layout(const SlabShape& sh, int P, int elem, bool stage) {
+  const int64_t A = 32 / elem;
+  SlabLayout L;
+  int64_t off = 0;
+  L.vbuf = off;
+  off = align_up(off + (stage ? 2 * (int64_t)sh.n2 * sh.n1 : 0), A);
+  L.x2 = off;
+  off = align_up(off + (int64_t)sh.n2 * P, A);
+  L.x1 = off;
+  off = align_up(off + (int64_t)sh.p1 * sh.LD, A);
+  L.ta = off;
+  off = align_up(off + (int64_t)sh.p1 * P, A);
+  L.sred = off;
+  off += (int64_t)sh.RG * P * sh.LD;
+  L.total = off;
+  return L;
+}
+
+template <typename T, int P, bool STAGE>
+__global__ void __launch_bounds__(max_threads<T>(), 1)
 fused_slab_kernel(SlabShape sh, const T* __restrict__ X1T, const T* __restrict__ X2T,
                   const T* __restrict__ Ta, const T* __restrict__ V, T* __restrict__ Sb,
-                  const int* __restrict__ skip) {
+                  const int* __restrict__ skip, int* __restrict__ err) {
   if (skip != nullptr && *skip) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n1 = sh.n1, n2 = sh.n2, p1 = sh.p1, p2 = sh.p2, LD = sh.LD;
-  T* X2s = reinterpret_cast<T*>(smem_raw);        // [n2][P]   X2s[i2][j2] = X_2(i2, j2)
-  T* X1s = X2s + n2 * P;                          // [p1][LD]  X1s[j1][i1] = X_1(i1, j1)
-  T* Tas = X1s + p1 * LD;                         // [p2 * p1] (rounded up to 4)
-  T* Tbs = Tas + ((p2 * p1 + 3) & ~3);            // [P][LD]
-  T* Sred = Tbs + P * LD;                         // [RG][P][LD]
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ uint64_t mbar[2];
+  __shared__ int timed_out;
+  const int n1 = sh.n1, n2 = sh.n2, n3 = sh.n3, p1 = sh.p1, p2 = sh.p2, LD = sh.LD;
+  const int nv = n2 * n1;
+  const SlabLayout L = slab_layout(sh, P, (int)sizeof(T), STAGE);
+  T* const base = reinterpret_cast<T*>(smem_raw);
+  T* Vbuf = base + L.vbuf;  // [2][n2 * n1]          (STAGE only)
+  T* X2s = base + L.x2;     // [n2][P]   X2s[i2][j2] = X_2(i2, j2)
+  T* X1s = base + L.x1;     // [p1][LD]  X1s[j1][i1] = X_1(i1, j1)
+  T* TaT = base + L.ta;     // [p1][P]   TaT[j1][j2] = T_a[i3](j2, j1)
+  T* Sred = base + L.sred;  // [RG][P][LD]
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int i3 = blockIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
 
-  for (int idx = tid; idx < n2 * P; idx += nth) {
-    const int i2 = idx / P, j2 = idx - i2 * P;
-    X2s[idx] = (j2 < p2) ? X2T[(int64_t)j2 * n2 + i2] : T(0);
+  for (int idx = tid; idx < p2 * n2; idx += nth) {    // coalesced read of X_2^T rows
+    const int j2 = idx / n2, i2 = idx - j2 * n2;
+    X2s[i2 * P + j2] = X2T[idx];
+  }
+  for (int idx = tid; idx < n2 * (P - p2); idx += nth) {
+    const int i2 = idx / (P - p2), j2 = p2 + idx - i2 * (P - p2);
+    X2s[i2 * P + j2] = T(0);
   }
   for (int idx = tid; idx < p1 * n1; idx += nth) {
     const int j1 = idx / n1, i1 = idx - j1 * n1;
     X1s[j1 * LD + i1] = X1T[idx];
   }
-  const T* ta = Ta + (int64_t)i3 * p2 * p1;
-  for (int idx = tid; idx < p2 * p1; idx += nth) Tas[idx] = ta[idx];
-  __syncthreads();
-
-  // phase 1: T_b = T_a[i3] . X_1^T  (mode-1 product of the slab)
-  for (int idx = tid; idx < P * n1; idx += nth) {
-    const int j2 = idx / n1, c = idx - j2 * n1;
-    T acc = T(0);
-    if (j2 < p2) {
-      for (int j1 = 0; j1 < p1; ++j1) acc = fma(Tas[j2 * p1 + j1], X1s[j1 * LD + c], acc);
+  if (tid == 0) {
+    timed_out = 0;
+    if (STAGE) {
+      mbar_init(&mbar[0], 1);
+      mbar_init(&mbar[1], 1);
+      fence_mbar_init();
     }
-    Tbs[j2 * LD + c] = acc;
   }
   __syncthreads();
+  if (STAGE && tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      const int s0 = blockIdx.x + b * gridDim.x;
+      if (s0 < n3) {
+        mbar_expect_tx(&mbar[b], sh.vbytes);
+        bulk_g2s(Vbuf + b * nv, V + (int64_t)s0 * nv, sh.vbytes, &mbar[b]);
+      }
+    }
+  }
 
-  // phase 2: eta = X_2 T_b, r = V (.) eta, S = X_2^T r  (fused mode-2 products)
-  const int warp = tid >> 5, lane = tid & 31, nwarps = nth >> 5;
-  const T* Vs = V + (int64_t)i3 * n2 * n1;
-  for (int task = warp; task < sh.CT * sh.RG; task += nwarps) {
-    const int ct = task % sh.CT, rg = task / sh.CT;
-    const int c = ct * 32 + lane;
-    const bool valid = c < n1;
-    const int r0 = (int)(((int64_t)n2 * rg) / sh.RG);
-    const int r1 = (int)(((int64_t)n2 * (rg + 1)) / sh.RG);
+  const int ct = warp % sh.CT, rg = warp / sh.CT;
+  const int c = ct * 32 + lane;
+  const bool valid = (c < n1) && (rg < sh.RG);
+  const int r0 = (int)(((int64_t)n2 * rg) / sh.RG);
+  const int r1 = (int)(((int64_t)n2 * (rg + 1)) / sh.RG);
+
+  int k = 0;
+  for (int slab = blockIdx.x; slab < n3; slab += gridDim.x, ++k) {
+    const int b = k & 1;
+    const T* ta = Ta + (int64_t)slab * p2 * p1;
+    for (int idx = tid; idx < p1 * P; idx += nth) {
+      const int j1 = idx / P, j2 = idx - j1 * P;
+      TaT[idx] = (j2 < p2) ? ta[j2 * p1 + j1] : T(0);
+    }
+    __syncthreads();  // (A) T_a slab in place; the previous slab is done with Sred
+
+    // T_b column of this lane: tb[j2] = sum_j1 T_a(j2, j1) X_1(c, j1)   (mode-1 product)
     T tb[P], s[P];
 #pragma unroll
     for (int j = 0; j < P; ++j) {
-      tb[j] = valid ? Tbs[j * LD + c] : T(0);
+      tb[j] = T(0);
       s[j] = T(0);
     }
-    const T* vcol = Vs + (valid ? c : 0);
-#pragma unroll 2
-    for (int i2 = r0; i2 < r1; ++i2) {
-      T x2[P];
-      load_row<T, P>(X2s + i2 * P, x2);
-      T e0 = T(0), e1 = T(0), e2 = T(0), e3 = T(0);
-#pragma unroll
-      for (int j = 0; j < P; j += 4) {
-        e0 = fma(x2[j + 0], tb[j + 0], e0);
-        e1 = fma(x2[j + 1], tb[j + 1], e1);
-        e2 = fma(x2[j + 2], tb[j + 2], e2);
-        e3 = fma(x2[j + 3], tb[j + 3], e3);
-      }
-      const T v = valid ? vcol[(int64_t)i2 * n1] : T(0);
-      const T r = v * ((e0 + e1) + (e2 + e3));
-#pragma unroll
-      for (int j = 0; j < P; ++j) s[j] = fma(x2[j], r, s[j]);
-    }
     if (valid) {
+      for (int j1 = 0; j1 < p1; ++j1) {
+        const T x1 = X1s[j1 * LD + c];
+        T trow[P];
+        load_row<T, P>(TaT + j1 * P, trow);
 #pragma unroll
-      for (int j = 0; j < P; ++j) Sred[(rg * P + j) * LD + c] = s[j];
+        for (int j = 0; j < P; ++j) tb[j] = fma(trow[j], x1, tb[j]);
+      }
     }
-  }
-  __syncthreads();
-  if (sh.RG > 1) {
-    for (int idx = tid; idx < p2 * n1; idx += nth) {
-      const int j2 = idx / n1, c = idx - j2 * n1;
-      T acc = Sred[j2 * LD + c];
-      for (int rg = 1; rg < sh.RG; ++rg) acc += Sred[(rg * P + j2) * LD + c];
-      Sred[j2 * LD + c] = acc;
-    }
-    __syncthreads();
-  }
 
-  // phase 3: S_b[i3] = S . X_1  (mode-1 product back to p1)
-  T* out = Sb + (int64_t)i3 * p2 * p1;
-  for (int o = tid; o < p2 * p1; o += nth) {
-    const int j2 = o / p1, j1 = o - j2 * p1;
-    const T* srow = Sred + j2 * LD;
-    const T* xrow = X1s + j1 * LD;
-    T a0 = T(0), a1 = T(0);
-    int c = 0;
-    for (; c + 1 < n1; c += 2) {
-      a0 = fma(srow[c], xrow[c], a0);
-      a1 = fma(srow[c + 1], xrow[c + 1], a1);
+    const T* Vs;
+    if (STAGE) {
+      bool ok = true;
+      if (valid || tid == 0) ok = mbar_wait_bounded(&mbar[b], (uint32_t)((k >> 1) & 1));
+      if (!ok) atomicOr(&timed_out, 1);
+      Vs = Vbuf + b * nv;
+      __syncthreads();
+      if (timed_out) break;
+    } else {
+      Vs = V + (int64_t)slab * nv;
     }
-    if (c < n1) a0 = fma(srow[c], xrow[c], a0);
-    out[o] = a0 + a1;
+
+    // eta = X_2 T_b, r = V (.) eta, S = X_2^T r over this warp's rows (fused mode-2 products)
+    if (valid) {
+      const T* vcol = Vs + c;
+#pragma unroll 2
+      for (int i2 = r0; i2 < r1; ++i2) {
+        T x2[P];
+        load_row<T, P>(X2s + i2 * P, x2);
+        T e0 = T(0), e1 = T(0), e2 = T(0), e3 = T(0);
+#pragma unroll
+        for (int j = 0; j < P; j += 4) {
+          e0 = fma(x2[j + 0], tb[j + 0], e0);
+          e1 = fma(x2[j + 1], tb[j + 1], e1);
+          e2 = fma(x2[j + 2], tb[j + 2], e2);
+          e3 = fma(x2[j + 3], tb[j + 3], e3);
+        }
+        const T r = vcol[(int64_t)i2 * n1] * ((e0 + e1) + (e2 + e3));
+#pragma unroll
+        for (int j = 0; j < P; ++j) s[j] = fma(x2[j], r, s[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < P; ++j)
+        if (j < p2) Sred[(rg * P + j) * LD + c] = s[j];
+    }
+    __syncthreads();  // (B) partial S complete; every thread is done with this V buffer
+    if (STAGE && tid == 0) {
+      const int nxt = slab + 2 * gridDim.x;
+      if (nxt < n3) {
+        fence_proxy_async();
+        mbar_expect_tx(&mbar[b], sh.vbytes);
+        bulk_g2s(Vbuf + b * nv, V + (int64_t)nxt * nv, sh.vbytes, &mbar[b]);
+      }
+    }
+    if (sh.RG > 1) {
+      for (int idx = tid; idx < p2 * n1; idx += nth) {
+        const int j2 = idx / n1, cc = idx - j2 * n1;
+        T acc = Sred[j2 * LD + cc];
+        for (int g = 1; g < sh.RG; ++g) acc += Sred[(g * P + j2) * LD + cc];
+        Sred[j2 * LD + cc] = acc;
+      }
+      __syncthreads();  // (C)
+    }
+
+    // S_b[slab](j2, j1) = sum_c S(j2, c) X_1(c, j1)   (mode-1 product back to p1)
+    T* out = Sb + (int64_t)slab * p2 * p1;
+    const int nw = nth >> 5;
+    for (int j2 = warp; j2 < p2; j2 += nw) {
+      const T* srow = Sred + j2 * LD;
+      for (int j1 = lane; j1 < p1; j1 += 32) {
+        const T* xrow = X1s + j1 * LD;
+        T a0 = T(0), a1 = T(0);
+        int cc = 0;
+        for (; cc + 1 < n1; cc += 2) {
+          a0 = fma(srow[cc], xrow[cc], a0);
+          a1 = fma(srow[cc + 1], xrow[cc + 1], a1);
+        }
+        if (cc < n1) a0 = fma(srow[cc], xrow[cc], a0);
+        out[j2 * p1 + j1] = a0 + a1;
+      }
+    }
+  }
+  if (STAGE && timed_out) {
+    if (tid == 0) {
+      atomicOr(err, 1);
+      // give copies still in flight a bounded chance to land before the CTA leaves
+      mbar_wait_bounded(&mbar[0], 0u);
+      mbar_wait_bounded(&mbar[1], 0u);
+    }
   }
 }
 
@@ -171,49 +326,96 @@ int pick_P(int p2) {
   return 0;
 }
 
-void slab_config(int n1, int n2, int p1, int p2, SlabShape& sh, int& threads) {
+size_t smem_bytes(const SlabShape& sh, int P, int elem, bool stage) {
+  return (size_t)slab_layout(sh, P, elem, stage).total * elem;
+}
+
+// Dynamic shared-memory budget of one CTA: the device's opt-in limit minus room for the
+// kernels' static shared variables (set by fused_prepare).
+size_t g_smem_budget = 227 * 1024 - 256;
+
+// Shape, block size and shared-memory plan; stage = false plans direct V loads.
+bool configure(int n1, int n2, int p1, int p2, int elem, bool stage, SlabShape& sh, int& threads,
+               size_t& smem) {
+  const int P = pick_P(p2);
+  if (P == 0 || n1 <= 0 || n2 <= 0 || p1 <= 0 || n1 > 256 || p1 > 64) return false;
+  if (elem == 8 && P > 24) return false;  // FP64 register arrays beyond this spill
   sh.n1 = n1;
   sh.n2 = n2;
+  sh.n3 = 0;
   sh.p1 = p1;
   sh.p2 = p2;
   sh.CT = (n1 + 31) / 32;
-  sh.RG = sh.CT >= 8 ? 1 : 8 / sh.CT;
-  if (sh.RG > n2) sh.RG = n2 > 0 ? n2 : 1;
   sh.LD = n1 + 1;
+  const int max_warps = (elem == 8 ? 256 : 512) / 32;
+  if (sh.CT > max_warps) return false;
+  sh.RG = max_warps / sh.CT;
+  if (sh.RG < 1) sh.RG = 1;
+  if (sh.RG > n2) sh.RG = n2;
+  sh.vbytes = (uint32_t)((size_t)n1 * n2 * elem);
+  while (true) {
+    smem = smem_bytes(sh, P, elem, stage);
+    if (smem <= g_smem_budget) break;
+    if (sh.RG > 1) {
+      sh.RG = sh.RG / 2;
+      continue;
+    }
+    return false;
+  }
   threads = 32 * sh.CT * sh.RG;
+  return threads <= (elem == 8 ? 256 : 512);
 }
 
-size_t slab_smem(const SlabShape& sh, int P, int elem) {
-  size_t e = (size_t)sh.n2 * P + (size_t)sh.p1 * sh.LD + (((size_t)sh.p2 * sh.p1 + 3) & ~(size_t)3) +
-             (size_t)P * sh.LD * (1 + sh.RG);
-  return e * elem;
-}
-
-template <typename T, int P>
-cudaError_t launch_P(const SlabShape& sh, int threads, size_t smem, int n3, const T* X1T,
-                     const T* X2T, const T* Ta, const T* V, T* Sb, cudaStream_t s,
-                     const int* skip) {
-  fused_slab_kernel<T, P><<<n3, threads, smem, s>>>(sh, X1T, X2T, Ta, V, Sb, skip);
+template <typename T, int P, bool STAGE>
+cudaError_t launch_P(const SlabShape& sh, int grid, int threads, size_t smem, const T* X1T,
+                     const T* X2T, const T* Ta, const T* V, T* Sb, cudaStream_t s, const int* skip,
+                     int* err) {
+  fused_slab_kernel<T, P, STAGE><<<grid, threads, smem, s>>>(sh, X1T, X2T, Ta, V, Sb, skip, err);
+  count_launches(1);
   return cudaGetLastError();
 }
 
-template <typename T, int P>
-cudaError_t prepare_P() {
-  return cudaFuncSetAttribute(fused_slab_kernel<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              227 * 1024);
+template <typename T, bool STAGE>
+cudaError_t launch_S(int P, const SlabShape& sh, int grid, int threads, size_t smem, const T* X1T,
+                     const T* X2T, const T* Ta, const T* V, T* Sb, cudaStream_t s, const int* skip,
+                     int* err) {
+  switch (P) {
+    case 8: return launch_P<T, 8, STAGE>(sh, grid, threads, smem, X1T, X2T, Ta, V, Sb, s, skip, err);
+    case 12: return launch_P<T, 12, STAGE>(sh, grid, threads, smem, X1T, X2T, Ta, V, Sb, s, skip, err);
+    case 16: return launch_P<T, 16, STAGE>(sh, grid, threads, smem, X1T, X2T, Ta, V, Sb, s, skip, err);
+    case 20: return launch_P<T, 20, STAGE>(sh, grid, threads, smem, X1T, X2T, Ta, V, Sb, s, skip, err);
+    case 24: return launch_P<T, 24, STAGE>(sh, grid, threads, smem, X1T, X2T, Ta, V, Sb, s, skip, err);
+    case 28: return launch_P<T, 28, STAGE>(sh, grid, threads, smem, X1T, X2T, Ta, V, Sb, s, skip, err);
+    case 32: return launch_P<T, 32, STAGE>(sh, grid, threads, smem, X1T, X2T, Ta, V, Sb, s, skip, err);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
-template <typename T>
-cudaError_t prepare_T() {
-  cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = prepare_P<T, 8>();
-  if (e == cudaSuccess) e = prepare_P<T, 12>();
-  if (e == cudaSuccess) e = prepare_P<T, 16>();
-  if (e == cudaSuccess) e = prepare_P<T, 20>();
-  if (e == cudaSuccess) e = prepare_P<T, 24>();
-  if (e == cudaSuccess) e = prepare_P<T, 28>();
-  if (e == cudaSuccess) e = prepare_P<T, 32>();
+template <typename T, int P, bool STAGE>
+cudaError_t prepare_P() {
+  return cudaFuncSetAttribute(fused_slab_kernel<T, P, STAGE>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g_smem_budget);
+}
+
+template <typename T, bool STAGE>
+cudaError_t prepare_TS() {
+  cudaError_t e = prepare_P<T, 8, STAGE>();
+  if (e == cudaSuccess) e = prepare_P<T, 12, STAGE>();
+  if (e == cudaSuccess) e = prepare_P<T, 16, STAGE>();
+  if (e == cudaSuccess) e = prepare_P<T, 20, STAGE>();
+  if (e == cudaSuccess) e = prepare_P<T, 24, STAGE>();
+  if (e == cudaSuccess) e = prepare_P<T, 28, STAGE>();
+  if (e == cudaSuccess) e = prepare_P<T, 32, STAGE>();
   return e;
+}
+
+// Staging needs a 16-byte aligned slab start and a slab size that is a multiple of 16 bytes
+// (the rules of cp.async.bulk), and is used for FP32 only: the FP64 path is bound by FP64 ALU
+// throughput, not by the V stream.
+bool can_stage(int n1, int n2, int elem, const void* V) {
+  const size_t bytes = (size_t)n1 * n2 * elem;
+  return elem == 4 && bytes % 16 == 0 && bytes < (1u << 20) &&
+         (reinterpret_cast<uintptr_t>(V) % 16) == 0;
 }
 
 }  // namespace
@@ -221,51 +423,51 @@ cudaError_t prepare_T() {
 // Raise the dynamic shared-memory limit of every fused-slab instantiation on the current
 // device (called once per plan, outside any stream capture).
 cudaError_t fused_prepare() {
-  cudaError_t e = prepare_T<float>();
-  if (e == cudaSuccess) e = prepare_T<double>();
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  g_smem_budget = optin > 1024 ? (size_t)optin - 1024 : 0;  // 1 KB kept for static variables
+  e = prepare_TS<float, true>();
+  if (e == cudaSuccess) e = prepare_TS<float, false>();
+  if (e == cudaSuccess) e = prepare_TS<double, false>();
   return e;
 }
 
 int fused_slab_supported(int n1, int n2, int p1, int p2, int elem_bytes) {
-  if (n1 <= 0 || n2 <= 0 || p1 <= 0 || p2 <= 0) return 0;
-  if (n1 > 256) return 0;
-  const int P = pick_P(p2);
-  if (P == 0) return 0;
   SlabShape sh;
   int threads;
-  slab_config(n1, n2, p1, p2, sh, threads);
-  if (threads > 256) return 0;
-  return slab_smem(sh, P, elem_bytes) <= 227 * 1024 ? 1 : 0;
+  size_t smem;
+  return configure(n1, n2, p1, p2, elem_bytes, false, sh, threads, smem) ? 1 : 0;
 }
 
 template <typename T>
 cudaError_t launch_fused_slab(int n1, int n2, int n3, int p1, int p2, const T* X1T, const T* X2T,
-                              const T* Ta, const T* V, T* Sb, cudaStream_t s, const int* skip) {
-  if (!fused_slab_supported(n1, n2, p1, p2, (int)sizeof(T))) return cudaErrorInvalidValue;
+                              const T* Ta, const T* V, T* Sb, cudaStream_t s, const int* skip,
+                              int* err) {
   if (n3 <= 0) return cudaSuccess;
   SlabShape sh;
   int threads;
-  slab_config(n1, n2, p1, p2, sh, threads);
+  size_t smem;
+  bool stage = sizeof(T) == 4 && can_stage(n1, n2, (int)sizeof(T), V);
+  if (stage && !configure(n1, n2, p1, p2, (int)sizeof(T), true, sh, threads, smem)) stage = false;
+  if (!stage && !configure(n1, n2, p1, p2, (int)sizeof(T), false, sh, threads, smem))
+    return cudaErrorInvalidValue;
   sh.n3 = n3;
+  int grid = stage ? num_sms() : 2 * num_sms();
+  if (grid > n3) grid = n3;
   const int P = pick_P(p2);
-  const size_t smem = slab_smem(sh, P, (int)sizeof(T));
-  switch (P) {
-    case 8: return launch_P<T, 8>(sh, threads, smem, n3, X1T, X2T, Ta, V, Sb, s, skip);
-    case 12: return launch_P<T, 12>(sh, threads, smem, n3, X1T, X2T, Ta, V, Sb, s, skip);
-    case 16: return launch_P<T, 16>(sh, threads, smem, n3, X1T, X2T, Ta, V, Sb, s, skip);
-    case 20: return launch_P<T, 20>(sh, threads, smem, n3, X1T, X2T, Ta, V, Sb, s, skip);
-    case 24: return launch_P<T, 24>(sh, threads, smem, n3, X1T, X2T, Ta, V, Sb, s, skip);
-    case 28: return launch_P<T, 28>(sh, threads, smem, n3, X1T, X2T, Ta, V, Sb, s, skip);
-    case 32: return launch_P<T, 32>(sh, threads, smem, n3, X1T, X2T, Ta, V, Sb, s, skip);
-    default: return cudaErrorInvalidValue;
+  if constexpr (sizeof(T) == 4) {
+    if (stage) return launch_S<T, true>(P, sh, grid, threads, smem, X1T, X2T, Ta, V, Sb, s, skip, err);
   }
+  return launch_S<T, false>(P, sh, grid, threads, smem, X1T, X2T, Ta, V, Sb, s, skip, err);
 }
 
 template cudaError_t launch_fused_slab<float>(int, int, int, int, int, const float*, const float*,
                                               const float*, const float*, float*, cudaStream_t,
-                                              const int*);
+                                              const int*, int*);
 template cudaError_t launch_fused_slab<double>(int, int, int, int, int, const double*,
                                                const double*, const double*, const double*,
-                                               double*, cudaStream_t, const int*);
+                                               double*, cudaStream_t, const int*, int*);
 
 }  // namespace glam

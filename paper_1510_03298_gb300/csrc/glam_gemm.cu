@@ -19,16 +19,18 @@
 namespace glam {
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16;
+constexpr int BK = 16;
 
 // TB is the storage type of the B operand.  With EXTRAP the operand is formed on load as
 // B + omega (B - Bp) - Bs (Bp, Bs optional), in double when TB is double, then rounded to T:
 // the FISTA extrapolation y = x + omega (x - x_prev) of Sec. 3.2, minus the anchor theta_k.
-template <typename T, typename TB, bool EXTRAP>
+// Tiles of (16 TM) x (16 TN) outputs; 256 threads with TM x TN outputs each.
+template <typename T, typename TB, bool EXTRAP, int TM, int TN>
 __global__ void __launch_bounds__(256)
 gemm_kernel(GemmDesc d, const T* __restrict__ A, const TB* __restrict__ B, T* __restrict__ C,
             const TB* __restrict__ Bp, const TB* __restrict__ Bs, const InnerCtl* __restrict__ ctl,
             double omega_h, const int* __restrict__ skip) {
+  constexpr int BM = 16 * TM, BN = 16 * TN;
   if (skip != nullptr && *skip) return;
   __shared__ T As[BK][BM + 4];
   __shared__ T Bsm[BK][BN + 4];
@@ -51,37 +53,41 @@ gemm_kernel(GemmDesc d, const T* __restrict__ A, const TB* __restrict__ B, T* __
     const int l = ctl->l;  // omega_l = (l - 1) / (l + 2), Sec. 3.2
     omega = TB(l - 1) / TB(l + 2);
   }
-  T acc[4][4];
+  T acc[TM][TN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
 
   const bool a_m_unit = (d.sAm == 1);
   const bool b_n_unit = (d.sBn == 1);
   for (int k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < (BM * BK) / 256; ++r) {
       const int idx = tid + r * 256;
       int mm, ka;
       if (a_m_unit) {
-        mm = idx & 63;
-        ka = idx >> 6;
+        mm = idx % BM;
+        ka = idx / BM;
       } else {
-        ka = idx & 15;
-        mm = idx >> 4;
+        ka = idx % BK;
+        mm = idx / BK;
       }
       const int gm = m0 + mm, gk = k0 + ka;
       T v = T(0);
       if (gm < d.M && gk < kend) v = A[(int64_t)gm * d.sAm + (int64_t)gk * d.sAk];
       As[ka][mm] = v;
+    }
+#pragma unroll
+    for (int r = 0; r < (BN * BK) / 256; ++r) {
+      const int idx = tid + r * 256;
       int nn, kb;
       if (b_n_unit) {
-        nn = idx & 63;
-        kb = idx >> 6;
+        nn = idx % BN;
+        kb = idx / BN;
       } else {
-        kb = idx & 15;
-        nn = idx >> 4;
+        kb = idx % BK;
+        nn = idx / BK;
       }
       const int gn = n0 + nn, gkb = k0 + kb;
       T w = T(0);
@@ -99,28 +105,64 @@ gemm_kernel(GemmDesc d, const T* __restrict__ A, const TB* __restrict__ B, T* __
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      T a[4], b[4];
+      T a[TM], b[TN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bsm[kk][tx + 16 * j];
+      for (int j = 0; j < TN; ++j) b[j] = Bsm[kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < TM; ++i) {
     const int gm = m0 + ty + 16 * i;
     if (gm >= d.M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < TN; ++j) {
       const int gn = n0 + tx + 16 * j;
       if (gn < d.N) C[(int64_t)gm * d.sCm + (int64_t)gn * d.sCn] = acc[i][j];
     }
   }
+}
+
+template <typename T, typename TB, bool EXTRAP>
+cudaError_t launch_tiles(const GemmDesc& d, int tm, int tn, const T* A, const TB* B, T* C,
+                         cudaStream_t s, const TB* Bp, const TB* Bs, const InnerCtl* ctl,
+                         double omega, const int* skip) {
+  dim3 grid((d.N + 16 * tn - 1) / (16 * tn), (d.M + 16 * tm - 1) / (16 * tm), d.batch * d.ksplit);
+  if (grid.y > 65535) return cudaErrorInvalidValue;
+  if (tm == 4 && tn == 4)
+    gemm_kernel<T, TB, EXTRAP, 4, 4><<<grid, 256, 0, s>>>(d, A, B, C, Bp, Bs, ctl, omega, skip);
+  else if (tm == 2 && tn == 4)
+    gemm_kernel<T, TB, EXTRAP, 2, 4><<<grid, 256, 0, s>>>(d, A, B, C, Bp, Bs, ctl, omega, skip);
+  else if (tm == 4 && tn == 2)
+    gemm_kernel<T, TB, EXTRAP, 4, 2><<<grid, 256, 0, s>>>(d, A, B, C, Bp, Bs, ctl, omega, skip);
+  else
+    gemm_kernel<T, TB, EXTRAP, 2, 2><<<grid, 256, 0, s>>>(d, A, B, C, Bp, Bs, ctl, omega, skip);
+  return cudaSuccess;
+}
+
+int64_t ctas(const GemmDesc& d, int tm, int tn) {
+  return (int64_t)((d.N + 16 * tn - 1) / (16 * tn)) * ((d.M + 16 * tm - 1) / (16 * tm)) * d.batch * d.ksplit;
+}
+
+// Largest tile whose grid still fills the GPU (about 1.5 CTAs per SM), else the smallest.
+void pick_tile(const GemmDesc& d, int& tm, int& tn) {
+  const int64_t want = (3 * num_sms()) / 2;
+  const int cand[4][2] = {{4, 4}, {2, 4}, {4, 2}, {2, 2}};
+  for (auto& c : cand) {
+    if (ctas(d, c[0], c[1]) >= want) {
+      tm = c[0];
+      tn = c[1];
+      return;
+    }
+  }
+  tm = 2;
+  tn = 2;
 }
 
 }  // namespace
@@ -131,12 +173,15 @@ cudaError_t launch_gemm(const GemmDesc& d, const T* A, const TB* B, T* C, cudaSt
                         const int* skip) {
   if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return cudaSuccess;
   if (d.K <= 0 || d.ksplit < 1 || (int64_t)d.batch * d.ksplit > 65535) return cudaErrorInvalidValue;
-  dim3 grid((d.N + BN - 1) / BN, (d.M + BM - 1) / BM, d.batch * d.ksplit);
-  if (grid.y > 65535) return cudaErrorInvalidValue;
+  int tm = 4, tn = 4;
+  pick_tile(d, tm, tn);
+  cudaError_t e;
   if (Bprev != nullptr || Bsub != nullptr || ctl != nullptr || !std::is_same<T, TB>::value)
-    gemm_kernel<T, TB, true><<<grid, 256, 0, s>>>(d, A, B, C, Bprev, Bsub, ctl, omega, skip);
+    e = launch_tiles<T, TB, true>(d, tm, tn, A, B, C, s, Bprev, Bsub, ctl, omega, skip);
   else
-    gemm_kernel<T, TB, false><<<grid, 256, 0, s>>>(d, A, B, C, nullptr, nullptr, nullptr, 0.0, skip);
+    e = launch_tiles<T, TB, false>(d, tm, tn, A, B, C, s, nullptr, nullptr, nullptr, 0.0, skip);
+  if (e != cudaSuccess) return e;
+  count_launches(1);
   return cudaGetLastError();
 }
 

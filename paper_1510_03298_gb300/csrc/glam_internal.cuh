@@ -56,7 +56,7 @@ struct DevScalars {
   int accepted;                // index j of the accepted trial, -1 if none in this pass
   int nnz;
   int nonfinite;               // set by kernels that meet a non-finite value
-  int pad;
+  int timeout;                 // set by a kernel whose bounded wait ran out
 };
 
 struct RedScratch {
@@ -89,8 +89,8 @@ cudaError_t launch_gemm(const GemmDesc& d, const T* A, const TB* B, T* C, cudaSt
 // ------------------------------------------------------------------------------------
 template <typename T>
 cudaError_t launch_fused_slab(int n1, int n2, int n3, int p1, int p2, const T* X1T, const T* X2T,
-                              const T* Ta, const T* V, T* Sb, cudaStream_t s,
-                              const int* skip = nullptr);
+                              const T* Ta, const T* V, T* Sb, cudaStream_t s, const int* skip,
+                              int* err);
 int fused_slab_supported(int n1, int n2, int p1, int p2, int elem_bytes);
 cudaError_t fused_prepare();
 
@@ -108,7 +108,8 @@ template <typename Tq, typename TP>
 cudaError_t launch_prox(int64_t p, int ksplit, const Tq* Qpart, const TP* lin, double lin_scale,
                         const TP* x, const TP* xprev, const TP* pen_w, TP* out, double inv_n,
                         InnerCtl* ctl, double omega, double delta, double lambda,
-                        const double* Lhat, cudaStream_t s);
+                        const double* Lhat, cudaStream_t s, Tq* dnext = nullptr,
+                        const TP* anchor = nullptr);
 
 template <typename TE, typename T>
 cudaError_t launch_armijo_stream(int family, int64_t n, const TE* eta, const T* deta, const TE* Y,
@@ -145,6 +146,9 @@ cudaError_t launch_convert(int64_t n, const TI* in, TO* out, cudaStream_t s);
 cudaError_t launch_gram(int nj, int pj, const double* XT, double* gram, cudaStream_t s);
 
 template <typename T>
+cudaError_t launch_sum_splits(int64_t p, int ksplit, const T* part, T* out, cudaStream_t s);
+
+template <typename T>
 cudaError_t launch_vmul(int64_t n, const T* V, T* x, const int* skip, cudaStream_t s);
 
 template <typename T>
@@ -155,5 +159,10 @@ cudaError_t launch_loss_only(int family, int64_t n, const T* eta, const T* Y, co
                              double* out, RedScratch red, cudaStream_t s);
 
 int num_sms();
+
+// Process-wide count of kernels launched by the library (graph replays add their kernel nodes).
+void count_launches(int64_t k);
+int64_t launch_count();
+void set_capturing(bool on);
 
 }  // namespace glam

@@ -37,6 +37,9 @@ def _active_sets_agree(d, th_gpu, th_ref, lam, lmax, r_tot):
         Hs = Phi[:, ia].T @ (w[:, None] * Phi[:, ia]) / d.n
         mu = max(np.linalg.eigvalsh(Hs).min(), 1e-300)
         bound = 10.0 * r_tot * lmax / mu
+    # values at rounding level are not active in any meaningful sense (at lambda = lambda_max the
+    # soft threshold of |z| equal to the threshold up to one rounding can leave ~1e-20)
+    bound = max(bound, 1e-12 * max(1.0, float(np.abs(th_ref).max())))
     degenerate = (~act & (np.abs(np.abs(g) - thr) <= 10.0 * r_tot * lmax)) | (act & (np.abs(th_ref) <= bound))
     ok = ~degenerate
     return np.array_equal((th_gpu != 0)[ok], (th_ref != 0)[ok]), int(degenerate.sum())
