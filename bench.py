@@ -362,6 +362,28 @@ def measure_e2e(g, torch, pr, plan, opts, dev, steps):
     return {"value": iters / t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
 
+def run_kernels(reps):
+    """Diagnostic mode for profilers: build the 128x128x600 plan and launch the four kernels of
+    one inner iteration 2 + reps times each (glam_time_inner_kernels); prints their mean times.
+    It produces no bench line."""
+    import torch
+    import gen
+    import paper_1510_03298_gb300 as g
+    from paper_1510_03298_gb300 import build as gb
+    if not os.path.exists(g.library_path()):
+        gb.build()
+    pr = gen.make_workload(1)
+    f32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+    plan = g.Plan(pr.n, pr.p, pr.family, g.GLAM_FP32)
+    X = [f32(x) for x in pr.XT]
+    theta = f32(0.01 * np.random.default_rng(0).standard_normal((pr.p[2], pr.p[1], pr.p[0])))
+    q = g.glam_quad_build(plan, X, theta, f32(pr.Y), f32(pr.W))
+    ms = g.glam_time_inner_kernels(plan, X, q, reps=reps)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernels_ms": dict(zip(["mode3", "fused_slab", "mode3_adj_split", "prox"], ms))}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -369,7 +391,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
+    ap.add_argument("--kernels", type=int, default=0, metavar="REPS",
+                    help="diagnostic: launch the inner-iteration kernels REPS times for a profiler")
     args = ap.parse_args()
+    if args.kernels > 0:
+        return run_kernels(args.kernels)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
