@@ -189,6 +189,27 @@ int glam_fit_path(glam_plan* plan, const void* const X[3], const void* Y, const 
                   const void* pen_w, int nlambda, double* lambda, const glam_opts* opts,
                   const double* Theta0, double* Theta_path, glam_stats* stats, int* nfit);
 
+/* ---- allocation-free entry point (the paper has no counterpart) ----
+ *
+ * f(eta) = (1/n) sum_i a_i l_i(eta_i, y_i), the loss of glam_loss (constants as stated at the
+ * top of this header) computed from a caller-supplied linear predictor eta instead of Theta,
+ * for callers that cannot allocate device memory where they need it: code running while a
+ * stream is captured into a CUDA graph, hosts that hand out every byte of device memory from
+ * their own pool, real-time paths where an allocation could block.  It calls no cudaMalloc,
+ * cudaFree or allocating library routine and needs no plan: its reduction scratch (1024 FP64
+ * block partials and a completion counter, 8448 bytes) is a fixed __device__ array inside
+ * libglam, which every GPU that loads the library holds until the process exits.
+ *   family: GLAM_GAUSSIAN_IDENTITY or GLAM_POISSON_LOG; precision: GLAM_FP64 (double arrays)
+ *   or GLAM_FP32 (float arrays); n: cells, 1 <= n <= 2^40 (larger n returns GLAM_EINVAL);
+ *   eta, Y, W: n elements (DEVICE); out: one DEVICE double (written); stream: cudaStream_t.
+ * Asynchronous on `stream`; FP64 accumulation with a fixed summation order (same bits on every
+ * call).  The first call on a device looks up the scratch address (cudaGetSymbolAddress), so
+ * make that first call before any stream capture.  All calls share the one scratch array:
+ * calls whose kernels overlap on the GPU race on it and must be serialized (one stream).
+ * Errors: GLAM_EINVAL (message from glam_last_error(NULL)), GLAM_ECUDA. */
+int glam_loss_eta_noalloc(int family, int precision, int64_t n, const void* eta, const void* Y,
+                          const void* W, double* out, void* stream);
+
 /* ---- diagnostics (tracing hooks of this library; the paper has no counterpart) ---- */
 
 /* Number of kernels this process has launched through libglam so far (each replay of a captured

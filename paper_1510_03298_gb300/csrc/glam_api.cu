@@ -292,6 +292,10 @@ int check_plan(glam_plan* pl) {
 
 }  // namespace
 
+namespace glam {
+int thread_fail(int code, const std::string& msg) { return fail(nullptr, code, msg); }
+}  // namespace glam
+
 // ======================================================================== ABI
 // (every entry point is declared extern "C" in glam.h, so these definitions have C linkage)
 

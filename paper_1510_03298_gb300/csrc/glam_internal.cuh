@@ -160,6 +160,9 @@ cudaError_t launch_loss_only(int family, int64_t n, const T* eta, const T* Y, co
 
 int num_sms();
 
+// Record msg as the calling thread's last error (read by glam_last_error(NULL)); returns code.
+int thread_fail(int code, const std::string& msg);
+
 // Process-wide count of kernels launched by the library (graph replays add their kernel nodes).
 void count_launches(int64_t k);
 int64_t launch_count();
