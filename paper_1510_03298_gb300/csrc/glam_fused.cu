@@ -125,10 +125,15 @@ struct SlabShape {
   uint32_t vbytes;  // n2 * n1 * sizeof(T) (bulk copy size)
 };
 
+// Row pitch (elements) of the row-per-column arrays S[c][*] and X_1[c][*]: 16-byte rows whose
+// pitch keeps the 8 lanes of one 128-bit shared-memory wavefront on distinct banks.
+__host__ __device__ constexpr int row_pitch(int w) { return (w % 8 == 0) ? w + 4 : w; }
+
 // Shared-memory layout of one CTA, in elements.  Every section starts on a 32-byte boundary
-// (the 16-byte vector reads of X_2 and T_a rows and the bulk-copy destinations need 16).
+// (16-byte vector reads of X_2, T_a, S and X_1 rows and the bulk-copy destinations need 16).
 struct SlabLayout {
-  int64_t vbuf, x2, x1, ta, sred, total;
+  int64_t vbuf, x2, x1, x1c, ta, tb, sred, total;
+  int sp, q1, q1p;  // S row pitch, p1 rounded up to 4, X_1 row pitch
 };
 
 __host__ __device__ inline int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
@@ -136,19 +141,50 @@ __host__ __device__ inline int64_t align_up(int64_t v, int64_t a) { return (v + 
 __host__ __device__ inline SlabLayout slab_layout(const SlabShape& sh, int P, int elem, bool stage) {
   const int64_t A = 32 / elem;
   SlabLayout L;
+  L.sp = row_pitch(P);
+  L.q1 = (sh.p1 + 3) / 4 * 4;
+  L.q1p = row_pitch(L.q1);
   int64_t off = 0;
   L.vbuf = off;
   off = align_up(off + (stage ? 2 * (int64_t)sh.n2 * sh.n1 : 0), A);
-  L.x2 = off;
+  L.x2 = off;                                   // [n2][P]
   off = align_up(off + (int64_t)sh.n2 * P, A);
-  L.x1 = off;
+  L.x1 = off;                                   // [p1][LD]
   off = align_up(off + (int64_t)sh.p1 * sh.LD, A);
-  L.ta = off;
+  L.x1c = off;                                  // [n1][q1p]
+  off = align_up(off + (int64_t)sh.n1 * L.q1p, A);
+  L.ta = off;                                   // [p1][P]
   off = align_up(off + (int64_t)sh.p1 * P, A);
-  L.sred = off;
-  off += (int64_t)sh.RG * P * sh.LD;
+  L.tb = off;                                   // [P][LD]
+  off = align_up(off + (int64_t)P * sh.LD, A);
+  L.sred = off;                                 // [RG][n1][sp]
+  off += (int64_t)sh.RG * sh.n1 * L.sp;
   L.total = off;
   return L;
+}
+
+template <typename T>
+__device__ __forceinline__ void load4(const T* src, T (&d)[4]) {
+  using V = typename Vec16<T>::type;
+  if constexpr (Vec16<T>::width == 4) {
+    const V v = *reinterpret_cast<const V*>(src);
+    d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+  } else {
+    const V a = reinterpret_cast<const V*>(src)[0];
+    const V b = reinterpret_cast<const V*>(src)[1];
+    d[0] = a.x; d[1] = a.y; d[2] = b.x; d[3] = b.y;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void store4(T* dst, T a, T b, T c, T d) {
+  using V = typename Vec16<T>::type;
+  if constexpr (Vec16<T>::width == 4) {
+    *reinterpret_cast<V*>(dst) = V{a, b, c, d};
+  } else {
+    reinterpret_cast<V*>(dst)[0] = V{a, b};
+    reinterpret_cast<V*>(dst)[1] = V{c, d};
+  }
 }
 
 template <typename T, int P, bool STAGE>
@@ -160,19 +196,22 @@ fused_slab_kernel(SlabShape sh, const T* __restrict__ X1T, const T* __restrict__
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ uint64_t mbar[2];
   __shared__ int timed_out;
-  const int n1 = sh.n1, n2 = sh.n2, n3 = sh.n3, p1 = sh.p1, p2 = sh.p2, LD = sh.LD;
+  const int n1 = sh.n1, n2 = sh.n2, n3 = sh.n3, p1 = sh.p1, p2 = sh.p2, LD = sh.LD, RG = sh.RG;
   const int nv = n2 * n1;
   const SlabLayout L = slab_layout(sh, P, (int)sizeof(T), STAGE);
+  const int SP = L.sp, Q1 = L.q1, Q1P = L.q1p;
   T* const base = reinterpret_cast<T*>(smem_raw);
-  T* Vbuf = base + L.vbuf;  // [2][n2 * n1]          (STAGE only)
-  T* X2s = base + L.x2;     // [n2][P]   X2s[i2][j2] = X_2(i2, j2)
-  T* X1s = base + L.x1;     // [p1][LD]  X1s[j1][i1] = X_1(i1, j1)
-  T* TaT = base + L.ta;     // [p1][P]   TaT[j1][j2] = T_a[i3](j2, j1)
-  T* Sred = base + L.sred;  // [RG][P][LD]
+  T* Vbuf = base + L.vbuf;  // [2][n2 * n1]   (STAGE only)
+  T* X2s = base + L.x2;     // [n2][P]    X2s[i2][j2] = X_2(i2, j2)
+  T* X1s = base + L.x1;     // [p1][LD]   X1s[j1][i1] = X_1(i1, j1)
+  T* X1c = base + L.x1c;    // [n1][Q1P]  X1c[i1][j1] = X_1(i1, j1)
+  T* TaT = base + L.ta;     // [p1][P]    TaT[j1][j2] = T_a[i3](j2, j1)
+  T* Tbs = base + L.tb;     // [P][LD]    Tbs[j2][i1] = T_b(j2, i1)
+  T* Sred = base + L.sred;  // [RG][n1][SP] Sred[g][i1][j2] = partial S(j2, i1) of row group g
   const int tid = threadIdx.x, nth = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31;
 
-  for (int idx = tid; idx < p2 * n2; idx += nth) {    // coalesced read of X_2^T rows
+  for (int idx = tid; idx < p2 * n2; idx += nth) {  // coalesced read of X_2^T rows
     const int j2 = idx / n2, i2 = idx - j2 * n2;
     X2s[i2 * P + j2] = X2T[idx];
   }
@@ -182,7 +221,21 @@ fused_slab_kernel(SlabShape sh, const T* __restrict__ X1T, const T* __restrict__
   }
   for (int idx = tid; idx < p1 * n1; idx += nth) {
     const int j1 = idx / n1, i1 = idx - j1 * n1;
-    X1s[j1 * LD + i1] = X1T[idx];
+    const T x = X1T[idx];
+    X1s[j1 * LD + i1] = x;
+    X1c[i1 * Q1P + j1] = x;
+  }
+  for (int idx = tid; idx < n1 * (Q1 - p1); idx += nth) {
+    const int i1 = idx / (Q1 - p1), j1 = p1 + idx - i1 * (Q1 - p1);
+    X1c[i1 * Q1P + j1] = T(0);
+  }
+  // T_a of the first slab
+  if ((int)blockIdx.x < n3) {
+    const T* ta = Ta + (int64_t)blockIdx.x * p2 * p1;
+    for (int idx = tid; idx < p1 * P; idx += nth) {
+      const int j1 = idx / P, j2 = idx - j1 * P;
+      TaT[idx] = (j2 < p2) ? ta[j2 * p1 + j1] : T(0);
+    }
   }
   if (tid == 0) {
     timed_out = 0;
@@ -203,53 +256,78 @@ fused_slab_kernel(SlabShape sh, const T* __restrict__ X1T, const T* __restrict__
     }
   }
 
+  // warp roles in phase 2: column tile ct (32 columns i1), row group rg (rows i2 in [r0, r1))
   const int ct = warp % sh.CT, rg = warp / sh.CT;
   const int c = ct * 32 + lane;
-  const bool valid = (c < n1) && (rg < sh.RG);
-  const int r0 = (int)(((int64_t)n2 * rg) / sh.RG);
-  const int r1 = (int)(((int64_t)n2 * (rg + 1)) / sh.RG);
+  const bool valid = (c < n1) && (rg < RG);
+  const int r0 = (int)(((int64_t)n2 * rg) / RG);
+  const int r1 = (int)(((int64_t)n2 * (rg + 1)) / RG);
+  // phase-3 roles: 4 x 4 output blocks (jb2, jb1), 16 lanes split the columns c
+  const int NB1 = Q1 / 4, NB = (P / 4) * NB1;
+  const int q = lane & 15;
+  // T_a elements this thread prefetches for the next slab
+  constexpr int kTaPer = (32 * P + 255) / 256;  // >= ceil(p1 * P / blockDim) for p1 <= 64, 256+ threads
 
   int k = 0;
   for (int slab = blockIdx.x; slab < n3; slab += gridDim.x, ++k) {
     const int b = k & 1;
-    const T* ta = Ta + (int64_t)slab * p2 * p1;
-    for (int idx = tid; idx < p1 * P; idx += nth) {
-      const int j1 = idx / P, j2 = idx - j1 * P;
-      TaT[idx] = (j2 < p2) ? ta[j2 * p1 + j1] : T(0);
-    }
-    __syncthreads();  // (A) T_a slab in place; the previous slab is done with Sred
-
-    // T_b column of this lane: tb[j2] = sum_j1 T_a(j2, j1) X_1(c, j1)   (mode-1 product)
-    T tb[P], s[P];
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-      tb[j] = T(0);
-      s[j] = T(0);
-    }
-    if (valid) {
-      for (int j1 = 0; j1 < p1; ++j1) {
-        const T x1 = X1s[j1 * LD + c];
-        T trow[P];
-        load_row<T, P>(TaT + j1 * P, trow);
-#pragma unroll
-        for (int j = 0; j < P; ++j) tb[j] = fma(trow[j], x1, tb[j]);
+    // ---- phase 1: T_b(j2, c) = sum_j1 T_a(j2, j1) X_1(c, j1); task = (column tile, 4 rows j2) ----
+    {
+      const int ntask = sh.CT * (P / 4);
+      for (int task = warp; task < ntask; task += (nth >> 5)) {
+        const int ct1 = task % sh.CT, jb = task / sh.CT;
+        const int c1 = ct1 * 32 + lane;
+        if (c1 < n1) {
+          T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+          for (int j1 = 0; j1 < p1; ++j1) {
+            const T x1 = X1s[j1 * LD + c1];
+            T t4[4];
+            load4<T>(TaT + j1 * P + 4 * jb, t4);
+            a0 = fma(t4[0], x1, a0);
+            a1 = fma(t4[1], x1, a1);
+            a2 = fma(t4[2], x1, a2);
+            a3 = fma(t4[3], x1, a3);
+          }
+          Tbs[(4 * jb + 0) * LD + c1] = a0;
+          Tbs[(4 * jb + 1) * LD + c1] = a1;
+          Tbs[(4 * jb + 2) * LD + c1] = a2;
+          Tbs[(4 * jb + 3) * LD + c1] = a3;
+        }
       }
     }
-
     const T* Vs;
     if (STAGE) {
       bool ok = true;
       if (valid || tid == 0) ok = mbar_wait_bounded(&mbar[b], (uint32_t)((k >> 1) & 1));
       if (!ok) atomicOr(&timed_out, 1);
       Vs = Vbuf + b * nv;
-      __syncthreads();
-      if (timed_out) break;
     } else {
       Vs = V + (int64_t)slab * nv;
     }
+    __syncthreads();  // (1) T_b complete; the previous slab's phase 3 is done with Sred
+    if (STAGE && timed_out) break;
 
-    // eta = X_2 T_b, r = V (.) eta, S = X_2^T r over this warp's rows (fused mode-2 products)
+    // prefetch the next slab's T_a into registers (stored after phase 2)
+    T ta_next[kTaPer];
+    const int nxt_slab = slab + gridDim.x;
+#pragma unroll
+    for (int r = 0; r < kTaPer; ++r) {
+      const int idx = tid + r * nth;
+      ta_next[r] = T(0);
+      if (nxt_slab < n3 && idx < p1 * P) {
+        const int j1 = idx / P, j2 = idx - j1 * P;
+        if (j2 < p2) ta_next[r] = Ta[(int64_t)nxt_slab * p2 * p1 + j2 * p1 + j1];
+      }
+    }
+
+    // ---- phase 2: eta = X_2 T_b, r = V (.) eta, S = X_2^T r over this warp's rows ----
     if (valid) {
+      T tb[P], sacc[P];
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        tb[j] = Tbs[j * LD + c];
+        sacc[j] = T(0);
+      }
       const T* vcol = Vs + c;
 #pragma unroll 2
       for (int i2 = r0; i2 < r1; ++i2) {
@@ -263,15 +341,20 @@ fused_slab_kernel(SlabShape sh, const T* __restrict__ X1T, const T* __restrict__
           e2 = fma(x2[j + 2], tb[j + 2], e2);
           e3 = fma(x2[j + 3], tb[j + 3], e3);
         }
-        const T r = vcol[(int64_t)i2 * n1] * ((e0 + e1) + (e2 + e3));
+        const T rr = vcol[(int64_t)i2 * n1] * ((e0 + e1) + (e2 + e3));
 #pragma unroll
-        for (int j = 0; j < P; ++j) s[j] = fma(x2[j], r, s[j]);
+        for (int j = 0; j < P; ++j) sacc[j] = fma(x2[j], rr, sacc[j]);
       }
+      T* srow = Sred + ((int64_t)rg * n1 + c) * SP;
 #pragma unroll
-      for (int j = 0; j < P; ++j)
-        if (j < p2) Sred[(rg * P + j) * LD + c] = s[j];
+      for (int j = 0; j < P; j += 4) store4<T>(srow + j, sacc[j], sacc[j + 1], sacc[j + 2], sacc[j + 3]);
     }
-    __syncthreads();  // (B) partial S complete; every thread is done with this V buffer
+#pragma unroll
+    for (int r = 0; r < kTaPer; ++r) {
+      const int idx = tid + r * nth;
+      if (nxt_slab < n3 && idx < p1 * P) TaT[idx] = ta_next[r];
+    }
+    __syncthreads();  // (2) partial S complete; this V buffer and T_a are free
     if (STAGE && tid == 0) {
       const int nxt = slab + 2 * gridDim.x;
       if (nxt < n3) {
@@ -280,31 +363,66 @@ fused_slab_kernel(SlabShape sh, const T* __restrict__ X1T, const T* __restrict__
         bulk_g2s(Vbuf + b * nv, V + (int64_t)nxt * nv, sh.vbytes, &mbar[b]);
       }
     }
-    if (sh.RG > 1) {
-      for (int idx = tid; idx < p2 * n1; idx += nth) {
-        const int j2 = idx / n1, cc = idx - j2 * n1;
-        T acc = Sred[j2 * LD + cc];
-        for (int g = 1; g < sh.RG; ++g) acc += Sred[(g * P + j2) * LD + cc];
-        Sred[j2 * LD + cc] = acc;
+    if (RG > 1) {
+      const int nq = n1 * (P / 4);
+      for (int idx = tid; idx < nq; idx += nth) {
+        const int cc = idx / (P / 4), j = 4 * (idx - cc * (P / 4));
+        T a[4], t[4];
+        load4<T>(Sred + (int64_t)cc * SP + j, a);
+        for (int g = 1; g < RG; ++g) {
+          load4<T>(Sred + ((int64_t)g * n1 + cc) * SP + j, t);
+          a[0] += t[0]; a[1] += t[1]; a[2] += t[2]; a[3] += t[3];
+        }
+        store4<T>(Sred + (int64_t)cc * SP + j, a[0], a[1], a[2], a[3]);
       }
-      __syncthreads();  // (C)
+      __syncthreads();  // (3) S complete in Sred[0]
     }
 
-    // S_b[slab](j2, j1) = sum_c S(j2, c) X_1(c, j1)   (mode-1 product back to p1)
+    // ---- phase 3: S_b(j2, j1) = sum_c S(j2, c) X_1(c, j1), 4 x 4 blocks, 16 lanes over c ----
     T* out = Sb + (int64_t)slab * p2 * p1;
-    const int nw = nth >> 5;
-    for (int j2 = warp; j2 < p2; j2 += nw) {
-      const T* srow = Sred + j2 * LD;
-      for (int j1 = lane; j1 < p1; j1 += 32) {
-        const T* xrow = X1s + j1 * LD;
-        T a0 = T(0), a1 = T(0);
-        int cc = 0;
-        for (; cc + 1 < n1; cc += 2) {
-          a0 = fma(srow[cc], xrow[cc], a0);
-          a1 = fma(srow[cc + 1], xrow[cc + 1], a1);
+    const int nwarps = nth >> 5;
+    for (int pair = warp; 2 * pair < NB; pair += nwarps) {
+      const int blk = 2 * pair + (lane >> 4);
+      const bool act = blk < NB;
+      const int jb2 = act ? blk / NB1 : 0, jb1 = act ? blk - jb2 * NB1 : 0;
+      T acc[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+      if (act) {
+        for (int cc = q; cc < n1; cc += 16) {
+          T sv[4], xv[4];
+          load4<T>(Sred + (int64_t)cc * SP + 4 * jb2, sv);
+          load4<T>(X1c + (int64_t)cc * Q1P + 4 * jb1, xv);
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fma(sv[u], xv[v], acc[u][v]);
         }
-        if (cc < n1) a0 = fma(srow[cc], xrow[cc], a0);
-        out[j2 * p1 + j1] = a0 + a1;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          T t = acc[u][v];
+          t += __shfl_xor_sync(0xffffffffu, t, 1);
+          t += __shfl_xor_sync(0xffffffffu, t, 2);
+          t += __shfl_xor_sync(0xffffffffu, t, 4);
+          t += __shfl_xor_sync(0xffffffffu, t, 8);
+          acc[u][v] = t;
+        }
+      if (act && q == 0) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j2 = 4 * jb2 + u;
+          if (j2 >= p2) continue;
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const int j1 = 4 * jb1 + v;
+            if (j1 < p1) out[j2 * p1 + j1] = acc[u][v];
+          }
+        }
       }
     }
   }
@@ -363,6 +481,8 @@ bool configure(int n1, int n2, int p1, int p2, int elem, bool stage, SlabShape& 
     return false;
   }
   threads = 32 * sh.CT * sh.RG;
+  // the next slab's T_a (p1 x P values) is prefetched with ceil(32 P / 256) values per thread
+  if ((int64_t)threads * ((32 * P + 255) / 256) < (int64_t)p1 * P) return false;
   return threads <= (elem == 8 ? 256 : 512);
 }
 
