@@ -303,15 +303,15 @@ def measure_details(g, torch, pr, plan, X, Y, W, pen, opts, dev, flush, last):
     fl = slab * n3
     by = 4 * n + 2 * 4 * n3 * p2 * p1 + 4 * (n1 * p1 + n2 * p2)
     peak_alu = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    t_f = ms[1] / 1e3
+    t_f = ms[0] / 1e3
     out["roofline"] = {"bound": "alu", "kernel": "fused_slab_kernel<float,20> (G(V(.)H) per slab)",
                        "achieved": fl / t_f / 1e12, "peak": peak_alu, "unit": "TFLOP/s",
                        "frac": fl / t_f / 1e12 / peak_alu, "traffic": None,
-                       "flops_per_launch": fl, "ms_per_launch": ms[1],
+                       "flops_per_launch": fl, "ms_per_launch": ms[0],
                        "peak_note": "FP32 SIMT: 152 SMs x 128 lanes x 2 FLOP x max SM clock",
                        "hbm_view": {"bytes_per_launch": by, "GB/s": by / t_f / 1e9,
                                     "frac": by / t_f / 1e9 / peaks["hbm_gbs"], "peak_src": src}}
-    out["inner_iteration_ms"] = {"mode3_extrap": ms[0], "fused_slab": ms[1], "mode3_adj_split": ms[2],
+    out["inner_iteration_ms"] = {"fused_slab": ms[0], "mode3": ms[1], "mode3_adj_split": ms[2],
                                  "prox": ms[3], "sum": per_iter}
     # the FP64 GPU path on a bounded sample of the same path (its first 4 lambdas)
     plan64 = g.Plan(pr.n, pr.p, pr.family, g.GLAM_FP64)
@@ -380,7 +380,7 @@ def run_kernels(reps):
     q = g.glam_quad_build(plan, X, theta, f32(pr.Y), f32(pr.W))
     ms = g.glam_time_inner_kernels(plan, X, q, reps=reps)
     torch.cuda.synchronize()
-    print(json.dumps({"kernels_ms": dict(zip(["mode3", "fused_slab", "mode3_adj_split", "prox"], ms))}))
+    print(json.dumps({"kernels_ms": dict(zip(["fused_slab", "mode3", "mode3_adj_split", "prox"], ms))}))
     return 0
 
 

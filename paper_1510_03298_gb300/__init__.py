@@ -389,7 +389,7 @@ def glam_launch_count() -> int:
 
 def glam_time_inner_kernels(plan: Plan, X, quad: Quad, reps: int = 50):
     """Mean CUDA-event time (ms) per launch of the four inner-iteration kernels on the plan's
-    stream: [mode-3 product, fused slab G(V(.)H), split mode-3 adjoint, prox step]."""
+    stream: [fused slab G(V(.)H), mode-3 product, split mode-3 adjoint, prox step]."""
     plan._sync_stream()
     xs = plan._X(X)
     ms = (C.c_double * 4)()

@@ -283,33 +283,53 @@ prox_kernel(int64_t p, int ksplit, const Tq* __restrict__ Qpart, const TP* __res
             TP lin_scale, const TP* __restrict__ x, const TP* xprev, const TP* __restrict__ pen_w,
             TP* out, TP inv_n, InnerCtl* ctl, TP omega_h, TP delta_h, TP lambda_h, const double* Lhat,
             Tq* __restrict__ dnext, const TP* __restrict__ anchor) {
+  // The element loads of the first grid-stride step are issued before the control block is
+  // read (they do not depend on it), so the two memory round trips overlap.
+  const int64_t m0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  TP q0 = TP(0), lin0 = TP(0), x0 = TP(0), xp0 = TP(0), pw0 = TP(0), an0 = TP(0);
+  if (m0 < p) {
+    for (int s = 0; s < ksplit; ++s) q0 += TP(Qpart[(int64_t)s * p + m0]);
+    lin0 = lin[m0];
+    x0 = x[m0];
+    xp0 = xprev[m0];
+    pw0 = pen_w[m0];
+    if (dnext != nullptr) an0 = anchor[m0];
+  }
   TP omega, delta, lam, omega_next = TP(0);
   if (ctl != nullptr) {
-    if (ctl->done) return;
+    const int done = ctl->done;
     const int l = ctl->l;
+    const double cdelta = ctl->delta, clambda = ctl->lambda;
+    if (done) return;
     omega = TP(l - 1) / TP(l + 2);
     omega_next = TP(l) / TP(l + 3);
-    delta = TP(ctl->delta);
-    lam = TP(ctl->lambda);
+    delta = TP(cdelta);
+    lam = TP(clambda);
   } else {
     omega = omega_h;
     delta = delta_h > TP(0) ? delta_h : TP(1.0 / *Lhat);
     lam = lambda_h;
   }
   double crit = 0.0;
-  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < p;
-       m += (int64_t)gridDim.x * blockDim.x) {
-    TP q = TP(0);
-    for (int s = 0; s < ksplit; ++s) q += TP(Qpart[(int64_t)s * p + m]);
-    const TP g = lin_scale * lin[m] + q * inv_n;
-    const TP xm = x[m];
-    const TP y = xm + omega * (xm - xprev[m]);   // extrapolation, Sec. 3.2
+  for (int64_t m = m0; m < p; m += stride) {
+    TP q, lm, xm, xpm, pwm, anm;
+    if (m == m0) {
+      q = q0; lm = lin0; xm = x0; xpm = xp0; pwm = pw0; anm = an0;
+    } else {
+      q = TP(0);
+      for (int s = 0; s < ksplit; ++s) q += TP(Qpart[(int64_t)s * p + m]);
+      lm = lin[m]; xm = x[m]; xpm = xprev[m]; pwm = pen_w[m];
+      anm = dnext != nullptr ? anchor[m] : TP(0);
+    }
+    const TP g = lin_scale * lm + q * inv_n;    // gradient of the quadratic model
+    const TP y = xm + omega * (xm - xpm);       // extrapolation, Sec. 3.2
     const TP z = y - delta * g;
-    const TP thr = delta * lam * pen_w[m];
-    const TP az = fabs(z) - thr;                 // soft threshold, Sec. 6.3
+    const TP thr = delta * lam * pwm;
+    const TP az = fabs(z) - thr;                // soft threshold, Sec. 6.3
     const TP xn = az > TP(0) ? copysign(az, z) : TP(0);
     out[m] = xn;
-    if (dnext != nullptr) dnext[m] = Tq(xn + omega_next * (xn - xm) - anchor[m]);
+    if (dnext != nullptr) dnext[m] = Tq(xn + omega_next * (xn - xm) - anm);
     crit = fmax(crit, (double)fabs(xn - y));
   }
   if (ctl == nullptr) return;

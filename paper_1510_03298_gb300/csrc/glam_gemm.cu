@@ -19,13 +19,14 @@
 namespace glam {
 namespace {
 
-constexpr int BK = 16;
 
 // TB is the storage type of the B operand.  With EXTRAP the operand is formed on load as
 // B + omega (B - Bp) - Bs (Bp, Bs optional), in double when TB is double, then rounded to T:
 // the FISTA extrapolation y = x + omega (x - x_prev) of Sec. 3.2, minus the anchor theta_k.
 // Tiles of (16 TM) x (16 TN) outputs; 256 threads with TM x TN outputs each.
-template <typename T, typename TB, bool EXTRAP, int TM, int TN>
+// BK is the K depth staged per step: 64 when the contraction fits in one step (all operand
+// loads of the tile are then in flight together), else 16.
+template <typename T, typename TB, bool EXTRAP, int TM, int TN, int BK>
 __global__ void __launch_bounds__(256)
 gemm_kernel(GemmDesc d, const T* __restrict__ A, const TB* __restrict__ B, T* __restrict__ C,
             const TB* __restrict__ Bp, const TB* __restrict__ Bs, const InnerCtl* __restrict__ ctl,
@@ -129,20 +130,36 @@ gemm_kernel(GemmDesc d, const T* __restrict__ A, const TB* __restrict__ B, T* __
   }
 }
 
+template <typename T, typename TB, bool EXTRAP, int BK>
+void launch_bk(const GemmDesc& d, dim3 grid, int tm, int tn, const T* A, const TB* B, T* C,
+               cudaStream_t s, const TB* Bp, const TB* Bs, const InnerCtl* ctl, double omega,
+               const int* skip) {
+  if (tm == 4 && tn == 4)
+    gemm_kernel<T, TB, EXTRAP, 4, 4, BK><<<grid, 256, 0, s>>>(d, A, B, C, Bp, Bs, ctl, omega, skip);
+  else if (tm == 2 && tn == 4)
+    gemm_kernel<T, TB, EXTRAP, 2, 4, BK><<<grid, 256, 0, s>>>(d, A, B, C, Bp, Bs, ctl, omega, skip);
+  else if (tm == 4 && tn == 2)
+    gemm_kernel<T, TB, EXTRAP, 4, 2, BK><<<grid, 256, 0, s>>>(d, A, B, C, Bp, Bs, ctl, omega, skip);
+  else
+    gemm_kernel<T, TB, EXTRAP, 2, 2, BK><<<grid, 256, 0, s>>>(d, A, B, C, Bp, Bs, ctl, omega, skip);
+}
+
 template <typename T, typename TB, bool EXTRAP>
 cudaError_t launch_tiles(const GemmDesc& d, int tm, int tn, const T* A, const TB* B, T* C,
                          cudaStream_t s, const TB* Bp, const TB* Bs, const InnerCtl* ctl,
                          double omega, const int* skip) {
   dim3 grid((d.N + 16 * tn - 1) / (16 * tn), (d.M + 16 * tm - 1) / (16 * tm), d.batch * d.ksplit);
   if (grid.y > 65535) return cudaErrorInvalidValue;
-  if (tm == 4 && tn == 4)
-    gemm_kernel<T, TB, EXTRAP, 4, 4><<<grid, 256, 0, s>>>(d, A, B, C, Bp, Bs, ctl, omega, skip);
-  else if (tm == 2 && tn == 4)
-    gemm_kernel<T, TB, EXTRAP, 2, 4><<<grid, 256, 0, s>>>(d, A, B, C, Bp, Bs, ctl, omega, skip);
-  else if (tm == 4 && tn == 2)
-    gemm_kernel<T, TB, EXTRAP, 4, 2><<<grid, 256, 0, s>>>(d, A, B, C, Bp, Bs, ctl, omega, skip);
-  else
-    gemm_kernel<T, TB, EXTRAP, 2, 2><<<grid, 256, 0, s>>>(d, A, B, C, Bp, Bs, ctl, omega, skip);
+  const int kper = (d.K + d.ksplit - 1) / d.ksplit;
+  // one 64-deep step when the split's contraction fits in it (single-precision tiles only: the
+  // FP64 tiles would need 2 x 64 x 68 x 8 = 70 KB of static shared memory at TM = TN = 4)
+  if constexpr (sizeof(T) == 4) {
+    if (kper > 16 && kper <= 64) {
+      launch_bk<T, TB, EXTRAP, 64>(d, grid, tm, tn, A, B, C, s, Bp, Bs, ctl, omega, skip);
+      return cudaSuccess;
+    }
+  }
+  launch_bk<T, TB, EXTRAP, 16>(d, grid, tm, tn, A, B, C, s, Bp, Bs, ctl, omega, skip);
   return cudaSuccess;
 }
 

@@ -163,3 +163,25 @@ def test_resume_from_a_warm_start():
         lam = full.lambdas[3 + k]
         assert abs(O.objective(d, th_full, lam) - O.objective(d, th_res, lam)) <= 1e-11 * abs(O.objective(d, th_full, lam))
         assert O.kkt_residual(d, th_res, lam, lmax) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_unfused_shape_path_matches_oracle(prec):
+    """p2 = 33 exceeds the fused slab kernel's limit: the inner iteration runs the unfused chain
+    of mode products and the separate prox kernel; the solutions must still meet the oracle."""
+    torch, g = gpu_or_skip()
+    n, p = (7, 36, 5), (3, 33, 2)
+    pr = gen.random_problem(16, n, p, gen.POISSON, mask_frac=0.1, basis="normal")
+    d = O.GlamData.from_c(pr.family, pr.XT, pr.Y, pr.W, pr.pen_w)
+    lams, thetas, stats, lmax = O.fit_path(d, nlambda=4, ratio=5e-2, tol=1e-10)
+    dt = dtype_of(prec)
+    plan = g.Plan(n, p, pr.family, plan_prec(g, prec))
+    res = g.glam_fit_path(plan, [dev(x, dt) for x in pr.XT], dev(pr.Y, dt), dev(pr.W, dt),
+                          dev(pr.pen_w, torch.float64), lambdas=list(lams),
+                          opts=g.glam_opts_default(tol=1e-9 if prec == "fp64" else 1e-6))
+    assert res.status == g.GLAM_OK, res.message
+    for k in range(len(lams)):
+        th = O.paper_array(host(res.path[k]))
+        assert O.kkt_residual(d, th, lams[k], lmax) <= (1e-9 if prec == "fp64" else 3e-6)
+        F, Fref = O.objective(d, th, lams[k]), O.objective(d, thetas[k], lams[k])
+        assert abs(F - Fref) <= (1e-10 if prec == "fp64" else 1e-6) * abs(Fref)
