@@ -382,6 +382,7 @@ int glam_plan_create(const glam_dims* dims, int family, int precision, void* str
   for (double** v : {&pl->th, &pl->x0, &pl->x1, &pl->gk, &pl->pen, &pl->ptmp})
     if ((st = dalloc(pl, v, p)) != GLAM_OK) return bail(st);
   if ((st = dalloc(pl, &pl->d_gram, 4096)) != GLAM_OK) return bail(st);
+
   if ((st = dalloc(pl, &pl->ctl, 1)) != GLAM_OK) return bail(st);
   if ((st = dalloc(pl, &pl->sc, 1)) != GLAM_OK) return bail(st);
   if ((st = dalloc(pl, &pl->red.partial, (size_t)kMaxRedBlocks * kRedSlots)) != GLAM_OK) return bail(st);
@@ -677,7 +678,19 @@ int capture_chunk(Fit<T>& f) {
   for (int it = 0; it < C && st == GLAM_OK; ++it) {
     double* x = (it % 2 == 0) ? pl->x0 : pl->x1;
     double* xp = (it % 2 == 0) ? pl->x1 : pl->x0;
-    st = op.template XtWX<T>(op.w.dn, nullptr, nullptr, op.w.V, nullptr, 0.0, &pl->ctl->done);
+    if (pl->fused[sizeof(T) == 8 ? 1 : 0]) {
+      // the fused kernel forms T_a = X_3 d from the correction itself, then the split adjoint
+      cudaError_t e = launch_fused_slab<T>((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1,
+                                           (int)pl->p2, op.X[0], op.X[1], op.w.dn, op.w.V, op.w.Sb,
+                                           f.s, &pl->ctl->done, &pl->sc->timeout, op.X[2],
+                                           (int)pl->p3);
+      if (e == cudaSuccess)
+        e = launch_gemm<T, T>(d_mode3_adj(pl, pl->ksplit), op.X[2], op.w.Sb, op.w.Qpart, f.s, nullptr,
+                              nullptr, nullptr, 0.0, &pl->ctl->done);
+      if (e != cudaSuccess) st = fail(pl, GLAM_ECUDA, std::string("inner iteration launch: ") + cudaGetErrorString(e));
+    } else {
+      st = op.template XtWX<T>(op.w.dn, nullptr, nullptr, op.w.V, nullptr, 0.0, &pl->ctl->done);
+    }
     if (st == GLAM_OK) {
       cudaError_t e = launch_prox<T, double>(pl->p, pl->ksplit, op.w.Qpart, pl->gk, 1.0, x, xp,
                                              pl->pen, xp, 1.0 / (double)pl->n, pl->ctl, 0.0, 0.0,
@@ -949,10 +962,11 @@ int time_inner_impl(glam_plan* pl, const void* const X[3], const glam_quad* q, i
       switch (which) {
         case 0:
           CK(launch_fused_slab<T>((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2,
-                                  op.X[0], op.X[1], op.w.Ta, V, op.w.Sb, pl->stream, nullptr,
-                                  &pl->sc->timeout));
+                                  op.X[0], op.X[1], op.w.dn, V, op.w.Sb, pl->stream, nullptr,
+                                  &pl->sc->timeout, op.X[2], (int)pl->p3));
           break;
         case 1:
+          if (pl->fused[slot]) return GLAM_OK;  // folded into the fused kernel
           CK(launch_gemm<T, T>(d_mode3_fwd(pl), op.X[2], op.w.dn, op.w.Ta, pl->stream));
           break;
         case 2:

@@ -72,7 +72,7 @@ constexpr int max_threads() {
 }
 
 struct SlabShape {
-  int n1, n2, n3, p1, p2, CT, RG, LD;
+  int n1, n2, n3, p1, p2, p3, CT, RG, LD;
   uint32_t vbytes;  // n2 * n1 * sizeof(T) (bulk copy size)
 };
 
@@ -83,13 +83,15 @@ __host__ __device__ constexpr int row_pitch(int w) { return (w % 8 == 0) ? w + 4
 // Shared-memory layout of one CTA, in elements.  Every section starts on a 32-byte boundary
 // (16-byte vector reads of X_2, T_a, S and X_1 rows and the bulk-copy destinations need 16).
 struct SlabLayout {
-  int64_t vbuf, x2, x1, x1c, ta, tb, sred, total;
+  int64_t vbuf, x2, x1, x1c, ta, tb, sred, taall, x3r, total;
   int sp, q1, q1p;  // S row pitch, p1 rounded up to 4, X_1 row pitch
+  int kcta;         // slabs per CTA (TAD)
 };
 
 __host__ __device__ inline int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
-__host__ __device__ inline SlabLayout slab_layout(const SlabShape& sh, int P, int elem, bool stage) {
+__host__ __device__ inline SlabLayout slab_layout(const SlabShape& sh, int P, int elem, bool stage,
+                                                  bool tad = false, int kcta = 0) {
   const int64_t A = 32 / elem;
   SlabLayout L;
   L.sp = row_pitch(P);
@@ -109,7 +111,12 @@ __host__ __device__ inline SlabLayout slab_layout(const SlabShape& sh, int P, in
   L.tb = off;                                   // [P][LD]
   off = align_up(off + (int64_t)P * sh.LD, A);
   L.sred = off;                                 // [RG][n1][sp]
-  off += (int64_t)sh.RG * sh.n1 * L.sp;
+  off = align_up(off + (int64_t)sh.RG * sh.n1 * L.sp, A);
+  L.kcta = tad ? kcta : 0;
+  L.taall = off;                                // [kcta][p2 p1]  (TAD)
+  off = align_up(off + (tad ? (int64_t)kcta * sh.p2 * sh.p1 : 0), A);
+  L.x3r = off;                                  // [kcta][p3]     (TAD)
+  off += tad ? (int64_t)kcta * sh.p3 : 0;
   L.total = off;
   return L;
 }
@@ -138,18 +145,23 @@ __device__ __forceinline__ void store4(T* dst, T a, T b, T c, T d) {
   }
 }
 
-template <typename T, int P, bool STAGE>
+// TAD: instead of reading T_a (n3 x p2p1) from memory, the CTA forms it for its own slabs at
+// the start, T_a(i3, :) = sum_j3 X_3(i3, j3) d(j3, :), from the correction d (p3 x p2p1, `Ta`
+// then points at d) and X_3^T (p3 x n3): the first H stage folded into this kernel.
+template <typename T, int P, bool STAGE, bool TAD>
 __global__ void __launch_bounds__(max_threads<T>(), 1)
 fused_slab_kernel(SlabShape sh, const T* __restrict__ X1T, const T* __restrict__ X2T,
                   const T* __restrict__ Ta, const T* __restrict__ V, T* __restrict__ Sb,
-                  const int* __restrict__ skip, int* __restrict__ err) {
+                  const int* __restrict__ skip, int* __restrict__ err, const T* __restrict__ X3T) {
   if (skip != nullptr && *skip) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ uint64_t mbar[2];
   __shared__ int timed_out;
   const int n1 = sh.n1, n2 = sh.n2, n3 = sh.n3, p1 = sh.p1, p2 = sh.p2, LD = sh.LD, RG = sh.RG;
   const int nv = n2 * n1;
-  const SlabLayout L = slab_layout(sh, P, (int)sizeof(T), STAGE);
+  const int kcta = TAD ? (n3 - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  const SlabLayout L = slab_layout(sh, P, (int)sizeof(T), STAGE, TAD,
+                                   TAD ? (n3 + (int)gridDim.x - 1) / (int)gridDim.x : 0);
   const int SP = L.sp, Q1 = L.q1, Q1P = L.q1p;
   T* const base = reinterpret_cast<T*>(smem_raw);
   T* Vbuf = base + L.vbuf;  // [2][n2 * n1]   (STAGE only)
@@ -180,9 +192,39 @@ fused_slab_kernel(SlabShape sh, const T* __restrict__ X1T, const T* __restrict__
     const int i1 = idx / (Q1 - p1), j1 = p1 + idx - i1 * (Q1 - p1);
     X1c[i1 * Q1P + j1] = T(0);
   }
+  T* TaAll = base + L.taall;  // [kcta][p2 p1]  T_a of this CTA's slabs (TAD)
+  T* X3r = base + L.x3r;      // [kcta][p3]     their rows of X_3 (TAD)
+  if (TAD) {
+    const int p3 = sh.p3, P21 = p2 * p1;
+    for (int idx = tid; idx < kcta * p3; idx += nth) {
+      const int kk = idx / p3, j3 = idx - kk * p3;
+      X3r[idx] = X3T[(int64_t)j3 * n3 + blockIdx.x + (int64_t)kk * gridDim.x];
+    }
+    __syncthreads();
+    // T_a(s_k, n) = sum_j3 X_3(s_k, j3) d(j3, n): columns n over the threads, slabs in chunks of 4
+    for (int n = tid; n < P21; n += nth) {
+      for (int k0 = 0; k0 < kcta; k0 += 4) {
+        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+        const T* x0r = X3r + (int64_t)k0 * p3;
+#pragma unroll 4
+        for (int j3 = 0; j3 < p3; ++j3) {
+          const T dv = Ta[(int64_t)j3 * P21 + n];
+          a0 = fma(x0r[j3], dv, a0);
+          if (k0 + 1 < kcta) a1 = fma(x0r[p3 + j3], dv, a1);
+          if (k0 + 2 < kcta) a2 = fma(x0r[2 * p3 + j3], dv, a2);
+          if (k0 + 3 < kcta) a3 = fma(x0r[3 * p3 + j3], dv, a3);
+        }
+        TaAll[(int64_t)k0 * P21 + n] = a0;
+        if (k0 + 1 < kcta) TaAll[(int64_t)(k0 + 1) * P21 + n] = a1;
+        if (k0 + 2 < kcta) TaAll[(int64_t)(k0 + 2) * P21 + n] = a2;
+        if (k0 + 3 < kcta) TaAll[(int64_t)(k0 + 3) * P21 + n] = a3;
+      }
+    }
+    __syncthreads();
+  }
   // T_a of the first slab
   if ((int)blockIdx.x < n3) {
-    const T* ta = Ta + (int64_t)blockIdx.x * p2 * p1;
+    const T* ta = TAD ? TaAll : Ta + (int64_t)blockIdx.x * p2 * p1;
     for (int idx = tid; idx < p1 * P; idx += nth) {
       const int j1 = idx / P, j2 = idx - j1 * P;
       TaT[idx] = (j2 < p2) ? ta[j2 * p1 + j1] : T(0);
@@ -267,7 +309,9 @@ fused_slab_kernel(SlabShape sh, const T* __restrict__ X1T, const T* __restrict__
       ta_next[r] = T(0);
       if (nxt_slab < n3 && idx < p1 * P) {
         const int j1 = idx / P, j2 = idx - j1 * P;
-        if (j2 < p2) ta_next[r] = Ta[(int64_t)nxt_slab * p2 * p1 + j2 * p1 + j1];
+        if (j2 < p2)
+          ta_next[r] = TAD ? TaAll[(int64_t)(k + 1) * p2 * p1 + j2 * p1 + j1]
+                           : Ta[(int64_t)nxt_slab * p2 * p1 + j2 * p1 + j1];
       }
     }
 
@@ -395,8 +439,8 @@ int pick_P(int p2) {
   return 0;
 }
 
-size_t smem_bytes(const SlabShape& sh, int P, int elem, bool stage) {
-  return (size_t)slab_layout(sh, P, elem, stage).total * elem;
+size_t smem_bytes(const SlabShape& sh, int P, int elem, bool stage, bool tad = false, int kcta = 0) {
+  return (size_t)slab_layout(sh, P, elem, stage, tad, kcta).total * elem;
 }
 
 // Dynamic shared-memory budget of one CTA: the device's opt-in limit minus room for the
@@ -405,13 +449,14 @@ size_t g_smem_budget = 227 * 1024 - 256;
 
 // Shape, block size and shared-memory plan; stage = false plans direct V loads.
 bool configure(int n1, int n2, int p1, int p2, int elem, bool stage, SlabShape& sh, int& threads,
-               size_t& smem) {
+               size_t& smem, bool tad = false, int kcta = 0, int p3 = 1) {
   const int P = pick_P(p2);
   if (P == 0 || n1 <= 0 || n2 <= 0 || p1 <= 0 || n1 > 256 || p1 > 64) return false;
   if (elem == 8 && P > 24) return false;  // FP64 register arrays beyond this spill
   sh.n1 = n1;
   sh.n2 = n2;
   sh.n3 = 0;
+  sh.p3 = p3;
   sh.p1 = p1;
   sh.p2 = p2;
   sh.CT = (n1 + 31) / 32;
@@ -423,7 +468,7 @@ bool configure(int n1, int n2, int p1, int p2, int elem, bool stage, SlabShape& 
   if (sh.RG > n2) sh.RG = n2;
   sh.vbytes = (uint32_t)((size_t)n1 * n2 * elem);
   while (true) {
-    smem = smem_bytes(sh, P, elem, stage);
+    smem = smem_bytes(sh, P, elem, stage, tad, kcta);
     if (smem <= g_smem_budget) break;
     if (sh.RG > 1) {
       sh.RG = sh.RG / 2;
@@ -437,46 +482,57 @@ bool configure(int n1, int n2, int p1, int p2, int elem, bool stage, SlabShape& 
   return threads <= (elem == 8 ? 256 : 512);
 }
 
-template <typename T, int P, bool STAGE>
-cudaError_t launch_P(const SlabShape& sh, int grid, int threads, size_t smem, const T* X1T,
-                     const T* X2T, const T* Ta, const T* V, T* Sb, cudaStream_t s, const int* skip,
-                     int* err) {
-  fused_slab_kernel<T, P, STAGE><<<grid, threads, smem, s>>>(sh, X1T, X2T, Ta, V, Sb, skip, err);
+struct FusedArgs {
+  const void* X1T;
+  const void* X2T;
+  const void* Ta;   // T_a (n3 x p2p1), or the correction d (p3 x p2p1) with TAD
+  const void* V;
+  void* Sb;
+  const int* skip;
+  int* err;
+  const void* X3T;  // TAD only
+};
+
+template <typename T, int P, bool STAGE, bool TAD>
+cudaError_t launch_P(const SlabShape& sh, int grid, int threads, size_t smem, const FusedArgs& a,
+                     cudaStream_t s) {
+  fused_slab_kernel<T, P, STAGE, TAD><<<grid, threads, smem, s>>>(
+      sh, (const T*)a.X1T, (const T*)a.X2T, (const T*)a.Ta, (const T*)a.V, (T*)a.Sb, a.skip, a.err,
+      (const T*)a.X3T);
   count_launches(1);
   return cudaGetLastError();
 }
 
-template <typename T, bool STAGE>
-cudaError_t launch_S(int P, const SlabShape& sh, int grid, int threads, size_t smem, const T* X1T,
-                     const T* X2T, const T* Ta, const T* V, T* Sb, cudaStream_t s, const int* skip,
-                     int* err) {
+template <typename T, bool STAGE, bool TAD>
+cudaError_t launch_S(int P, const SlabShape& sh, int grid, int threads, size_t smem,
+                     const FusedArgs& a, cudaStream_t s) {
   switch (P) {
-    case 8: return launch_P<T, 8, STAGE>(sh, grid, threads, smem, X1T, X2T, Ta, V, Sb, s, skip, err);
-    case 12: return launch_P<T, 12, STAGE>(sh, grid, threads, smem, X1T, X2T, Ta, V, Sb, s, skip, err);
-    case 16: return launch_P<T, 16, STAGE>(sh, grid, threads, smem, X1T, X2T, Ta, V, Sb, s, skip, err);
-    case 20: return launch_P<T, 20, STAGE>(sh, grid, threads, smem, X1T, X2T, Ta, V, Sb, s, skip, err);
-    case 24: return launch_P<T, 24, STAGE>(sh, grid, threads, smem, X1T, X2T, Ta, V, Sb, s, skip, err);
-    case 28: return launch_P<T, 28, STAGE>(sh, grid, threads, smem, X1T, X2T, Ta, V, Sb, s, skip, err);
-    case 32: return launch_P<T, 32, STAGE>(sh, grid, threads, smem, X1T, X2T, Ta, V, Sb, s, skip, err);
+    case 8: return launch_P<T, 8, STAGE, TAD>(sh, grid, threads, smem, a, s);
+    case 12: return launch_P<T, 12, STAGE, TAD>(sh, grid, threads, smem, a, s);
+    case 16: return launch_P<T, 16, STAGE, TAD>(sh, grid, threads, smem, a, s);
+    case 20: return launch_P<T, 20, STAGE, TAD>(sh, grid, threads, smem, a, s);
+    case 24: return launch_P<T, 24, STAGE, TAD>(sh, grid, threads, smem, a, s);
+    case 28: return launch_P<T, 28, STAGE, TAD>(sh, grid, threads, smem, a, s);
+    case 32: return launch_P<T, 32, STAGE, TAD>(sh, grid, threads, smem, a, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <typename T, int P, bool STAGE>
+template <typename T, int P, bool STAGE, bool TAD>
 cudaError_t prepare_P() {
-  return cudaFuncSetAttribute(fused_slab_kernel<T, P, STAGE>,
+  return cudaFuncSetAttribute(fused_slab_kernel<T, P, STAGE, TAD>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g_smem_budget);
 }
 
-template <typename T, bool STAGE>
+template <typename T, bool STAGE, bool TAD>
 cudaError_t prepare_TS() {
-  cudaError_t e = prepare_P<T, 8, STAGE>();
-  if (e == cudaSuccess) e = prepare_P<T, 12, STAGE>();
-  if (e == cudaSuccess) e = prepare_P<T, 16, STAGE>();
-  if (e == cudaSuccess) e = prepare_P<T, 20, STAGE>();
-  if (e == cudaSuccess) e = prepare_P<T, 24, STAGE>();
-  if (e == cudaSuccess) e = prepare_P<T, 28, STAGE>();
-  if (e == cudaSuccess) e = prepare_P<T, 32, STAGE>();
+  cudaError_t e = prepare_P<T, 8, STAGE, TAD>();
+  if (e == cudaSuccess) e = prepare_P<T, 12, STAGE, TAD>();
+  if (e == cudaSuccess) e = prepare_P<T, 16, STAGE, TAD>();
+  if (e == cudaSuccess) e = prepare_P<T, 20, STAGE, TAD>();
+  if (e == cudaSuccess) e = prepare_P<T, 24, STAGE, TAD>();
+  if (e == cudaSuccess) e = prepare_P<T, 28, STAGE, TAD>();
+  if (e == cudaSuccess) e = prepare_P<T, 32, STAGE, TAD>();
   return e;
 }
 
@@ -499,9 +555,12 @@ cudaError_t fused_prepare() {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
   g_smem_budget = optin > 1024 ? (size_t)optin - 1024 : 0;  // 1 KB kept for static variables
-  e = prepare_TS<float, true>();
-  if (e == cudaSuccess) e = prepare_TS<float, false>();
-  if (e == cudaSuccess) e = prepare_TS<double, false>();
+  e = prepare_TS<float, true, false>();
+  if (e == cudaSuccess) e = prepare_TS<float, false, false>();
+  if (e == cudaSuccess) e = prepare_TS<double, false, false>();
+  if (e == cudaSuccess) e = prepare_TS<float, true, true>();
+  if (e == cudaSuccess) e = prepare_TS<float, false, true>();
+  if (e == cudaSuccess) e = prepare_TS<double, false, true>();
   return e;
 }
 
@@ -515,30 +574,40 @@ int fused_slab_supported(int n1, int n2, int p1, int p2, int elem_bytes) {
 template <typename T>
 cudaError_t launch_fused_slab(int n1, int n2, int n3, int p1, int p2, const T* X1T, const T* X2T,
                               const T* Ta, const T* V, T* Sb, cudaStream_t s, const int* skip,
-                              int* err) {
+                              int* err, const T* X3T, int p3) {
   if (n3 <= 0) return cudaSuccess;
+  const bool tad = X3T != nullptr;
   SlabShape sh;
   int threads;
   size_t smem;
   bool stage = sizeof(T) == 4 && can_stage(n1, n2, (int)sizeof(T), V);
-  if (stage && !configure(n1, n2, p1, p2, (int)sizeof(T), true, sh, threads, smem)) stage = false;
-  if (!stage && !configure(n1, n2, p1, p2, (int)sizeof(T), false, sh, threads, smem))
+  const int grid_stage = n3 < num_sms() ? n3 : num_sms();
+  const int grid_plain = n3 < 2 * num_sms() ? n3 : 2 * num_sms();
+  const int kcta_stage = (n3 + grid_stage - 1) / grid_stage;
+  const int kcta_plain = (n3 + grid_plain - 1) / grid_plain;
+  if (stage && !configure(n1, n2, p1, p2, (int)sizeof(T), true, sh, threads, smem, tad, kcta_stage, p3))
+    stage = false;
+  if (!stage && !configure(n1, n2, p1, p2, (int)sizeof(T), false, sh, threads, smem, tad, kcta_plain, p3))
     return cudaErrorInvalidValue;
   sh.n3 = n3;
-  int grid = stage ? num_sms() : 2 * num_sms();
-  if (grid > n3) grid = n3;
+  const int grid = stage ? grid_stage : grid_plain;
   const int P = pick_P(p2);
+  const FusedArgs a{X1T, X2T, Ta, V, Sb, skip, err, X3T};
   if constexpr (sizeof(T) == 4) {
-    if (stage) return launch_S<T, true>(P, sh, grid, threads, smem, X1T, X2T, Ta, V, Sb, s, skip, err);
+    if (stage)
+      return tad ? launch_S<T, true, true>(P, sh, grid, threads, smem, a, s)
+                 : launch_S<T, true, false>(P, sh, grid, threads, smem, a, s);
   }
-  return launch_S<T, false>(P, sh, grid, threads, smem, X1T, X2T, Ta, V, Sb, s, skip, err);
+  return tad ? launch_S<T, false, true>(P, sh, grid, threads, smem, a, s)
+             : launch_S<T, false, false>(P, sh, grid, threads, smem, a, s);
 }
 
 template cudaError_t launch_fused_slab<float>(int, int, int, int, int, const float*, const float*,
                                               const float*, const float*, float*, cudaStream_t,
-                                              const int*, int*);
+                                              const int*, int*, const float*, int);
 template cudaError_t launch_fused_slab<double>(int, int, int, int, int, const double*,
                                                const double*, const double*, const double*,
-                                               double*, cudaStream_t, const int*, int*);
+                                               double*, cudaStream_t, const int*, int*,
+                                               const double*, int);
 
 }  // namespace glam

@@ -24,7 +24,7 @@ namespace {
 // B + omega (B - Bp) - Bs (Bp, Bs optional), in double when TB is double, then rounded to T:
 // the FISTA extrapolation y = x + omega (x - x_prev) of Sec. 3.2, minus the anchor theta_k.
 // Tiles of (16 TM) x (16 TN) outputs; 256 threads with TM x TN outputs each.
-// BK is the K depth staged per step: 64 when the contraction fits in one step (all operand
+// BK is the K depth staged per step: 32 or 64 when the contraction fits in one step (all operand
 // loads of the tile are then in flight together), else 16.
 template <typename T, typename TB, bool EXTRAP, int TM, int TN, int BK>
 __global__ void __launch_bounds__(256)
@@ -154,8 +154,13 @@ cudaError_t launch_tiles(const GemmDesc& d, int tm, int tn, const T* A, const TB
   // one 64-deep step when the split's contraction fits in it (single-precision tiles only: the
   // FP64 tiles would need 2 x 64 x 68 x 8 = 70 KB of static shared memory at TM = TN = 4)
   if constexpr (sizeof(T) == 4) {
-    if (kper > 16 && kper <= 64) {
+    // one staged step deep enough for the split's contraction, wasting at most half of it
+    if (kper > 32 && kper <= 64) {
       launch_bk<T, TB, EXTRAP, 64>(d, grid, tm, tn, A, B, C, s, Bp, Bs, ctl, omega, skip);
+      return cudaSuccess;
+    }
+    if (kper > 16 && kper <= 32) {
+      launch_bk<T, TB, EXTRAP, 32>(d, grid, tm, tn, A, B, C, s, Bp, Bs, ctl, omega, skip);
       return cudaSuccess;
     }
   }
@@ -181,6 +186,7 @@ void pick_tile(const GemmDesc& d, int& tm, int& tn) {
   tm = 2;
   tn = 2;
 }
+
 
 }  // namespace
 

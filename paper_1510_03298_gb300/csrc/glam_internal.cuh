@@ -85,12 +85,13 @@ cudaError_t launch_gemm(const GemmDesc& d, const T* A, const TB* B, T* C, cudaSt
 
 // ------------------------------------------------------------------------------------
 // Fused bottleneck of Sec. 6.2: per slab i3, S_b[i3] = X2^T (V[i3] (.) (X2 (T_a[i3] X1^T))) X1
-// (the last H stage and the first G stage on-chip; eta never reaches memory).
+// (the last H stage and the first G stage on-chip; eta never reaches memory).  With X3T given,
+// `Ta` is the correction d (p3 x p2p1) and the kernel forms T_a = X_3 d itself.
 // ------------------------------------------------------------------------------------
 template <typename T>
 cudaError_t launch_fused_slab(int n1, int n2, int n3, int p1, int p2, const T* X1T, const T* X2T,
                               const T* Ta, const T* V, T* Sb, cudaStream_t s, const int* skip,
-                              int* err);
+                              int* err, const T* X3T = nullptr, int p3 = 1);
 int fused_slab_supported(int n1, int n2, int p1, int p2, int elem_bytes);
 cudaError_t fused_prepare();
 
