@@ -301,7 +301,8 @@ def measure_details(g, torch, pr, plan, X, Y, W, pen, opts, dev, flush, last):
     per_iter = sum(ms)
     slab = 2 * p2 * p1 * n1 + 4 * n2 * n1 * p2 + n2 * n1 + 2 * p2 * n1 * p1
     fl = slab * n3
-    by = 4 * n + 2 * 4 * n3 * p2 * p1 + 4 * (n1 * p1 + n2 * p2)
+    # read V, the correction d and X_3 (the kernel forms T_a = X_3 d), X_1 and X_2; write S_b
+    by = 4 * n + 4 * n3 * p2 * p1 + 4 * (p + n3 * p3) + 4 * (n1 * p1 + n2 * p2)
     peak_alu = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     t_f = ms[0] / 1e3
     out["roofline"] = {"bound": "alu", "kernel": "fused_slab_kernel<float,20> (G(V(.)H) per slab)",
@@ -330,6 +331,46 @@ def measure_details(g, torch, pr, plan, X, Y, W, pen, opts, dev, flush, last):
                             "status": r64.status, "max_kkt": max(s["kkt"] for s in r64.stats),
                             "fp32_iters_same_lambdas": it32, "fp64_iters": it64}
     plan64.close()
+    out["tf32_path"] = measure_tf32(g, torch, pr, X, Y, W, pen, opts, flush, last, theta, by, peaks, src)
+    return out
+
+
+def measure_tf32(g, torch, pr, X, Y, W, pen, opts, flush, last, theta, by, peaks, src):
+    """The mixed-precision form: the same 50-lambda path with a GLAM_TF32 plan (the bottleneck
+    product on the tensor cores), timed like a bench step, against the FP32 path at the same KKT
+    tolerance; plus the HBM roofline of the tensor-core kernel."""
+    plan = g.Plan(pr.n, pr.p, pr.family, g.GLAM_TF32)
+    r = g.glam_fit_path(plan, X, Y, W, pen, nlambda=pr.nlambda, opts=opts)  # warm-up
+    times, res = [], None
+    for _ in range(2):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        res = g.glam_fit_path(plan, X, Y, W, pen, nlambda=pr.nlambda, opts=opts)
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    ms = min(times)
+    iters = sum(s["inner_iters"] for s in res.stats)
+    ms32 = sum(s["time_ms"] for s in last.stats)
+    q = g.glam_quad_build(plan, X, theta, Y, W)
+    k = g.glam_time_inner_kernels(plan, X, q, reps=100)
+    t_f = k[0] / 1e3
+    F32 = [s["objective"] for s in last.stats]
+    Ftf = [s["objective"] for s in res.stats]
+    out = {"iters_per_s": iters / (ms / 1e3), "ms_per_path": ms, "inner_iters": iters,
+           "fp32_ms_per_path": ms32, "speedup_vs_fp32_path": ms32 / ms,
+           "converged": res.status == g.GLAM_OK, "max_kkt": max(s["kkt"] for s in res.stats),
+           "max_rel_objective_diff_vs_fp32": max(abs(a - b) / abs(b) for a, b in zip(Ftf, F32)),
+           "outer_iters": sum(s["outer_iters"] for s in res.stats),
+           "inner_iteration_ms": {"fused_slab_tc": k[0], "mode3_adj_split": k[2], "prox": k[3],
+                                  "sum": sum(k)},
+           "roofline": {"bound": "hbm", "kernel": "fused_slab_tc_kernel<3,4> (TF32 mma.sync)",
+                        "achieved": by / t_f / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": by / t_f / 1e9 / peaks["hbm_gbs"], "traffic": None,
+                        "bytes_per_launch": by, "ms_per_launch": k[0], "peak_src": src}}
+    plan.close()
     return out
 
 
@@ -362,7 +403,7 @@ def measure_e2e(g, torch, pr, plan, opts, dev, steps):
     return {"value": iters / t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
 
-def run_kernels(reps):
+def run_kernels(reps, precision="fp32"):
     """Diagnostic mode for profilers: build the 128x128x600 plan and launch the four kernels of
     one inner iteration 2 + reps times each (glam_time_inner_kernels); prints their mean times.
     It produces no bench line."""
@@ -374,7 +415,7 @@ def run_kernels(reps):
         gb.build()
     pr = gen.make_workload(1)
     f32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
-    plan = g.Plan(pr.n, pr.p, pr.family, g.GLAM_FP32)
+    plan = g.Plan(pr.n, pr.p, pr.family, g.GLAM_TF32 if precision == "tf32" else g.GLAM_FP32)
     X = [f32(x) for x in pr.XT]
     theta = f32(0.01 * np.random.default_rng(0).standard_normal((pr.p[2], pr.p[1], pr.p[0])))
     q = g.glam_quad_build(plan, X, theta, f32(pr.Y), f32(pr.W))
@@ -393,9 +434,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
     ap.add_argument("--kernels", type=int, default=0, metavar="REPS",
                     help="diagnostic: launch the inner-iteration kernels REPS times for a profiler")
+    ap.add_argument("--kernels-precision", choices=["fp32", "tf32"], default="fp32",
+                    help="plan precision of the --kernels diagnostic")
     args = ap.parse_args()
     if args.kernels > 0:
-        return run_kernels(args.kernels)
+        return run_kernels(args.kernels, args.kernels_precision)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

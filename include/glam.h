@@ -122,8 +122,14 @@ typedef struct {
 int glam_opts_default(glam_opts* opts);
 
 /* Create a plan for one problem shape.  dims: HOST pointer (copied).  family: GLAM_GAUSSIAN_IDENTITY
- * or GLAM_POISSON_LOG.  precision: GLAM_FP64 or GLAM_FP32 (GLAM_TF32 / GLAM_BF16 return
- * GLAM_EINVAL until built).  stream: a cudaStream_t (NULL = legacy default stream) on the
+ * or GLAM_POISSON_LOG.  precision: GLAM_FP64, GLAM_FP32 or GLAM_TF32 (GLAM_BF16 returns
+ * GLAM_EINVAL).  A GLAM_TF32 plan is a GLAM_FP32 plan whose bottleneck product
+ * G(V (.) H(y)) (Sec. 6.2, Eq. twentysixnew: the inner-loop product of glam_prox_step and
+ * glam_fit_path) runs on the tensor cores with TF32 operands (10-bit mantissa, round to
+ * nearest) and FP32 accumulation, for shapes with n1 % 32 == 0, n2 % 8 == 0, p1, p2 <= 32 and
+ * 4 n1 n2 < 2^20 bytes; other shapes, and every other product (glam_predict, glam_gradient,
+ * glam_loss, glam_quad_build, the FP64 passes of glam_fit_path), use the GLAM_FP32 kernels.
+ * stream: a cudaStream_t (NULL = legacy default stream) on the
  * current device.  *out receives the plan.  Allocates the workspace on the current device. */
 int glam_plan_create(const glam_dims* dims, int family, int precision, void* stream, glam_plan** out);
 

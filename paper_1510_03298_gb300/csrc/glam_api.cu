@@ -31,6 +31,7 @@ struct Work {
   T *Yc = nullptr, *Wc = nullptr, *penc = nullptr;
   T* one = nullptr;                        // the 1 x 1 design of a d = 2 problem
   T* dn = nullptr;                         // y - theta_k of the next inner iteration (p)
+  T* yx = nullptr;                         // extrapolated point of a standalone prox step (p)
   bool ready = false;
 };
 
@@ -46,6 +47,7 @@ struct glam_plan {
   int64_t n1 = 1, n2 = 1, n3 = 1, p1 = 1, p2 = 1, p3 = 1, n = 1, p = 1;
   int ksplit = 1;
   bool fused[2] = {false, false};  // [float, double]: the fused slab kernel applies
+  bool tc = false;                 // TF32 plan whose shape the tensor-core fused kernel takes
   std::string err;
   Work<float> wf;
   Work<double> wd;
@@ -194,6 +196,18 @@ struct Ops {
   template <typename TB>
   int XtWX(const TB* x, const TB* xp, const TB* sub, const T* V, const InnerCtl* ctl,
            double omega, const int* skip) {
+    if constexpr (sizeof(T) == 4 && sizeof(TB) == 4) {
+      if (pl->tc && sub == nullptr && ctl == nullptr && fused_tc_pointers_ok(X[0], X[1], w.yx, V)) {
+        // tensor-core kernel: it forms T_a = X_3 y from the extrapolated point itself
+        CK(launch_extrap<T>(pl->p, x, xp, omega, w.yx, s));
+        CK(launch_fused_slab_tc((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2,
+                                (int)pl->p3, X[0], X[1], w.yx, V, w.Sb, s, skip, &pl->sc->timeout,
+                                X[2]));
+        CK(launch_gemm<T, T>(d_mode3_adj(pl, pl->ksplit), X[2], w.Sb, w.Qpart, s, nullptr, nullptr,
+                             nullptr, 0.0, skip));
+        return GLAM_OK;
+      }
+    }
     CK(launch_gemm<T, TB>(d_mode3_fwd(pl), X[2], x, w.Ta, s, xp, sub, ctl, omega, skip));
     if (pl->fused[sizeof(T) == 8 ? 1 : 0]) {
       CK(launch_fused_slab<T>((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2,
@@ -226,6 +240,7 @@ int alloc_work(glam_plan* pl, Work<T>& w, bool full) {
   CKS(dalloc(pl, &w.theta, p));
   CKS(dalloc(pl, &w.grad, p));
   CKS(dalloc(pl, &w.dn, p));
+  CKS(dalloc(pl, &w.yx, p));
   CKS(dalloc(pl, &w.one, 1));
   const T one = T(1);
   CK(cudaMemcpy(w.one, &one, sizeof(T), cudaMemcpyHostToDevice));
@@ -329,8 +344,8 @@ int glam_plan_create(const glam_dims* dims, int family, int precision, void* str
     return fail(nullptr, GLAM_EINVAL, "dims: d = 2 needs n3 = p3 = 1");
   if (family != GLAM_GAUSSIAN_IDENTITY && family != GLAM_POISSON_LOG)
     return fail(nullptr, GLAM_EINVAL, "unknown family");
-  if (precision != GLAM_FP64 && precision != GLAM_FP32)
-    return fail(nullptr, GLAM_EINVAL, "precision: only GLAM_FP64 and GLAM_FP32 are available");
+  if (precision != GLAM_FP64 && precision != GLAM_FP32 && precision != GLAM_TF32)
+    return fail(nullptr, GLAM_EINVAL, "precision: only GLAM_FP64, GLAM_FP32 and GLAM_TF32 are available");
   const int64_t n = dims->n[0] * dims->n[1] * dims->n[2];
   const int64_t p = dims->p[0] * dims->p[1] * dims->p[2];
   if (n > (int64_t)1 << 40 || dims->n[2] * dims->p[1] > 65535LL * 64 || dims->n[2] > 65535)
@@ -363,11 +378,20 @@ int glam_plan_create(const glam_dims* dims, int family, int precision, void* str
   {
     int64_t ks = (pl->n3 + 63) / 64;  // at most 64 rows of i3 per split: one staged K step
     if (ks < 1) ks = 1;
-    if (ks > 16) ks = 16;
+    if (ks > kMaxSplits) ks = kMaxSplits;
     pl->ksplit = (int)ks;
   }
   pl->fused[0] = fused_slab_supported((int)pl->n1, (int)pl->n2, (int)pl->p1, (int)pl->p2, 4) != 0;
   pl->fused[1] = fused_slab_supported((int)pl->n1, (int)pl->n2, (int)pl->p1, (int)pl->p2, 8) != 0;
+  if (precision == GLAM_TF32) {
+    const cudaError_t e = fused_tc_prepare();
+    if (e != cudaSuccess) {
+      pl->err = std::string("tensor-core kernel set-up (cudaFuncSetAttribute): ") + cudaGetErrorString(e);
+      return bail(GLAM_ECUDA);
+    }
+    pl->tc = fused_tc_supported((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2,
+                                (int)pl->p3) != 0;
+  }
   int st;
   if (precision == GLAM_FP64) {
     if ((st = alloc_work<double>(pl, pl->wd, true)) != GLAM_OK) return bail(st);
@@ -678,12 +702,22 @@ int capture_chunk(Fit<T>& f) {
   for (int it = 0; it < C && st == GLAM_OK; ++it) {
     double* x = (it % 2 == 0) ? pl->x0 : pl->x1;
     double* xp = (it % 2 == 0) ? pl->x1 : pl->x0;
-    if (pl->fused[sizeof(T) == 8 ? 1 : 0]) {
+    bool use_tc = false;
+    if constexpr (sizeof(T) == 4)
+      use_tc = pl->tc && fused_tc_pointers_ok(op.X[0], op.X[1], op.w.dn, op.w.V);
+    if (pl->fused[sizeof(T) == 8 ? 1 : 0] || use_tc) {
       // the fused kernel forms T_a = X_3 d from the correction itself, then the split adjoint
-      cudaError_t e = launch_fused_slab<T>((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1,
-                                           (int)pl->p2, op.X[0], op.X[1], op.w.dn, op.w.V, op.w.Sb,
-                                           f.s, &pl->ctl->done, &pl->sc->timeout, op.X[2],
-                                           (int)pl->p3);
+      cudaError_t e = cudaSuccess;
+      if constexpr (sizeof(T) == 4) {
+        if (use_tc)
+          e = launch_fused_slab_tc((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2,
+                                   (int)pl->p3, op.X[0], op.X[1], op.w.dn, op.w.V, op.w.Sb, f.s,
+                                   &pl->ctl->done, &pl->sc->timeout, op.X[2]);
+      }
+      if (!use_tc)
+        e = launch_fused_slab<T>((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2,
+                                 op.X[0], op.X[1], op.w.dn, op.w.V, op.w.Sb, f.s, &pl->ctl->done,
+                                 &pl->sc->timeout, op.X[2], (int)pl->p3);
       if (e == cudaSuccess)
         e = launch_gemm<T, T>(d_mode3_adj(pl, pl->ksplit), op.X[2], op.w.Sb, op.w.Qpart, f.s, nullptr,
                               nullptr, nullptr, 0.0, &pl->ctl->done);
@@ -956,17 +990,28 @@ int time_inner_impl(glam_plan* pl, const void* const X[3], const glam_quad* q, i
   const int slot = sizeof(T) == 8 ? 1 : 0;
   auto timed = [&](int which) -> int {
     ms[which] = 0.0;
-    if (which == 0 && !pl->fused[slot]) return GLAM_OK;
+    bool use_tc = false;
+    if constexpr (sizeof(T) == 4) use_tc = pl->tc && fused_tc_pointers_ok(op.X[0], op.X[1], op.w.dn, V);
+    const bool fused = pl->fused[slot] || use_tc;
+    if (which == 0 && !fused) return GLAM_OK;
     for (int r = -2; r < reps; ++r) {
       if (r == 0) CK(cudaEventRecord(a, pl->stream));
       switch (which) {
         case 0:
+          if constexpr (sizeof(T) == 4) {
+            if (use_tc) {
+              CK(launch_fused_slab_tc((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1,
+                                      (int)pl->p2, (int)pl->p3, op.X[0], op.X[1], op.w.dn, V,
+                                      op.w.Sb, pl->stream, nullptr, &pl->sc->timeout, op.X[2]));
+              break;
+            }
+          }
           CK(launch_fused_slab<T>((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2,
                                   op.X[0], op.X[1], op.w.dn, V, op.w.Sb, pl->stream, nullptr,
                                   &pl->sc->timeout, op.X[2], (int)pl->p3));
           break;
         case 1:
-          if (pl->fused[slot]) return GLAM_OK;  // folded into the fused kernel
+          if (fused) return GLAM_OK;  // folded into the fused kernel
           CK(launch_gemm<T, T>(d_mode3_fwd(pl), op.X[2], op.w.dn, op.w.Ta, pl->stream));
           break;
         case 2:

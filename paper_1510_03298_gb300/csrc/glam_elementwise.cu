@@ -240,6 +240,15 @@ __global__ void convert_kernel(int64_t n, const TI* __restrict__ in, TO* __restr
     out[i] = (TO)in[i];
 }
 
+// y = x + omega (x - x_prev) (the FISTA extrapolation of Sec. 3.2), x_prev may be NULL
+template <typename T>
+__global__ void extrap_kernel(int64_t n, const T* __restrict__ x, const T* __restrict__ xp,
+                              double omega, T* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = xp ? (T)((double)x[i] + omega * ((double)x[i] - (double)xp[i])) : x[i];
+}
+
 template <typename T>
 __global__ void sum_splits_kernel(int64_t p, int ksplit, const T* __restrict__ part, T* __restrict__ out) {
   for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < p;
@@ -289,7 +298,14 @@ prox_kernel(int64_t p, int ksplit, const Tq* __restrict__ Qpart, const TP* __res
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   TP q0 = TP(0), lin0 = TP(0), x0 = TP(0), xp0 = TP(0), pw0 = TP(0), an0 = TP(0);
   if (m0 < p) {
-    for (int s = 0; s < ksplit; ++s) q0 += TP(Qpart[(int64_t)s * p + m0]);
+    // every split partial is loaded before the first add (one memory round trip); the adds
+    // then run in split order
+    Tq qv[kMaxSplits];
+#pragma unroll
+    for (int s = 0; s < kMaxSplits; ++s) qv[s] = s < ksplit ? Qpart[(int64_t)s * p + m0] : Tq(0);
+#pragma unroll
+    for (int s = 0; s < kMaxSplits; ++s)
+      if (s < ksplit) q0 += TP(qv[s]);
     lin0 = lin[m0];
     x0 = x[m0];
     xp0 = xprev[m0];
@@ -651,6 +667,13 @@ cudaError_t launch_convert(int64_t n, const TI* in, TO* out, cudaStream_t s) {
 }
 
 template <typename T>
+cudaError_t launch_extrap(int64_t n, const T* x, const T* xp, double omega, T* y, cudaStream_t s) {
+  extrap_kernel<T><<<grid_for(n), kThreads, 0, s>>>(n, x, xp, omega, y);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_sum_splits(int64_t p, int ksplit, const T* part, T* out, cudaStream_t s) {
   sum_splits_kernel<T><<<grid_for(p), kThreads, 0, s>>>(p, ksplit, part, out);
   count_launches(1);
@@ -676,6 +699,7 @@ cudaError_t launch_prox(int64_t p, int ksplit, const Tq* Qpart, const TP* lin, d
                         const TP* x, const TP* xprev, const TP* pen_w, TP* out, double inv_n,
                         InnerCtl* ctl, double omega, double delta, double lambda,
                         const double* Lhat, cudaStream_t s, Tq* dnext, const TP* anchor) {
+  if (ksplit < 1 || ksplit > kMaxSplits) return cudaErrorInvalidValue;
   int blocks = (int)((p + kThreads - 1) / kThreads);
   if (blocks < 1) blocks = 1;
   if (blocks > 4 * num_sms()) blocks = 4 * num_sms();
@@ -808,5 +832,6 @@ template cudaError_t launch_convert<float, double>(int64_t, const float*, double
 template cudaError_t launch_convert<double, float>(int64_t, const double*, float*, cudaStream_t);
 template cudaError_t launch_convert<double, double>(int64_t, const double*, double*, cudaStream_t);
 template cudaError_t launch_convert<float, float>(int64_t, const float*, float*, cudaStream_t);
+template cudaError_t launch_extrap<float>(int64_t, const float*, const float*, double, float*, cudaStream_t);
 
 }  // namespace glam

@@ -25,6 +25,7 @@
 #include <cstdint>
 
 #include "glam_internal.cuh"
+#include "glam_stage.cuh"
 #include "glam_tma.cuh"
 
 namespace glam {
@@ -174,20 +175,35 @@ fused_slab_kernel(SlabShape sh, const T* __restrict__ X1T, const T* __restrict__
   const int tid = threadIdx.x, nth = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31;
 
-  for (int idx = tid; idx < p2 * n2; idx += nth) {  // coalesced read of X_2^T rows
-    const int j2 = idx / n2, i2 = idx - j2 * n2;
-    X2s[i2 * P + j2] = X2T[idx];
+  // the first two V slabs are requested before the prologue, so they arrive while it runs
+  if (tid == 0) {
+    timed_out = 0;
+    if (STAGE) {
+      mbar_init(&mbar[0], 1);
+      mbar_init(&mbar[1], 1);
+      fence_mbar_init();
+      for (int b = 0; b < 2; ++b) {
+        const int s0 = blockIdx.x + b * gridDim.x;
+        if (s0 < n3) {
+          mbar_expect_tx(&mbar[b], sh.vbytes);
+          bulk_g2s(Vbuf + b * nv, V + (int64_t)s0 * nv, sh.vbytes, &mbar[b]);
+        }
+      }
+    }
   }
+  stage::load_each<8>(p2 * n2, X2T, [&](int idx, T x) {  // coalesced read of X_2^T rows
+    const int j2 = idx / n2, i2 = idx - j2 * n2;
+    X2s[i2 * P + j2] = x;
+  });
   for (int idx = tid; idx < n2 * (P - p2); idx += nth) {
     const int i2 = idx / (P - p2), j2 = p2 + idx - i2 * (P - p2);
     X2s[i2 * P + j2] = T(0);
   }
-  for (int idx = tid; idx < p1 * n1; idx += nth) {
+  stage::load_each<8>(p1 * n1, X1T, [&](int idx, T x) {
     const int j1 = idx / n1, i1 = idx - j1 * n1;
-    const T x = X1T[idx];
     X1s[j1 * LD + i1] = x;
     X1c[i1 * Q1P + j1] = x;
-  }
+  });
   for (int idx = tid; idx < n1 * (Q1 - p1); idx += nth) {
     const int i1 = idx / (Q1 - p1), j1 = p1 + idx - i1 * (Q1 - p1);
     X1c[i1 * Q1P + j1] = T(0);
@@ -202,24 +218,7 @@ fused_slab_kernel(SlabShape sh, const T* __restrict__ X1T, const T* __restrict__
     }
     __syncthreads();
     // T_a(s_k, n) = sum_j3 X_3(s_k, j3) d(j3, n): columns n over the threads, slabs in chunks of 4
-    for (int n = tid; n < P21; n += nth) {
-      for (int k0 = 0; k0 < kcta; k0 += 4) {
-        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-        const T* x0r = X3r + (int64_t)k0 * p3;
-#pragma unroll 4
-        for (int j3 = 0; j3 < p3; ++j3) {
-          const T dv = Ta[(int64_t)j3 * P21 + n];
-          a0 = fma(x0r[j3], dv, a0);
-          if (k0 + 1 < kcta) a1 = fma(x0r[p3 + j3], dv, a1);
-          if (k0 + 2 < kcta) a2 = fma(x0r[2 * p3 + j3], dv, a2);
-          if (k0 + 3 < kcta) a3 = fma(x0r[3 * p3 + j3], dv, a3);
-        }
-        TaAll[(int64_t)k0 * P21 + n] = a0;
-        if (k0 + 1 < kcta) TaAll[(int64_t)(k0 + 1) * P21 + n] = a1;
-        if (k0 + 2 < kcta) TaAll[(int64_t)(k0 + 2) * P21 + n] = a2;
-        if (k0 + 3 < kcta) TaAll[(int64_t)(k0 + 3) * P21 + n] = a3;
-      }
-    }
+    stage::form_ta<16>(kcta, p3, P21, Ta, X3r, TaAll);
     __syncthreads();
   }
   // T_a of the first slab
@@ -230,24 +229,7 @@ fused_slab_kernel(SlabShape sh, const T* __restrict__ X1T, const T* __restrict__
       TaT[idx] = (j2 < p2) ? ta[j2 * p1 + j1] : T(0);
     }
   }
-  if (tid == 0) {
-    timed_out = 0;
-    if (STAGE) {
-      mbar_init(&mbar[0], 1);
-      mbar_init(&mbar[1], 1);
-      fence_mbar_init();
-    }
-  }
   __syncthreads();
-  if (STAGE && tid == 0) {
-    for (int b = 0; b < 2; ++b) {
-      const int s0 = blockIdx.x + b * gridDim.x;
-      if (s0 < n3) {
-        mbar_expect_tx(&mbar[b], sh.vbytes);
-        bulk_g2s(Vbuf + b * nv, V + (int64_t)s0 * nv, sh.vbytes, &mbar[b]);
-      }
-    }
-  }
 
   // warp roles in phase 2: column tile ct (32 columns i1), row group rg (rows i2 in [r0, r1))
   const int ct = warp % sh.CT, rg = warp / sh.CT;

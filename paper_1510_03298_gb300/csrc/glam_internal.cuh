@@ -18,6 +18,7 @@ constexpr int kThreads = 256;
 constexpr int kTrials = 8;          // Armijo trial step sizes evaluated per n-stream pass
 constexpr int kMaxRedBlocks = 1216; // 8 x 152 SMs: upper bound of blocks in a reduction grid
 constexpr int kRedSlots = 2 * kTrials + 4;
+constexpr int kMaxSplits = 16;      // split-K partials of the last G stage (mode 3), at most
 
 // ------------------------------------------------------------------------------------
 // Device-resident control of the inner PG loop (Sec. 3.2).  One instance per plan; every
@@ -95,6 +96,17 @@ cudaError_t launch_fused_slab(int n1, int n2, int n3, int p1, int p2, const T* X
 int fused_slab_supported(int n1, int n2, int p1, int p2, int elem_bytes);
 cudaError_t fused_prepare();
 
+// The same product on tensor cores (TF32 operands, FP32 accumulation), always forming
+// T_a = X_3 d from the correction D (p3 x p2p1); fused_tc_supported tells whether the shape
+// is in the kernel's domain.
+cudaError_t launch_fused_slab_tc(int n1, int n2, int n3, int p1, int p2, int p3, const float* X1T,
+                                 const float* X2T, const float* D, const float* V, float* Sb,
+                                 cudaStream_t s, const int* skip, int* err, const float* X3T);
+int fused_tc_supported(int n1, int n2, int n3, int p1, int p2, int p3);
+// the kernel bulk-copies X_1^T, X_2^T, D and V: each must start on a 16-byte boundary
+int fused_tc_pointers_ok(const float* X1T, const float* X2T, const float* D, const float* V);
+cudaError_t fused_tc_prepare();
+
 // ------------------------------------------------------------------------------------
 // Elementwise / reduction kernels.
 // ------------------------------------------------------------------------------------
@@ -143,6 +155,9 @@ cudaError_t launch_lambda_max(int64_t p, const double* g0, const T* pen_w, DevSc
 
 template <typename TI, typename TO>
 cudaError_t launch_convert(int64_t n, const TI* in, TO* out, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_extrap(int64_t n, const T* x, const T* xp, double omega, T* y, cudaStream_t s);
 
 cudaError_t launch_gram(int nj, int pj, const double* XT, double* gram, cudaStream_t s);
 
