@@ -47,7 +47,9 @@ struct glam_plan {
   int64_t n1 = 1, n2 = 1, n3 = 1, p1 = 1, p2 = 1, p3 = 1, n = 1, p = 1;
   int ksplit = 1;
   bool fused[2] = {false, false};  // [float, double]: the fused slab kernel applies
-  bool tc = false;                 // TF32 plan whose shape the tensor-core fused kernel takes
+  // form of the tensor-core fused kernel for this plan: 1 (TF32 plans: TF32 operands), 3 (FP32
+  // plans: 3xTF32, about FP32 accuracy), 0 when the shape is outside its domain or the plan is FP64
+  int tc_split = 0;
   std::string err;
   Work<float> wf;
   Work<double> wd;
@@ -197,12 +199,12 @@ struct Ops {
   int XtWX(const TB* x, const TB* xp, const TB* sub, const T* V, const InnerCtl* ctl,
            double omega, const int* skip) {
     if constexpr (sizeof(T) == 4 && sizeof(TB) == 4) {
-      if (pl->tc && sub == nullptr && ctl == nullptr && fused_tc_pointers_ok(X[0], X[1], w.yx, V)) {
+      if (pl->tc_split && sub == nullptr && ctl == nullptr && fused_tc_pointers_ok(X[0], X[1], w.yx, V)) {
         // tensor-core kernel: it forms T_a = X_3 y from the extrapolated point itself
         CK(launch_extrap<T>(pl->p, x, xp, omega, w.yx, s));
         CK(launch_fused_slab_tc((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2,
                                 (int)pl->p3, X[0], X[1], w.yx, V, w.Sb, s, skip, &pl->sc->timeout,
-                                X[2]));
+                                X[2], pl->tc_split));
         CK(launch_gemm<T, T>(d_mode3_adj(pl, pl->ksplit), X[2], w.Sb, w.Qpart, s, nullptr, nullptr,
                              nullptr, 0.0, skip));
         return GLAM_OK;
@@ -383,14 +385,16 @@ int glam_plan_create(const glam_dims* dims, int family, int precision, void* str
   }
   pl->fused[0] = fused_slab_supported((int)pl->n1, (int)pl->n2, (int)pl->p1, (int)pl->p2, 4) != 0;
   pl->fused[1] = fused_slab_supported((int)pl->n1, (int)pl->n2, (int)pl->p1, (int)pl->p2, 8) != 0;
-  if (precision == GLAM_TF32) {
+  if (precision != GLAM_FP64) {
     const cudaError_t e = fused_tc_prepare();
     if (e != cudaSuccess) {
       pl->err = std::string("tensor-core kernel set-up (cudaFuncSetAttribute): ") + cudaGetErrorString(e);
       return bail(GLAM_ECUDA);
     }
-    pl->tc = fused_tc_supported((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2,
-                                (int)pl->p3) != 0;
+    const int split = precision == GLAM_TF32 ? 1 : 3;
+    if (fused_tc_supported((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2, (int)pl->p3,
+                           split))
+      pl->tc_split = split;
   }
   int st;
   if (precision == GLAM_FP64) {
@@ -704,7 +708,7 @@ int capture_chunk(Fit<T>& f) {
     double* xp = (it % 2 == 0) ? pl->x1 : pl->x0;
     bool use_tc = false;
     if constexpr (sizeof(T) == 4)
-      use_tc = pl->tc && fused_tc_pointers_ok(op.X[0], op.X[1], op.w.dn, op.w.V);
+      use_tc = pl->tc_split && fused_tc_pointers_ok(op.X[0], op.X[1], op.w.dn, op.w.V);
     if (pl->fused[sizeof(T) == 8 ? 1 : 0] || use_tc) {
       // the fused kernel forms T_a = X_3 d from the correction itself, then the split adjoint
       cudaError_t e = cudaSuccess;
@@ -712,7 +716,7 @@ int capture_chunk(Fit<T>& f) {
         if (use_tc)
           e = launch_fused_slab_tc((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2,
                                    (int)pl->p3, op.X[0], op.X[1], op.w.dn, op.w.V, op.w.Sb, f.s,
-                                   &pl->ctl->done, &pl->sc->timeout, op.X[2]);
+                                   &pl->ctl->done, &pl->sc->timeout, op.X[2], pl->tc_split);
       }
       if (!use_tc)
         e = launch_fused_slab<T>((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2,
@@ -991,7 +995,7 @@ int time_inner_impl(glam_plan* pl, const void* const X[3], const glam_quad* q, i
   auto timed = [&](int which) -> int {
     ms[which] = 0.0;
     bool use_tc = false;
-    if constexpr (sizeof(T) == 4) use_tc = pl->tc && fused_tc_pointers_ok(op.X[0], op.X[1], op.w.dn, V);
+    if constexpr (sizeof(T) == 4) use_tc = pl->tc_split && fused_tc_pointers_ok(op.X[0], op.X[1], op.w.dn, V);
     const bool fused = pl->fused[slot] || use_tc;
     if (which == 0 && !fused) return GLAM_OK;
     for (int r = -2; r < reps; ++r) {
@@ -1002,7 +1006,8 @@ int time_inner_impl(glam_plan* pl, const void* const X[3], const glam_quad* q, i
             if (use_tc) {
               CK(launch_fused_slab_tc((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1,
                                       (int)pl->p2, (int)pl->p3, op.X[0], op.X[1], op.w.dn, V,
-                                      op.w.Sb, pl->stream, nullptr, &pl->sc->timeout, op.X[2]));
+                                      op.w.Sb, pl->stream, nullptr, &pl->sc->timeout, op.X[2],
+                                      pl->tc_split));
               break;
             }
           }

@@ -59,6 +59,51 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+// An MMA operand element as TF32 bits: the rounded value alone (SPLIT = 1), or the pair
+// hi + lo of the 3xTF32 form (SPLIT = 3): hi = tf32(x), lo = tf32(x - hi), so hi + lo carries about
+// 21 significant bits of x.
+template <int SPLIT>
+struct Tf {
+  uint32_t h, l;
+};
+// from an FP32 value
+template <int SPLIT>
+__device__ __forceinline__ Tf<SPLIT> tf_of(float x) {
+  Tf<SPLIT> r;
+  r.h = to_tf32(x);
+  r.l = SPLIT == 3 ? to_tf32(x - __uint_as_float(r.h)) : 0u;
+  return r;
+}
+// from a value stored in shared memory: already TF32 when SPLIT = 1, FP32 when SPLIT = 3
+template <int SPLIT>
+__device__ __forceinline__ Tf<SPLIT> tf_stored(float x) {
+  if constexpr (SPLIT == 1) {
+    Tf<SPLIT> r;
+    r.h = __float_as_uint(x);
+    r.l = 0u;
+    return r;
+  } else {
+    return tf_of<SPLIT>(x);
+  }
+}
+// shared-memory form of a constant operand
+template <int SPLIT>
+__device__ __forceinline__ float tf_store(float x) {
+  return SPLIT == 1 ? __uint_as_float(to_tf32(x)) : x;
+}
+// D += A B; the 3xTF32 form adds the two cross terms before the main one (hi lo' + lo hi' + hi hi';
+// the lo lo' term, below 2^-22 of the product, is dropped)
+template <int SPLIT>
+__device__ __forceinline__ void mma_x(float (&d)[4], const Tf<SPLIT>& a0, const Tf<SPLIT>& a1,
+                                      const Tf<SPLIT>& a2, const Tf<SPLIT>& a3, const Tf<SPLIT>& b0,
+                                      const Tf<SPLIT>& b1) {
+  if constexpr (SPLIT == 3) {
+    mma_tf32(d, a0.h, a1.h, a2.h, a3.h, b0.l, b1.l);
+    mma_tf32(d, a0.l, a1.l, a2.l, a3.l, b0.h, b1.h);
+  }
+  mma_tf32(d, a0.h, a1.h, a2.h, a3.h, b0.h, b1.h);
+}
+
 struct TcShape {
   int n1, n2, n3, p1, p2, p3;
   int CG, IG;  // column groups (16 NCT columns each) and row groups of the warps
@@ -135,13 +180,15 @@ __device__ __forceinline__ void issue_slab(float* vbuf_b, const CUtensorMap* tma
   }
 }
 
-template <int NCT>
+// block size limit of a tiling: the 3xTF32 form keeps hi and lo of the register operands, so it
+// runs with at most 256 threads (255 registers each)
+template <int NCT, int SPLIT>
 constexpr int tc_max_threads() {
-  return NCT == 4 ? 256 : (NCT == 2 ? 384 : 512);
+  return SPLIT == 3 ? 256 : (NCT == 4 ? 256 : (NCT == 2 ? 384 : 512));
 }
 
-template <int NB, int NCT>
-__global__ void __launch_bounds__(tc_max_threads<NCT>(), 1)
+template <int NB, int NCT, int SPLIT>
+__global__ void __launch_bounds__(tc_max_threads<NCT, SPLIT>(), 1)
 fused_slab_tc_kernel(TcShape sh, const float* __restrict__ X1T, const float* __restrict__ X2T,
                      const float* __restrict__ D, const __grid_constant__ CUtensorMap tmapV,
                      float* __restrict__ Sb, const int* __restrict__ skip, int* __restrict__ err,
@@ -211,24 +258,24 @@ fused_slab_tc_kernel(TcShape sh, const float* __restrict__ X1T, const float* __r
   // constant operands, rounded to TF32, from the staged copies
   for (int i = tid; i < p2 * n2; i += nth) {  // X_2^T is (p2, n2)
     const int j2 = i / n2, i2 = i - j2 * n2;
-    const float r = __uint_as_float(to_tf32(sX2[i]));
+    const float r = tf_store<SPLIT>(sX2[i]);
     X2t[i2 * KP + j2] = r;
     X2n[j2 * NP + i2] = r;
   }
   for (int i = tid; i < p1 * n1; i += nth) {  // X_1^T is (p1, n1)
     const int j1 = i / n1, c = i - j1 * n1;
-    X1s[j1 * LDc + c] = __uint_as_float(to_tf32(sX1[i]));
+    X1s[j1 * LDc + c] = tf_store<SPLIT>(sX1[i]);
   }
   // MMA0's A operand X_1(c, j1) for this warp's 16-row tile of c, kept in registers
   const bool mma0_warp = warp < n1 / 16;
-  uint32_t xa[NB][4];
+  Tf<SPLIT> xa[NB][4];
 #pragma unroll
   for (int s = 0; s < NB; ++s) {
     const int c = 16 * warp + g, j0 = 8 * s + t, j4 = j0 + 4;
-    xa[s][0] = (mma0_warp && j0 < p1) ? to_tf32(sX1[j0 * n1 + c]) : 0u;
-    xa[s][1] = (mma0_warp && j0 < p1) ? to_tf32(sX1[j0 * n1 + c + 8]) : 0u;
-    xa[s][2] = (mma0_warp && j4 < p1) ? to_tf32(sX1[j4 * n1 + c]) : 0u;
-    xa[s][3] = (mma0_warp && j4 < p1) ? to_tf32(sX1[j4 * n1 + c + 8]) : 0u;
+    xa[s][0] = tf_of<SPLIT>((mma0_warp && j0 < p1) ? sX1[j0 * n1 + c] : 0.f);
+    xa[s][1] = tf_of<SPLIT>((mma0_warp && j0 < p1) ? sX1[j0 * n1 + c + 8] : 0.f);
+    xa[s][2] = tf_of<SPLIT>((mma0_warp && j4 < p1) ? sX1[j4 * n1 + c] : 0.f);
+    xa[s][3] = tf_of<SPLIT>((mma0_warp && j4 < p1) ? sX1[j4 * n1 + c + 8] : 0.f);
   }
   // ---- first H stage for this CTA's slabs: T_a(s_k, :) = sum_j3 X_3(s_k, j3) d(j3, :), summed
   // in j3 order into TaS (FP32), chunk by chunk of staged rows of d ----
@@ -294,12 +341,14 @@ fused_slab_tc_kernel(TcShape sh, const float* __restrict__ X1T, const float* __r
     }
   }
   __syncthreads();  // every chunk is summed
-  // T_a to TF32 in place, then the V buffers are free
-  for (int n = tid; n < P21; n += nth) {
-    const int j2 = n / p1, j1 = n - j2 * p1;
-    for (int k = 0; k < kcta; ++k) {
-      float* e = TaS + k * K8 * QT + j2 * QT + j1;
-      *e = __uint_as_float(to_tf32(*e));
+  // T_a to its stored form in place (TF32 when SPLIT = 1), then the V buffers are free
+  if constexpr (SPLIT == 1) {
+    for (int n = tid; n < P21; n += nth) {
+      const int j2 = n / p1, j1 = n - j2 * p1;
+      for (int k = 0; k < kcta; ++k) {
+        float* e = TaS + k * K8 * QT + j2 * QT + j1;
+        *e = tf_store<SPLIT>(*e);
+      }
     }
   }
   __syncthreads();
@@ -340,13 +389,12 @@ fused_slab_tc_kernel(TcShape sh, const float* __restrict__ X1T, const float* __r
 #pragma unroll
       for (int s = 0; s < NB; ++s) {
         const float* tb = TaK + (8 * nb + g) * QT + 8 * s + t;
-        mma_tf32(acc, xa[s][0], xa[s][1], xa[s][2], xa[s][3], __float_as_uint(tb[0]),
-                 __float_as_uint(tb[4]));
+        mma_x<SPLIT>(acc, xa[s][0], xa[s][1], xa[s][2], xa[s][3], tf_stored<SPLIT>(tb[0]),
+                     tf_stored<SPLIT>(tb[4]));
       }
       // C (c, j2 = 8 nb + {2t, 2t+1}) -> A (c, K slot t <-> 2t, slot t + 4 <-> 2t + 1)
-      TbF[(warp * NB + nb) * 32 + lane] =
-          make_float4(__uint_as_float(to_tf32(acc[0])), __uint_as_float(to_tf32(acc[2])),
-                      __uint_as_float(to_tf32(acc[1])), __uint_as_float(to_tf32(acc[3])));
+      TbF[(warp * NB + nb) * 32 + lane] = make_float4(tf_store<SPLIT>(acc[0]), tf_store<SPLIT>(acc[2]),
+                                                      tf_store<SPLIT>(acc[1]), tf_store<SPLIT>(acc[3]));
     }
   };
   if (!timed_out) mma0(0);  // T_a is rounded: the barrier before the V requests orders it
@@ -362,16 +410,16 @@ fused_slab_tc_kernel(TcShape sh, const float* __restrict__ X1T, const float* __r
     if (timed_out) break;
     const float* Vs = Vbuf + (int64_t)b * nv;
     if (main_warp) {
-    uint32_t a1f[NCT][NB][4];
+    Tf<SPLIT> a1f[NCT][NB][4];
 #pragma unroll
     for (int ct = 0; ct < NCT; ++ct)
 #pragma unroll
       for (int nb = 0; nb < NB; ++nb) {
         const float4 f = TbF[((c0w / 16 + ct) * NB + nb) * 32 + lane];
-        a1f[ct][nb][0] = __float_as_uint(f.x);
-        a1f[ct][nb][1] = __float_as_uint(f.y);
-        a1f[ct][nb][2] = __float_as_uint(f.z);
-        a1f[ct][nb][3] = __float_as_uint(f.w);
+        a1f[ct][nb][0] = tf_stored<SPLIT>(f.x);
+        a1f[ct][nb][1] = tf_stored<SPLIT>(f.y);
+        a1f[ct][nb][2] = tf_stored<SPLIT>(f.z);
+        a1f[ct][nb][3] = tf_stored<SPLIT>(f.w);
       }
     float c2[MT][NCT][2][4];  // S(j2, c): [j2 tile][column tile][column half][fragment]
 #pragma unroll
@@ -394,35 +442,35 @@ fused_slab_tc_kernel(TcShape sh, const float* __restrict__ X1T, const float* __r
 #pragma unroll
       for (int ks = 0; ks < NB; ++ks) {
         const float2 bv = *reinterpret_cast<const float2*>(X2t + (i0 + g) * KP + 8 * ks + 2 * t);
+        const Tf<SPLIT> b0 = tf_stored<SPLIT>(bv.x), b1 = tf_stored<SPLIT>(bv.y);
 #pragma unroll
         for (int ct = 0; ct < NCT; ++ct)
-          mma_tf32(c1[ct], a1f[ct][ks][0], a1f[ct][ks][1], a1f[ct][ks][2], a1f[ct][ks][3],
-                   __float_as_uint(bv.x), __float_as_uint(bv.y));
+          mma_x<SPLIT>(c1[ct], a1f[ct][ks][0], a1f[ct][ks][1], a1f[ct][ks][2], a1f[ct][ks][3], b0, b1);
       }
       // ---- r = V (.) eta as MMA2 B fragments (K = i2 permuted, N = c) ----
-      uint32_t b2f[NCT][2][2];
+      Tf<SPLIT> b2f[NCT][2][2];
       const float* vrow = Vs + (int64_t)(c0w >> 5) * n2 * 32 + (i0 + 2 * t) * 32;
 #pragma unroll
       for (int ct = 0; ct < NCT; ++ct) {
         const float* vs = vrow + (int64_t)(ct >> 1) * n2 * 32;
         const int kq = 2 * (ct & 1);
-        b2f[ct][0][0] = to_tf32(vs[vofs[kq][0]] * c1[ct][0]);           // (c,     i0 + 2t)
-        b2f[ct][0][1] = to_tf32(vs[32 + vofs[kq][1]] * c1[ct][1]);      // (c,     i0 + 2t + 1)
-        b2f[ct][1][0] = to_tf32(vs[vofs[kq + 1][0]] * c1[ct][2]);       // (c + 8, i0 + 2t)
-        b2f[ct][1][1] = to_tf32(vs[32 + vofs[kq + 1][1]] * c1[ct][3]);  // (c + 8, i0 + 2t + 1)
+        b2f[ct][0][0] = tf_of<SPLIT>(vs[vofs[kq][0]] * c1[ct][0]);           // (c,     i0 + 2t)
+        b2f[ct][0][1] = tf_of<SPLIT>(vs[32 + vofs[kq][1]] * c1[ct][1]);      // (c,     i0 + 2t + 1)
+        b2f[ct][1][0] = tf_of<SPLIT>(vs[vofs[kq + 1][0]] * c1[ct][2]);       // (c + 8, i0 + 2t)
+        b2f[ct][1][1] = tf_of<SPLIT>(vs[32 + vofs[kq + 1][1]] * c1[ct][3]);  // (c + 8, i0 + 2t + 1)
       }
       // ---- MMA2: S(j2, c) += X_2^T(j2, i2) r(i2, c) ----
 #pragma unroll
       for (int mt = 0; mt < MT; ++mt) {
         const float2 lo = *reinterpret_cast<const float2*>(X2n + (16 * mt + g) * NP + i0 + 2 * t);
         const float2 hi = *reinterpret_cast<const float2*>(X2n + (16 * mt + g + 8) * NP + i0 + 2 * t);
-        const uint32_t a0 = __float_as_uint(lo.x), a2 = __float_as_uint(lo.y);
-        const uint32_t a1 = __float_as_uint(hi.x), a3 = __float_as_uint(hi.y);
+        const Tf<SPLIT> a0 = tf_stored<SPLIT>(lo.x), a2 = tf_stored<SPLIT>(lo.y);
+        const Tf<SPLIT> a1 = tf_stored<SPLIT>(hi.x), a3 = tf_stored<SPLIT>(hi.y);
 #pragma unroll
         for (int ct = 0; ct < NCT; ++ct)
 #pragma unroll
           for (int h = 0; h < 2; ++h)
-            mma_tf32(c2[mt][ct][h], a0, a1, a2, a3, b2f[ct][h][0], b2f[ct][h][1]);
+            mma_x<SPLIT>(c2[mt][ct][h], a0, a1, a2, a3, b2f[ct][h][0], b2f[ct][h][1]);
       }
     }
     // ---- MMA3: S_b(j2, j1) += S(j2, c) X_1(c, j1); A from S with the permuted K = c ----
@@ -438,19 +486,19 @@ fused_slab_tc_kernel(TcShape sh, const float* __restrict__ X1T, const float* __r
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int cb = c0w + 16 * ct + 8 * h + 2 * t;
-        uint32_t bx[NB][2];
+        Tf<SPLIT> bx[NB][2];
 #pragma unroll
         for (int nj = 0; nj < NB; ++nj) {
           const float2 bv = *reinterpret_cast<const float2*>(X1s + (8 * nj + g) * LDc + cb);
-          bx[nj][0] = __float_as_uint(bv.x);
-          bx[nj][1] = __float_as_uint(bv.y);
+          bx[nj][0] = tf_stored<SPLIT>(bv.x);
+          bx[nj][1] = tf_stored<SPLIT>(bv.y);
         }
 #pragma unroll
         for (int mt = 0; mt < MT; ++mt) {
-          const uint32_t a0 = to_tf32(c2[mt][ct][h][0]), a1 = to_tf32(c2[mt][ct][h][2]);
-          const uint32_t a2 = to_tf32(c2[mt][ct][h][1]), a3 = to_tf32(c2[mt][ct][h][3]);
+          const Tf<SPLIT> a0 = tf_of<SPLIT>(c2[mt][ct][h][0]), a1 = tf_of<SPLIT>(c2[mt][ct][h][2]);
+          const Tf<SPLIT> a2 = tf_of<SPLIT>(c2[mt][ct][h][1]), a3 = tf_of<SPLIT>(c2[mt][ct][h][3]);
 #pragma unroll
-          for (int nj = 0; nj < NB; ++nj) mma_tf32(c3[mt][nj], a0, a1, a2, a3, bx[nj][0], bx[nj][1]);
+          for (int nj = 0; nj < NB; ++nj) mma_x<SPLIT>(c3[mt][nj], a0, a1, a2, a3, bx[nj][0], bx[nj][1]);
         }
       }
     // this warp's partial S_b (rows j2 < p2, columns j1 < p1)
@@ -505,7 +553,8 @@ size_t tc_smem_bytes(int NB, const TcShape& sh, int nwarps) {
 // (NCT column tiles of 16 per warp, IG row groups; IG = 0 takes as many as the block allows);
 // false when the shape is outside the kernel's domain.
 bool tc_configure_with(int n1, int n2, int n3, int p1, int p2, int p3, int grid, int NCT, int IGreq,
-                       TcShape& sh, int& threads, size_t& smem, int& NB) {
+                       int split, TcShape& sh, int& threads, size_t& smem, int& NB) {
+  if (split != 1 && split != 3) return false;
   if (n1 < 32 || n2 < 8 || n3 < 1 || p1 < 1 || p2 < 1 || p3 < 1 || n1 % 32 != 0 || n2 % 8 != 0 ||
       n2 > 256 || p1 > 32 || p2 > 32 || grid < 1 || !(NCT == 1 || NCT == 2 || NCT == 4) ||
       n1 % (16 * NCT) != 0)
@@ -519,7 +568,7 @@ bool tc_configure_with(int n1, int n2, int n3, int p1, int p2, int p3, int grid,
   sh.p2 = p2;
   sh.p3 = p3;
   sh.CG = n1 / (16 * NCT);
-  const int max_warps = (NCT == 4 ? 256 : (NCT == 2 ? 384 : 512)) / 32;
+  const int max_warps = (split == 3 ? 256 : (NCT == 4 ? 256 : (NCT == 2 ? 384 : 512))) / 32;
   if (sh.CG > max_warps) return false;
   sh.IG = IGreq > 0 ? IGreq : max_warps / sh.CG;
   if (sh.IG > n2 / 8) sh.IG = n2 / 8;
@@ -545,18 +594,19 @@ bool tc_configure_with(int n1, int n2, int n3, int p1, int p2, int p3, int grid,
   return smem <= g_tc_budget;
 }
 
-// The tiling the kernel runs with.
-bool tc_configure(int n1, int n2, int n3, int p1, int p2, int p3, int grid, TcShape& sh, int& threads,
-                  size_t& smem, int& NB, int& NCT) {
-  NCT = (n1 % 64 == 0) ? 4 : 2;
-  return tc_configure_with(n1, n2, n3, p1, p2, p3, grid, NCT, 0, sh, threads, smem, NB);
+// The tiling the kernel runs with: 64 or 32 columns per warp for TF32; 16 for 3xTF32, whose
+// register operands are twice as large.
+bool tc_configure(int n1, int n2, int n3, int p1, int p2, int p3, int grid, int split, TcShape& sh,
+                  int& threads, size_t& smem, int& NB, int& NCT) {
+  NCT = split == 3 ? 1 : ((n1 % 64 == 0) ? 4 : 2);
+  return tc_configure_with(n1, n2, n3, p1, p2, p3, grid, NCT, 0, split, sh, threads, smem, NB);
 }
 
-template <int NB, int NCT>
+template <int NB, int NCT, int SPLIT>
 cudaError_t tc_launch(const TcShape& sh, int grid, int threads, size_t smem, const float* X1T,
                       const float* X2T, const float* D, const CUtensorMap& tmapV, float* Sb,
                       cudaStream_t s, const int* skip, int* err, const float* X3T) {
-  fused_slab_tc_kernel<NB, NCT><<<grid, threads, smem, s>>>(sh, X1T, X2T, D, tmapV, Sb, skip, err, X3T);
+  fused_slab_tc_kernel<NB, NCT, SPLIT><<<grid, threads, smem, s>>>(sh, X1T, X2T, D, tmapV, Sb, skip, err, X3T);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -589,10 +639,10 @@ bool encode_v_map(CUtensorMap* m, const float* V, int n1, int n2, int n3) {
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int NB, int NCT>
+template <int NB, int NCT, int SPLIT>
 cudaError_t tc_prepare_one() {
-  return cudaFuncSetAttribute(fused_slab_tc_kernel<NB, NCT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)g_tc_budget);
+  return cudaFuncSetAttribute(fused_slab_tc_kernel<NB, NCT, SPLIT>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g_tc_budget);
 }
 
 }  // namespace
@@ -605,27 +655,31 @@ cudaError_t fused_tc_prepare() {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
   g_tc_budget = optin > 1024 ? (size_t)optin - 1024 : 0;  // 1 KB kept for static variables
-  if (e == cudaSuccess) e = tc_prepare_one<1, 1>();
-  if (e == cudaSuccess) e = tc_prepare_one<2, 1>();
-  if (e == cudaSuccess) e = tc_prepare_one<3, 1>();
-  if (e == cudaSuccess) e = tc_prepare_one<4, 1>();
-  if (e == cudaSuccess) e = tc_prepare_one<1, 2>();
-  if (e == cudaSuccess) e = tc_prepare_one<2, 2>();
-  if (e == cudaSuccess) e = tc_prepare_one<3, 2>();
-  if (e == cudaSuccess) e = tc_prepare_one<4, 2>();
-  if (e == cudaSuccess) e = tc_prepare_one<1, 4>();
-  if (e == cudaSuccess) e = tc_prepare_one<2, 4>();
-  if (e == cudaSuccess) e = tc_prepare_one<3, 4>();
-  if (e == cudaSuccess) e = tc_prepare_one<4, 4>();
+  if (e == cudaSuccess) e = tc_prepare_one<1, 1, 1>();
+  if (e == cudaSuccess) e = tc_prepare_one<2, 1, 1>();
+  if (e == cudaSuccess) e = tc_prepare_one<3, 1, 1>();
+  if (e == cudaSuccess) e = tc_prepare_one<4, 1, 1>();
+  if (e == cudaSuccess) e = tc_prepare_one<1, 2, 1>();
+  if (e == cudaSuccess) e = tc_prepare_one<2, 2, 1>();
+  if (e == cudaSuccess) e = tc_prepare_one<3, 2, 1>();
+  if (e == cudaSuccess) e = tc_prepare_one<4, 2, 1>();
+  if (e == cudaSuccess) e = tc_prepare_one<1, 4, 1>();
+  if (e == cudaSuccess) e = tc_prepare_one<2, 4, 1>();
+  if (e == cudaSuccess) e = tc_prepare_one<3, 4, 1>();
+  if (e == cudaSuccess) e = tc_prepare_one<4, 4, 1>();
+  if (e == cudaSuccess) e = tc_prepare_one<1, 1, 3>();
+  if (e == cudaSuccess) e = tc_prepare_one<2, 1, 3>();
+  if (e == cudaSuccess) e = tc_prepare_one<3, 1, 3>();
+  if (e == cudaSuccess) e = tc_prepare_one<4, 1, 3>();
   return e;
 }
 
-int fused_tc_supported(int n1, int n2, int n3, int p1, int p2, int p3) {
+int fused_tc_supported(int n1, int n2, int n3, int p1, int p2, int p3, int split) {
   TcShape sh;
   int threads, NB, NCT;
   size_t smem;
   const int grid = n3 < num_sms() ? n3 : num_sms();
-  return tc_configure(n1, n2, n3, p1, p2, p3, grid, sh, threads, smem, NB, NCT) ? 1 : 0;
+  return tc_configure(n1, n2, n3, p1, p2, p3, grid, split, sh, threads, smem, NB, NCT) ? 1 : 0;
 }
 
 int fused_tc_pointers_ok(const float* X1T, const float* X2T, const float* D, const float* V) {
@@ -635,30 +689,52 @@ int fused_tc_pointers_ok(const float* X1T, const float* X2T, const float* D, con
 
 cudaError_t launch_fused_slab_tc(int n1, int n2, int n3, int p1, int p2, int p3, const float* X1T,
                                  const float* X2T, const float* D, const float* V, float* Sb,
-                                 cudaStream_t s, const int* skip, int* err, const float* X3T) {
+                                 cudaStream_t s, const int* skip, int* err, const float* X3T,
+                                 int split) {
   if (n3 <= 0) return cudaSuccess;
   if (!fused_tc_pointers_ok(X1T, X2T, D, V)) return cudaErrorInvalidValue;
   const int grid = n3 < num_sms() ? n3 : num_sms();
   TcShape sh;
   int threads, NB, NCT;
   size_t smem;
-  if (!tc_configure(n1, n2, n3, p1, p2, p3, grid, sh, threads, smem, NB, NCT)) return cudaErrorInvalidValue;
+  if (!tc_configure(n1, n2, n3, p1, p2, p3, grid, split, sh, threads, smem, NB, NCT))
+    return cudaErrorInvalidValue;
   alignas(64) CUtensorMap tmapV;
   if (!encode_v_map(&tmapV, V, n1, n2, n3)) return cudaErrorInvalidValue;
-  const int key = NB * 8 + NCT;
+  const int key = (split * 8 + NB) * 8 + NCT;
   switch (key) {
-    case 1 * 8 + 1: return tc_launch<1, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
-    case 2 * 8 + 1: return tc_launch<2, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
-    case 3 * 8 + 1: return tc_launch<3, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
-    case 4 * 8 + 1: return tc_launch<4, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
-    case 1 * 8 + 2: return tc_launch<1, 2>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
-    case 2 * 8 + 2: return tc_launch<2, 2>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
-    case 3 * 8 + 2: return tc_launch<3, 2>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
-    case 4 * 8 + 2: return tc_launch<4, 2>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
-    case 1 * 8 + 4: return tc_launch<1, 4>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
-    case 2 * 8 + 4: return tc_launch<2, 4>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
-    case 3 * 8 + 4: return tc_launch<3, 4>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
-    case 4 * 8 + 4: return tc_launch<4, 4>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+    case (1 * 8 + 1) * 8 + 1:
+      return tc_launch<1, 1, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+    case (1 * 8 + 2) * 8 + 1:
+      return tc_launch<2, 1, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+    case (1 * 8 + 3) * 8 + 1:
+      return tc_launch<3, 1, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+    case (1 * 8 + 4) * 8 + 1:
+      return tc_launch<4, 1, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+    case (1 * 8 + 1) * 8 + 2:
+      return tc_launch<1, 2, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+    case (1 * 8 + 2) * 8 + 2:
+      return tc_launch<2, 2, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+    case (1 * 8 + 3) * 8 + 2:
+      return tc_launch<3, 2, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+    case (1 * 8 + 4) * 8 + 2:
+      return tc_launch<4, 2, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+    case (1 * 8 + 1) * 8 + 4:
+      return tc_launch<1, 4, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+    case (1 * 8 + 2) * 8 + 4:
+      return tc_launch<2, 4, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+    case (1 * 8 + 3) * 8 + 4:
+      return tc_launch<3, 4, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+    case (1 * 8 + 4) * 8 + 4:
+      return tc_launch<4, 4, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+    case (3 * 8 + 1) * 8 + 1:
+      return tc_launch<1, 1, 3>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+    case (3 * 8 + 2) * 8 + 1:
+      return tc_launch<2, 1, 3>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+    case (3 * 8 + 3) * 8 + 1:
+      return tc_launch<3, 1, 3>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+    case (3 * 8 + 4) * 8 + 1:
+      return tc_launch<4, 1, 3>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
     default: return cudaErrorInvalidValue;
   }
 }

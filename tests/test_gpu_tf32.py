@@ -84,6 +84,33 @@ def test_tf32_product_parity(n, p, fam):
 
 
 @pytest.mark.parametrize("fam", [gen.GAUSSIAN, gen.POISSON])
+@pytest.mark.parametrize("n,p", TC_SHAPES)
+def test_fp32_tensor_core_product_parity(n, p, fam):
+    """GLAM_FP32 plans run the same product in the 3xTF32 form where its domain allows (each
+    operand as hi + lo, both TF32, so the split leaves at most 2^-22 of it; three MMAs per product,
+    the lo lo term dropped).  Bound: 32 x 2^-22 of the absolute-value chain (the split errors of
+    the eight operands and the dropped terms) plus 1e-6 of its maximum for the FP32 sums."""
+    torch, g = gpu_or_skip()
+    pr = gen.random_problem(24, n, p, fam, mask_frac=0.1, basis="normal")
+    dt = torch.float32
+    X = [dev(x, dt) for x in pr.XT]
+    rng = np.random.default_rng(25)
+    theta_k = 0.2 * rng.standard_normal((p[2], p[1], p[0]))
+    x32 = rng.standard_normal(theta_k.shape).astype(np.float32)
+    xp32 = (x32 + 0.1 * rng.standard_normal(theta_k.shape)).astype(np.float32)
+    plan = g.Plan(n, p, fam, g.GLAM_FP32)
+    q = g.glam_quad_build(plan, X, dev(theta_k, dt), dev(pr.Y, dt), dev(pr.W, dt))
+    q.b.zero_()
+    y, got = _product(g, torch, plan, X, q, x32, xp32, 0.3, dev(pr.pen_w, dt))
+    d = O.GlamData.from_c(pr.family, pr.XT, pr.Y, pr.W, pr.pen_w)
+    Vp, yp = O.paper_array(host(q.V)), O.paper_array(y)
+    ref = O.c_array(O.G(d.Xs, Vp * O.H(d.Xs, yp)))
+    scale = O.c_array(_abs_chain(d.Xs, Vp, yp))
+    err = np.abs(got - ref)
+    assert np.all(err <= 32 * 2.0 ** -22 * scale + 1e-6 * scale.max()), float((err / scale).max())
+
+
+@pytest.mark.parametrize("fam", [gen.GAUSSIAN, gen.POISSON])
 def test_tf32_small_path_matches_oracle(fam):
     """A masked lambda path on a tensor-core shape: the TF32 inner products only change the
     iteration count, the FP64 KKT test decides when each lambda is done."""
