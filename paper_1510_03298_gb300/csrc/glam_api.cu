@@ -50,6 +50,7 @@ struct glam_plan {
   // form of the tensor-core fused kernel for this plan: 1 (TF32 plans: TF32 operands), 3 (FP32
   // plans: 3xTF32, about FP32 accuracy), 0 when the shape is outside its domain or the plan is FP64
   int tc_split = 0;
+  float* tc_cst = nullptr;  // the tensor-core kernel's constant block (X_1, X_2 in its layouts)
   std::string err;
   Work<float> wf;
   Work<double> wd;
@@ -199,11 +200,13 @@ struct Ops {
   int XtWX(const TB* x, const TB* xp, const TB* sub, const T* V, const InnerCtl* ctl,
            double omega, const int* skip) {
     if constexpr (sizeof(T) == 4 && sizeof(TB) == 4) {
-      if (pl->tc_split && sub == nullptr && ctl == nullptr && fused_tc_pointers_ok(X[0], X[1], w.yx, V)) {
+      if (pl->tc_split && sub == nullptr && ctl == nullptr && fused_tc_pointers_ok(pl->tc_cst, w.yx, V)) {
         // tensor-core kernel: it forms T_a = X_3 y from the extrapolated point itself
         CK(launch_extrap<T>(pl->p, x, xp, omega, w.yx, s));
+        CK(launch_fused_tc_const((int)pl->n1, (int)pl->n2, (int)pl->p1, (int)pl->p2, X[0], X[1],
+                                 pl->tc_cst, pl->tc_split, s));
         CK(launch_fused_slab_tc((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2,
-                                (int)pl->p3, X[0], X[1], w.yx, V, w.Sb, s, skip, &pl->sc->timeout,
+                                (int)pl->p3, pl->tc_cst, w.yx, V, w.Sb, s, skip, &pl->sc->timeout,
                                 X[2], pl->tc_split));
         CK(launch_gemm<T, T>(d_mode3_adj(pl, pl->ksplit), X[2], w.Sb, w.Qpart, s, nullptr, nullptr,
                              nullptr, 0.0, skip));
@@ -410,6 +413,14 @@ int glam_plan_create(const glam_dims* dims, int family, int precision, void* str
   for (double** v : {&pl->th, &pl->x0, &pl->x1, &pl->gk, &pl->pen, &pl->ptmp})
     if ((st = dalloc(pl, v, p)) != GLAM_OK) return bail(st);
   if ((st = dalloc(pl, &pl->d_gram, 4096)) != GLAM_OK) return bail(st);
+  if (pl->tc_split) {
+    const int64_t nc = fused_tc_const_floats((int)pl->n1, (int)pl->n2, (int)pl->p1, (int)pl->p2);
+    if (nc <= 0) {
+      pl->tc_split = 0;
+    } else if ((st = dalloc(pl, &pl->tc_cst, (size_t)nc)) != GLAM_OK) {
+      return bail(st);
+    }
+  }
 
   if ((st = dalloc(pl, &pl->ctl, 1)) != GLAM_OK) return bail(st);
   if ((st = dalloc(pl, &pl->sc, 1)) != GLAM_OK) return bail(st);
@@ -708,14 +719,14 @@ int capture_chunk(Fit<T>& f) {
     double* xp = (it % 2 == 0) ? pl->x1 : pl->x0;
     bool use_tc = false;
     if constexpr (sizeof(T) == 4)
-      use_tc = pl->tc_split && fused_tc_pointers_ok(op.X[0], op.X[1], op.w.dn, op.w.V);
+      use_tc = pl->tc_split && fused_tc_pointers_ok(pl->tc_cst, op.w.dn, op.w.V);
     if (pl->fused[sizeof(T) == 8 ? 1 : 0] || use_tc) {
       // the fused kernel forms T_a = X_3 d from the correction itself, then the split adjoint
       cudaError_t e = cudaSuccess;
       if constexpr (sizeof(T) == 4) {
         if (use_tc)
           e = launch_fused_slab_tc((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2,
-                                   (int)pl->p3, op.X[0], op.X[1], op.w.dn, op.w.V, op.w.Sb, f.s,
+                                   (int)pl->p3, pl->tc_cst, op.w.dn, op.w.V, op.w.Sb, f.s,
                                    &pl->ctl->done, &pl->sc->timeout, op.X[2], pl->tc_split);
       }
       if (!use_tc)
@@ -852,6 +863,9 @@ int fit_impl(glam_plan* pl, const void* const X[3], const T* Y, const T* W, cons
   CK(cudaEventRecord(pl->ev_in, pl->stream));
   CK(cudaStreamWaitEvent(f.s, pl->ev_in, 0));
   for (int j = 0; j < 3; ++j) f.Xw[j] = X[j];
+  if (sizeof(T) == 4 && pl->tc_split)  // the tensor-core kernel's constant block, once per fit
+    CK(launch_fused_tc_const((int)pl->n1, (int)pl->n2, (int)pl->p1, (int)pl->p2, (const float*)X[0],
+                             (const float*)X[1], pl->tc_cst, pl->tc_split, f.s));
   if (sizeof(T) == 8) {
     for (int j = 0; j < 3; ++j) f.X64[j] = X[j];
     f.Y64 = (const double*)Y;
@@ -992,10 +1006,15 @@ int time_inner_impl(glam_plan* pl, const void* const X[3], const glam_quad* q, i
   CK(cudaEventCreate(&a));
   CK(cudaEventCreate(&b));
   const int slot = sizeof(T) == 8 ? 1 : 0;
+  if constexpr (sizeof(T) == 4) {
+    if (pl->tc_split)
+      CK(launch_fused_tc_const((int)pl->n1, (int)pl->n2, (int)pl->p1, (int)pl->p2, op.X[0], op.X[1],
+                               pl->tc_cst, pl->tc_split, pl->stream));
+  }
   auto timed = [&](int which) -> int {
     ms[which] = 0.0;
     bool use_tc = false;
-    if constexpr (sizeof(T) == 4) use_tc = pl->tc_split && fused_tc_pointers_ok(op.X[0], op.X[1], op.w.dn, V);
+    if constexpr (sizeof(T) == 4) use_tc = pl->tc_split && fused_tc_pointers_ok(pl->tc_cst, op.w.dn, V);
     const bool fused = pl->fused[slot] || use_tc;
     if (which == 0 && !fused) return GLAM_OK;
     for (int r = -2; r < reps; ++r) {
@@ -1005,7 +1024,7 @@ int time_inner_impl(glam_plan* pl, const void* const X[3], const glam_quad* q, i
           if constexpr (sizeof(T) == 4) {
             if (use_tc) {
               CK(launch_fused_slab_tc((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1,
-                                      (int)pl->p2, (int)pl->p3, op.X[0], op.X[1], op.w.dn, V,
+                                      (int)pl->p2, (int)pl->p3, pl->tc_cst, op.w.dn, V,
                                       op.w.Sb, pl->stream, nullptr, &pl->sc->timeout, op.X[2],
                                       pl->tc_split));
               break;

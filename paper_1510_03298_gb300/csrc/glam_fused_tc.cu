@@ -91,17 +91,27 @@ template <int SPLIT>
 __device__ __forceinline__ float tf_store(float x) {
   return SPLIT == 1 ? __uint_as_float(to_tf32(x)) : x;
 }
-// D += A B; the 3xTF32 form adds the two cross terms before the main one (hi lo' + lo hi' + hi hi';
-// the lo lo' term, below 2^-22 of the product, is dropped)
+// D += A B.  The 3xTF32 form adds hi hi' to D and the two cross terms hi lo' + lo hi' to a
+// second accumulator X, which the caller adds to D when the sum is complete (two independent
+// chains of MMAs instead of one three times as long); the lo lo' term, below 2^-22 of the
+// product, is dropped.  X is untouched when SPLIT = 1.
 template <int SPLIT>
-__device__ __forceinline__ void mma_x(float (&d)[4], const Tf<SPLIT>& a0, const Tf<SPLIT>& a1,
-                                      const Tf<SPLIT>& a2, const Tf<SPLIT>& a3, const Tf<SPLIT>& b0,
-                                      const Tf<SPLIT>& b1) {
+__device__ __forceinline__ void mma_x(float (&d)[4], float (&x)[4], const Tf<SPLIT>& a0,
+                                      const Tf<SPLIT>& a1, const Tf<SPLIT>& a2, const Tf<SPLIT>& a3,
+                                      const Tf<SPLIT>& b0, const Tf<SPLIT>& b1) {
   if constexpr (SPLIT == 3) {
-    mma_tf32(d, a0.h, a1.h, a2.h, a3.h, b0.l, b1.l);
-    mma_tf32(d, a0.l, a1.l, a2.l, a3.l, b0.h, b1.h);
+    mma_tf32(x, a0.h, a1.h, a2.h, a3.h, b0.l, b1.l);
+    mma_tf32(x, a0.l, a1.l, a2.l, a3.l, b0.h, b1.h);
   }
   mma_tf32(d, a0.h, a1.h, a2.h, a3.h, b0.h, b1.h);
+}
+// D += X (the cross terms of the 3xTF32 form), once a sum is complete
+template <int SPLIT>
+__device__ __forceinline__ void fold_cross(float (&d)[4], const float (&x)[4]) {
+  if constexpr (SPLIT == 3) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) d[e] += x[e];
+  }
 }
 
 struct TcShape {
@@ -109,6 +119,7 @@ struct TcShape {
   int CG, IG;  // column groups (16 NCT columns each) and row groups of the warps
   int kmax;    // slabs per CTA, at most
   int R;       // rows of d per staged chunk of the prologue
+  int v4d;     // 1: V's tensor map is 4-D and a slab is one copy; 0: 3-D, one copy per strip
 };
 
 // pitch >= w with pitch = 8 (mod 16): 64-bit fragment reads whose half warp touches rows
@@ -119,7 +130,8 @@ __host__ __device__ constexpr int pitch4(int w) { return ((w + 3) / 8) * 8 + 4; 
 
 struct TcLayout {
   int64_t vbuf, x2t, x2n, x1s, tas, tbf, pbuf, x3r, total;  // offsets in floats
-  int64_t sx1, sx2, sd;  // prologue staging of X_1^T, X_2^T and a chunk of d, inside vbuf
+  int64_t sd;     // prologue staging of a chunk of d, inside vbuf
+  int64_t cst_n;  // floats of the constant block [x2t, x2n, x1s], copied whole from global memory
   int KP, NP, LDc, QT;   // pitches in floats
 };
 
@@ -158,19 +170,27 @@ __host__ __device__ inline TcLayout tc_layout(const TcShape& sh, int nwarps) {
   L.x3r = off;                                    // [p3][KQ]        X_3(slab_k, j3) at [j3][k]
   off += (int64_t)sh.p3 * ((sh.kmax + 3) / 4 * 4);
   L.total = off;
-  // prologue staging (16-byte aligned pieces)
-  L.sx1 = L.vbuf;
-  L.sx2 = L.sx1 + al4((int64_t)sh.p1 * sh.n1);
-  L.sd = L.sx2 + al4((int64_t)sh.p2 * sh.n2);
+  L.sd = L.vbuf;
+  L.cst_n = L.tas - L.x2t;  // a multiple of 8 floats
   return L;
 }
 
 // One V slab into buffer b (called by one thread): the byte count of the slab is posted, then
-// one tiled copy per 32-column strip, box {32, n2, 1} at coordinates {32 s, 0, slab}.
-__device__ __forceinline__ void issue_slab(float* vbuf_b, const CUtensorMap* tmap, int slab, int n1,
-                                           int n2, uint64_t* bar) {
+// the copies.  With the 4-D map (dims: 32 columns, n2 rows, n1/32 strips, n3 slabs) one box
+// {32, n2, n1/32, 1} lands as [strip][row][32]; with the 3-D map (32-column boxes of the
+// (n3, n2, n1) array) one copy per strip, box {32, n2, 1} at {32 s, 0, slab}.
+__device__ __forceinline__ void issue_slab(float* vbuf_b, const CUtensorMap* tmap, int v4d, int slab,
+                                           int n1, int n2, uint64_t* bar) {
   fence_proxy_async();
   mbar_expect_tx(bar, (uint32_t)n1 * (uint32_t)n2 * 4u);
+  if (v4d) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(vbuf_b)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(0), "r"(0), "r"(0), "r"(slab), "r"(smem_u32(bar))
+        : "memory");
+    return;
+  }
   for (int s = 0; s < n1 / 32; ++s) {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
@@ -189,8 +209,8 @@ constexpr int tc_max_threads() {
 
 template <int NB, int NCT, int SPLIT>
 __global__ void __launch_bounds__(tc_max_threads<NCT, SPLIT>(), 1)
-fused_slab_tc_kernel(TcShape sh, const float* __restrict__ X1T, const float* __restrict__ X2T,
-                     const float* __restrict__ D, const __grid_constant__ CUtensorMap tmapV,
+fused_slab_tc_kernel(TcShape sh, const float* __restrict__ Cst, const float* __restrict__ D,
+                     const __grid_constant__ CUtensorMap tmapV,
                      float* __restrict__ Sb, const int* __restrict__ skip, int* __restrict__ err,
                      const float* __restrict__ X3T) {
   constexpr int K8 = 8 * NB, MT = (K8 + 15) / 16;
@@ -215,14 +235,13 @@ fused_slab_tc_kernel(TcShape sh, const float* __restrict__ X1T, const float* __r
   float4* TbF = reinterpret_cast<float4*>(base + L.tbf);
   float* Pbuf = base + L.pbuf;
   float* X3r = base + L.x3r;
-  const float* sX1 = base + L.sx1;
-  const float* sX2 = base + L.sx2;
   float* sD = base + L.sd;
   const int KP = L.KP, NP = L.NP, LDc = L.LDc, QT = L.QT;
   const int R = sh.R, nchunk = (p3 + R - 1) / R;
 
-  // ---- prologue: X_1^T, X_2^T and the first rows of d arrive by bulk copies into the V buffers
-  // (one memory round trip), the rows of X_3 of the CTA's slabs by one gather ----
+  // ---- prologue: the constant operands (X_2 and X_1 in their shared-memory layouts, prepared
+  // once per fit by tc_const_kernel) and the first rows of d arrive by bulk copies (one memory
+  // round trip), the X_3 entries of the CTA's slabs by one gather ----
   if (tid == 0) {
     // the descriptor of V's tensor map is fetched now, not at the first V request
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmapV)) : "memory");
@@ -237,10 +256,9 @@ fused_slab_tc_kernel(TcShape sh, const float* __restrict__ X1T, const float* __r
   // a chunk of d moves as its 16-byte multiple; the last < 4 floats (odd p2 p1) by plain loads
   auto chunk_bulk = [&](int c) { return (uint32_t)(((int64_t)chunk_rows(c) * P21) / 4 * 16); };
   if (tid == 0) {
-    const uint32_t bx1 = (uint32_t)p1 * n1 * 4u, bx2 = (uint32_t)p2 * n2 * 4u;
-    mbar_expect_tx(&mbar[2], bx1 + bx2 + chunk_bulk(0));
-    bulk_g2s(base + L.sx1, X1T, bx1, &mbar[2]);
-    bulk_g2s(base + L.sx2, X2T, bx2, &mbar[2]);
+    const uint32_t bc = (uint32_t)L.cst_n * 4u;
+    mbar_expect_tx(&mbar[2], bc + chunk_bulk(0));
+    bulk_g2s(X2t, Cst, bc, &mbar[2]);
     if (chunk_bulk(0) > 0) bulk_g2s(sD, D, chunk_bulk(0), &mbar[2]);
   }
   const int KQ = (sh.kmax + 3) / 4 * 4;  // slabs of X3r rounded up to float4 groups
@@ -248,34 +266,21 @@ fused_slab_tc_kernel(TcShape sh, const float* __restrict__ X1T, const float* __r
     const int j3 = idx / KQ, kk = idx - j3 * KQ;
     X3r[idx] = kk < kcta ? X3T[(int64_t)j3 * n3 + blockIdx.x + (int64_t)kk * gridDim.x] : 0.f;
   }
-  for (int idx = tid; idx < n2 * KP; idx += nth) X2t[idx] = 0.f;
-  for (int idx = tid; idx < 16 * MT * NP; idx += nth) X2n[idx] = 0.f;
-  for (int idx = tid; idx < K8 * LDc; idx += nth) X1s[idx] = 0.f;
   for (int idx = tid; idx < sh.kmax * K8 * QT; idx += nth) TaS[idx] = 0.f;
   bool ok0 = mbar_wait_bounded(&mbar[2], 0u);
   if (!ok0) atomicOr(&timed_out, 1);
   __syncthreads();
-  // constant operands, rounded to TF32, from the staged copies
-  for (int i = tid; i < p2 * n2; i += nth) {  // X_2^T is (p2, n2)
-    const int j2 = i / n2, i2 = i - j2 * n2;
-    const float r = tf_store<SPLIT>(sX2[i]);
-    X2t[i2 * KP + j2] = r;
-    X2n[j2 * NP + i2] = r;
-  }
-  for (int i = tid; i < p1 * n1; i += nth) {  // X_1^T is (p1, n1)
-    const int j1 = i / n1, c = i - j1 * n1;
-    X1s[j1 * LDc + c] = tf_store<SPLIT>(sX1[i]);
-  }
-  // MMA0's A operand X_1(c, j1) for this warp's 16-row tile of c, kept in registers
+  // MMA0's A operand X_1(c, j1) for this warp's 16-row tile of c, kept in registers (X1s holds
+  // zeros in the rows j1 >= p1)
   const bool mma0_warp = warp < n1 / 16;
   Tf<SPLIT> xa[NB][4];
 #pragma unroll
   for (int s = 0; s < NB; ++s) {
     const int c = 16 * warp + g, j0 = 8 * s + t, j4 = j0 + 4;
-    xa[s][0] = tf_of<SPLIT>((mma0_warp && j0 < p1) ? sX1[j0 * n1 + c] : 0.f);
-    xa[s][1] = tf_of<SPLIT>((mma0_warp && j0 < p1) ? sX1[j0 * n1 + c + 8] : 0.f);
-    xa[s][2] = tf_of<SPLIT>((mma0_warp && j4 < p1) ? sX1[j4 * n1 + c] : 0.f);
-    xa[s][3] = tf_of<SPLIT>((mma0_warp && j4 < p1) ? sX1[j4 * n1 + c + 8] : 0.f);
+    xa[s][0] = tf_stored<SPLIT>(mma0_warp ? X1s[j0 * LDc + c] : 0.f);
+    xa[s][1] = tf_stored<SPLIT>(mma0_warp ? X1s[j0 * LDc + c + 8] : 0.f);
+    xa[s][2] = tf_stored<SPLIT>(mma0_warp ? X1s[j4 * LDc + c] : 0.f);
+    xa[s][3] = tf_stored<SPLIT>(mma0_warp ? X1s[j4 * LDc + c + 8] : 0.f);
   }
   // ---- first H stage for this CTA's slabs: T_a(s_k, :) = sum_j3 X_3(s_k, j3) d(j3, :), summed
   // in j3 order into TaS (FP32), chunk by chunk of staged rows of d ----
@@ -333,30 +338,20 @@ fused_slab_tc_kernel(TcShape sh, const float* __restrict__ X1T, const float* __r
 #pragma unroll
           for (int cc = 0; cc < 2; ++cc) a[r][cc] = fmaf(xv[r], dv[cc], a[r][cc]);
       }
+      const bool last = c == nchunk - 1;  // the last chunk stores T_a in its operand form
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int cc = 0; cc < 2; ++cc)
-          if (k0 + r < kcta && in[cc]) TaS[(k0 + r) * K8 * QT + eo[cc]] = a[r][cc];
+          if (k0 + r < kcta && in[cc]) TaS[(k0 + r) * K8 * QT + eo[cc]] = last ? tf_store<SPLIT>(a[r][cc]) : a[r][cc];
     }
   }
-  __syncthreads();  // every chunk is summed
-  // T_a to its stored form in place (TF32 when SPLIT = 1), then the V buffers are free
-  if constexpr (SPLIT == 1) {
-    for (int n = tid; n < P21; n += nth) {
-      const int j2 = n / p1, j1 = n - j2 * p1;
-      for (int k = 0; k < kcta; ++k) {
-        float* e = TaS + k * K8 * QT + j2 * QT + j1;
-        *e = tf_store<SPLIT>(*e);
-      }
-    }
-  }
-  __syncthreads();
+  __syncthreads();  // every chunk is summed: T_a is in place and the V buffers are free
   if (tid == 0 && !timed_out) {
     fence_proxy_async();
     for (int b = 0; b < 2; ++b) {
       const int s0 = blockIdx.x + b * gridDim.x;
-      if (s0 < n3) issue_slab(Vbuf + (int64_t)b * nv, &tmapV, s0, n1, n2, &mbar[b]);
+      if (s0 < n3) issue_slab(Vbuf + (int64_t)b * nv, &tmapV, sh.v4d, s0, n1, n2, &mbar[b]);
     }
   }
 
@@ -385,19 +380,20 @@ fused_slab_tc_kernel(TcShape sh, const float* __restrict__ X1T, const float* __r
     const float* TaK = TaS + kk * K8 * QT;
 #pragma unroll
     for (int nb = 0; nb < NB; ++nb) {
-      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      float acc[4] = {0.f, 0.f, 0.f, 0.f}, accx[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int s = 0; s < NB; ++s) {
         const float* tb = TaK + (8 * nb + g) * QT + 8 * s + t;
-        mma_x<SPLIT>(acc, xa[s][0], xa[s][1], xa[s][2], xa[s][3], tf_stored<SPLIT>(tb[0]),
+        mma_x<SPLIT>(acc, accx, xa[s][0], xa[s][1], xa[s][2], xa[s][3], tf_stored<SPLIT>(tb[0]),
                      tf_stored<SPLIT>(tb[4]));
       }
+      fold_cross<SPLIT>(acc, accx);
       // C (c, j2 = 8 nb + {2t, 2t+1}) -> A (c, K slot t <-> 2t, slot t + 4 <-> 2t + 1)
       TbF[(warp * NB + nb) * 32 + lane] = make_float4(tf_store<SPLIT>(acc[0]), tf_store<SPLIT>(acc[2]),
                                                       tf_store<SPLIT>(acc[1]), tf_store<SPLIT>(acc[3]));
     }
   };
-  if (!timed_out) mma0(0);  // T_a is rounded: the barrier before the V requests orders it
+  if (!timed_out) mma0(0);
 
   int k = 0;
   for (int slab = blockIdx.x; slab < n3; slab += gridDim.x, ++k) {
@@ -422,6 +418,7 @@ fused_slab_tc_kernel(TcShape sh, const float* __restrict__ X1T, const float* __r
         a1f[ct][nb][3] = tf_stored<SPLIT>(f.w);
       }
     float c2[MT][NCT][2][4];  // S(j2, c): [j2 tile][column tile][column half][fragment]
+    float c2x[SPLIT == 3 ? MT : 1][NCT][2][4];  // its 3xTF32 cross terms
 #pragma unroll
     for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
@@ -429,24 +426,34 @@ fused_slab_tc_kernel(TcShape sh, const float* __restrict__ X1T, const float* __r
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
-          for (int e = 0; e < 4; ++e) c2[mt][ct][h][e] = 0.f;
+          for (int e = 0; e < 4; ++e) {
+            c2[mt][ct][h][e] = 0.f;
+            if (SPLIT == 3) c2x[SPLIT == 3 ? mt : 0][ct][h][e] = 0.f;
+          }
 
+#pragma unroll (NCT == 1 ? 2 : 1)
     for (int ib = ib0; ib < ib1; ++ib) {
       const int i0 = 8 * ib;
       // ---- MMA1: eta^T(c, i0 .. i0 + 7); B = X_2(i2, j2) with the permuted K = j2 ----
-      float c1[NCT][4];
+      float c1[NCT][4], c1x[NCT][4];
 #pragma unroll
       for (int ct = 0; ct < NCT; ++ct)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) c1[ct][e] = 0.f;
+        for (int e = 0; e < 4; ++e) {
+          c1[ct][e] = 0.f;
+          c1x[ct][e] = 0.f;
+        }
 #pragma unroll
       for (int ks = 0; ks < NB; ++ks) {
         const float2 bv = *reinterpret_cast<const float2*>(X2t + (i0 + g) * KP + 8 * ks + 2 * t);
         const Tf<SPLIT> b0 = tf_stored<SPLIT>(bv.x), b1 = tf_stored<SPLIT>(bv.y);
 #pragma unroll
         for (int ct = 0; ct < NCT; ++ct)
-          mma_x<SPLIT>(c1[ct], a1f[ct][ks][0], a1f[ct][ks][1], a1f[ct][ks][2], a1f[ct][ks][3], b0, b1);
+          mma_x<SPLIT>(c1[ct], c1x[ct], a1f[ct][ks][0], a1f[ct][ks][1], a1f[ct][ks][2], a1f[ct][ks][3],
+                       b0, b1);
       }
+#pragma unroll
+      for (int ct = 0; ct < NCT; ++ct) fold_cross<SPLIT>(c1[ct], c1x[ct]);
       // ---- r = V (.) eta as MMA2 B fragments (K = i2 permuted, N = c) ----
       Tf<SPLIT> b2f[NCT][2][2];
       const float* vrow = Vs + (int64_t)(c0w >> 5) * n2 * 32 + (i0 + 2 * t) * 32;
@@ -470,17 +477,27 @@ fused_slab_tc_kernel(TcShape sh, const float* __restrict__ X1T, const float* __r
         for (int ct = 0; ct < NCT; ++ct)
 #pragma unroll
           for (int h = 0; h < 2; ++h)
-            mma_x<SPLIT>(c2[mt][ct][h], a0, a1, a2, a3, b2f[ct][h][0], b2f[ct][h][1]);
+            mma_x<SPLIT>(c2[mt][ct][h], c2x[SPLIT == 3 ? mt : 0][ct][h], a0, a1, a2, a3, b2f[ct][h][0],
+                         b2f[ct][h][1]);
       }
     }
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+      for (int ct = 0; ct < NCT; ++ct)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) fold_cross<SPLIT>(c2[mt][ct][h], c2x[SPLIT == 3 ? mt : 0][ct][h]);
     // ---- MMA3: S_b(j2, j1) += S(j2, c) X_1(c, j1); A from S with the permuted K = c ----
-    float c3[MT][NB][4];
+    float c3[MT][NB][4], c3x[MT][NB][4];
 #pragma unroll
     for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
       for (int nj = 0; nj < NB; ++nj)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) c3[mt][nj][e] = 0.f;
+        for (int e = 0; e < 4; ++e) {
+          c3[mt][nj][e] = 0.f;
+          c3x[mt][nj][e] = 0.f;
+        }
 #pragma unroll
     for (int ct = 0; ct < NCT; ++ct)
 #pragma unroll
@@ -498,9 +515,14 @@ fused_slab_tc_kernel(TcShape sh, const float* __restrict__ X1T, const float* __r
           const Tf<SPLIT> a0 = tf_of<SPLIT>(c2[mt][ct][h][0]), a1 = tf_of<SPLIT>(c2[mt][ct][h][2]);
           const Tf<SPLIT> a2 = tf_of<SPLIT>(c2[mt][ct][h][1]), a3 = tf_of<SPLIT>(c2[mt][ct][h][3]);
 #pragma unroll
-          for (int nj = 0; nj < NB; ++nj) mma_x<SPLIT>(c3[mt][nj], a0, a1, a2, a3, bx[nj][0], bx[nj][1]);
+          for (int nj = 0; nj < NB; ++nj)
+            mma_x<SPLIT>(c3[mt][nj], c3x[mt][nj], a0, a1, a2, a3, bx[nj][0], bx[nj][1]);
         }
       }
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+      for (int nj = 0; nj < NB; ++nj) fold_cross<SPLIT>(c3[mt][nj], c3x[mt][nj]);
     // this warp's partial S_b (rows j2 < p2, columns j1 < p1)
     float* pw = Pbuf + (int64_t)warp * P21;
 #pragma unroll
@@ -517,7 +539,7 @@ fused_slab_tc_kernel(TcShape sh, const float* __restrict__ X1T, const float* __r
     __syncthreads();  // (S3) partials complete; every thread is done with this V buffer and TbF
     if (tid == 0) {
       const int nxt = slab + 2 * gridDim.x;
-      if (nxt < n3) issue_slab(Vbuf + (int64_t)b * nv, &tmapV, nxt, n1, n2, &mbar[b]);
+      if (nxt < n3) issue_slab(Vbuf + (int64_t)b * nv, &tmapV, sh.v4d, nxt, n1, n2, &mbar[b]);
     }
     if (k + 1 < kcta) mma0(k + 1);  // overlaps the reduction below
     // sum of the partials in warp order
@@ -534,6 +556,70 @@ fused_slab_tc_kernel(TcShape sh, const float* __restrict__ X1T, const float* __r
     mbar_wait_bounded(&mbar[0], 0u);
     mbar_wait_bounded(&mbar[1], 0u);
     mbar_wait_bounded(&mbar[2], (uint32_t)((nchunk - 1) & 1));
+  }
+}
+
+// Positions of the constant block [x2t, x2n, x1s] of the kernel's shared-memory layout.
+struct CstLayout {
+  int n1, n2, p1, p2, KP, NP, LDc, K8, M16;
+  int64_t o2n, o1s, total;
+};
+
+// The constant block in global memory, element for element as the kernel keeps it in shared
+// memory: X_2(i2, j2) at [i2][KP], X_2 by rows j2 at [16 MT][NP], X_1 by rows j1 at [K8][LDc],
+// zeros in every padding entry; TF32-rounded for the TF32 form, FP32 for the 3xTF32 form.
+__global__ void tc_const_kernel(CstLayout c, const float* __restrict__ X1T,
+                                const float* __restrict__ X2T, float* __restrict__ out, int split) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < c.total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    float v = 0.f;
+    if (e < (int64_t)c.n2 * c.KP) {
+      const int i2 = (int)(e / c.KP), j2 = (int)(e % c.KP);
+      if (j2 < c.p2) v = X2T[(int64_t)j2 * c.n2 + i2];
+    } else if (e >= c.o2n && e < c.o2n + (int64_t)c.M16 * c.NP) {
+      const int64_t f = e - c.o2n;
+      const int j2 = (int)(f / c.NP), i2 = (int)(f % c.NP);
+      if (j2 < c.p2 && i2 < c.n2) v = X2T[(int64_t)j2 * c.n2 + i2];
+    } else if (e >= c.o1s && e < c.o1s + (int64_t)c.K8 * c.LDc) {
+      const int64_t f = e - c.o1s;
+      const int j1 = (int)(f / c.LDc), i1 = (int)(f % c.LDc);
+      if (j1 < c.p1 && i1 < c.n1) v = X1T[(int64_t)j1 * c.n1 + i1];
+    }
+    out[e] = split == 1 ? __uint_as_float(to_tf32(v)) : v;
+  }
+}
+
+template <int NB>
+CstLayout cst_layout_nb(int n1, int n2, int p1, int p2) {
+  TcShape sh{};
+  sh.n1 = n1;
+  sh.n2 = n2;
+  sh.p1 = p1;
+  sh.p2 = p2;
+  const TcLayout L = tc_layout<NB>(sh, 1);  // the constant block does not depend on the warps
+  CstLayout c;
+  c.n1 = n1;
+  c.n2 = n2;
+  c.p1 = p1;
+  c.p2 = p2;
+  c.KP = L.KP;
+  c.NP = L.NP;
+  c.LDc = L.LDc;
+  c.K8 = 8 * NB;
+  c.M16 = 16 * ((8 * NB + 15) / 16);
+  c.o2n = L.x2n - L.x2t;
+  c.o1s = L.x1s - L.x2t;
+  c.total = L.cst_n;
+  return c;
+}
+
+bool cst_layout(int n1, int n2, int p1, int p2, CstLayout& c) {
+  switch (((p1 > p2 ? p1 : p2) + 7) / 8) {
+    case 1: c = cst_layout_nb<1>(n1, n2, p1, p2); return true;
+    case 2: c = cst_layout_nb<2>(n1, n2, p1, p2); return true;
+    case 3: c = cst_layout_nb<3>(n1, n2, p1, p2); return true;
+    case 4: c = cst_layout_nb<4>(n1, n2, p1, p2); return true;
+    default: return false;
   }
 }
 
@@ -580,7 +666,7 @@ bool tc_configure_with(int n1, int n2, int n3, int p1, int p2, int p3, int grid,
   threads = 32 * nwarps;
   {  // rows of d per prologue chunk: what fits in the staging area after X_1^T and X_2^T
     const int64_t P21 = (int64_t)p1 * p2;
-    const int64_t sd = al4((int64_t)p1 * n1) + al4((int64_t)p2 * n2);
+    const int64_t sd = 0;  // d is staged from the start of the V buffers
     const int64_t stage_end = al8(al8(2LL * n1 * n2) + (int64_t)(n1 / 16) * NB * 128) +
                               (int64_t)nwarps * P21;  // the start of x2t
     const int64_t avail = stage_end - sd;
@@ -590,23 +676,24 @@ bool tc_configure_with(int n1, int n2, int n3, int p1, int p2, int p3, int grid,
     if (R < 1) return false;
     sh.R = (int)R;
   }
+  sh.v4d = 0;
   smem = tc_smem_bytes(NB, sh, nwarps) + kTcAlignSlack;
   return smem <= g_tc_budget;
 }
 
-// The tiling the kernel runs with: 64 or 32 columns per warp for TF32; 16 for 3xTF32, whose
+// The tiling the kernel runs with: 64 or 32 columns per warp for TF32; 32 for 3xTF32, whose
 // register operands are twice as large.
 bool tc_configure(int n1, int n2, int n3, int p1, int p2, int p3, int grid, int split, TcShape& sh,
                   int& threads, size_t& smem, int& NB, int& NCT) {
-  NCT = split == 3 ? 1 : ((n1 % 64 == 0) ? 4 : 2);
+  NCT = split == 3 ? 2 : ((n1 % 64 == 0) ? 4 : 2);
   return tc_configure_with(n1, n2, n3, p1, p2, p3, grid, NCT, 0, split, sh, threads, smem, NB);
 }
 
 template <int NB, int NCT, int SPLIT>
-cudaError_t tc_launch(const TcShape& sh, int grid, int threads, size_t smem, const float* X1T,
-                      const float* X2T, const float* D, const CUtensorMap& tmapV, float* Sb,
-                      cudaStream_t s, const int* skip, int* err, const float* X3T) {
-  fused_slab_tc_kernel<NB, NCT, SPLIT><<<grid, threads, smem, s>>>(sh, X1T, X2T, D, tmapV, Sb, skip, err, X3T);
+cudaError_t tc_launch(const TcShape& sh, int grid, int threads, size_t smem, const float* Cst,
+                      const float* D, const CUtensorMap& tmapV, float* Sb, cudaStream_t s,
+                      const int* skip, int* err, const float* X3T) {
+  fused_slab_tc_kernel<NB, NCT, SPLIT><<<grid, threads, smem, s>>>(sh, Cst, D, tmapV, Sb, skip, err, X3T);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -626,17 +713,31 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
   return fn;
 }
 
-// The 3-D tensor map of V (n3, n2, n1) with boxes of 32 x n2 x 1 and the 128-byte swizzle.
-bool encode_v_map(CUtensorMap* m, const float* V, int n1, int n2, int n3) {
+// V's tensor map with the 128-byte swizzle: 4-D (32 columns, n2 rows, n1/32 strips, n3 slabs;
+// strides n1 * 4, 128 and n1 n2 * 4 bytes) so that one box {32, n2, n1/32, 1} moves a slab; if
+// the driver does not take that map, the 3-D map of the (n3, n2, n1) array with boxes
+// {32, n2, 1}.  Returns 4, 3, or 0 when neither map can be made.
+int encode_v_map(CUtensorMap* m, const float* V, int n1, int n2, int n3) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
-  if (fn == nullptr) return false;
+  if (fn == nullptr) return 0;
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  {
+    const cuuint64_t dims[4] = {32, (cuuint64_t)n2, (cuuint64_t)(n1 / 32), (cuuint64_t)n3};
+    const cuuint64_t strides[3] = {(cuuint64_t)n1 * 4, 128, (cuuint64_t)n1 * n2 * 4};
+    const cuuint32_t box[4] = {32, (cuuint32_t)n2, (cuuint32_t)(n1 / 32), 1};
+    if (fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(V), dims, strides, box, estr,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+      return 4;
+  }
   const cuuint64_t dims[3] = {(cuuint64_t)n1, (cuuint64_t)n2, (cuuint64_t)n3};
   const cuuint64_t strides[2] = {(cuuint64_t)n1 * 4, (cuuint64_t)n1 * n2 * 4};
   const cuuint32_t box[3] = {32, (cuuint32_t)n2, 1};
-  const cuuint32_t estr[3] = {1, 1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(V), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS
+             ? 3
+             : 0;
 }
 
 template <int NB, int NCT, int SPLIT>
@@ -667,10 +768,10 @@ cudaError_t fused_tc_prepare() {
   if (e == cudaSuccess) e = tc_prepare_one<2, 4, 1>();
   if (e == cudaSuccess) e = tc_prepare_one<3, 4, 1>();
   if (e == cudaSuccess) e = tc_prepare_one<4, 4, 1>();
-  if (e == cudaSuccess) e = tc_prepare_one<1, 1, 3>();
-  if (e == cudaSuccess) e = tc_prepare_one<2, 1, 3>();
-  if (e == cudaSuccess) e = tc_prepare_one<3, 1, 3>();
-  if (e == cudaSuccess) e = tc_prepare_one<4, 1, 3>();
+  if (e == cudaSuccess) e = tc_prepare_one<1, 2, 3>();
+  if (e == cudaSuccess) e = tc_prepare_one<2, 2, 3>();
+  if (e == cudaSuccess) e = tc_prepare_one<3, 2, 3>();
+  if (e == cudaSuccess) e = tc_prepare_one<4, 2, 3>();
   return e;
 }
 
@@ -682,17 +783,33 @@ int fused_tc_supported(int n1, int n2, int n3, int p1, int p2, int p3, int split
   return tc_configure(n1, n2, n3, p1, p2, p3, grid, split, sh, threads, smem, NB, NCT) ? 1 : 0;
 }
 
-int fused_tc_pointers_ok(const float* X1T, const float* X2T, const float* D, const float* V) {
+int fused_tc_pointers_ok(const float* Cst, const float* D, const float* V) {
   auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) % 16) == 0; };
-  return al16(X1T) && al16(X2T) && al16(D) && al16(V) ? 1 : 0;
+  return al16(Cst) && al16(D) && al16(V) ? 1 : 0;
 }
 
-cudaError_t launch_fused_slab_tc(int n1, int n2, int n3, int p1, int p2, int p3, const float* X1T,
-                                 const float* X2T, const float* D, const float* V, float* Sb,
+int64_t fused_tc_const_floats(int n1, int n2, int p1, int p2) {
+  CstLayout c;
+  return cst_layout(n1, n2, p1, p2, c) ? c.total : 0;
+}
+
+cudaError_t launch_fused_tc_const(int n1, int n2, int p1, int p2, const float* X1T, const float* X2T,
+                                  float* Cst, int split, cudaStream_t s) {
+  CstLayout c;
+  if (!cst_layout(n1, n2, p1, p2, c)) return cudaErrorInvalidValue;
+  int blocks = (int)((c.total + 255) / 256);
+  if (blocks > 4 * num_sms()) blocks = 4 * num_sms();
+  tc_const_kernel<<<blocks, 256, 0, s>>>(c, X1T, X2T, Cst, split);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fused_slab_tc(int n1, int n2, int n3, int p1, int p2, int p3, const float* Cst,
+                                 const float* D, const float* V, float* Sb,
                                  cudaStream_t s, const int* skip, int* err, const float* X3T,
                                  int split) {
   if (n3 <= 0) return cudaSuccess;
-  if (!fused_tc_pointers_ok(X1T, X2T, D, V)) return cudaErrorInvalidValue;
+  if (!fused_tc_pointers_ok(Cst, D, V)) return cudaErrorInvalidValue;
   const int grid = n3 < num_sms() ? n3 : num_sms();
   TcShape sh;
   int threads, NB, NCT;
@@ -700,41 +817,43 @@ cudaError_t launch_fused_slab_tc(int n1, int n2, int n3, int p1, int p2, int p3,
   if (!tc_configure(n1, n2, n3, p1, p2, p3, grid, split, sh, threads, smem, NB, NCT))
     return cudaErrorInvalidValue;
   alignas(64) CUtensorMap tmapV;
-  if (!encode_v_map(&tmapV, V, n1, n2, n3)) return cudaErrorInvalidValue;
+  const int rank = encode_v_map(&tmapV, V, n1, n2, n3);
+  if (rank == 0) return cudaErrorInvalidValue;
+  sh.v4d = rank == 4 ? 1 : 0;
   const int key = (split * 8 + NB) * 8 + NCT;
   switch (key) {
     case (1 * 8 + 1) * 8 + 1:
-      return tc_launch<1, 1, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+      return tc_launch<1, 1, 1>(sh, grid, threads, smem, Cst, D, tmapV, Sb, s, skip, err, X3T);
     case (1 * 8 + 2) * 8 + 1:
-      return tc_launch<2, 1, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+      return tc_launch<2, 1, 1>(sh, grid, threads, smem, Cst, D, tmapV, Sb, s, skip, err, X3T);
     case (1 * 8 + 3) * 8 + 1:
-      return tc_launch<3, 1, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+      return tc_launch<3, 1, 1>(sh, grid, threads, smem, Cst, D, tmapV, Sb, s, skip, err, X3T);
     case (1 * 8 + 4) * 8 + 1:
-      return tc_launch<4, 1, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+      return tc_launch<4, 1, 1>(sh, grid, threads, smem, Cst, D, tmapV, Sb, s, skip, err, X3T);
     case (1 * 8 + 1) * 8 + 2:
-      return tc_launch<1, 2, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+      return tc_launch<1, 2, 1>(sh, grid, threads, smem, Cst, D, tmapV, Sb, s, skip, err, X3T);
     case (1 * 8 + 2) * 8 + 2:
-      return tc_launch<2, 2, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+      return tc_launch<2, 2, 1>(sh, grid, threads, smem, Cst, D, tmapV, Sb, s, skip, err, X3T);
     case (1 * 8 + 3) * 8 + 2:
-      return tc_launch<3, 2, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+      return tc_launch<3, 2, 1>(sh, grid, threads, smem, Cst, D, tmapV, Sb, s, skip, err, X3T);
     case (1 * 8 + 4) * 8 + 2:
-      return tc_launch<4, 2, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+      return tc_launch<4, 2, 1>(sh, grid, threads, smem, Cst, D, tmapV, Sb, s, skip, err, X3T);
     case (1 * 8 + 1) * 8 + 4:
-      return tc_launch<1, 4, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+      return tc_launch<1, 4, 1>(sh, grid, threads, smem, Cst, D, tmapV, Sb, s, skip, err, X3T);
     case (1 * 8 + 2) * 8 + 4:
-      return tc_launch<2, 4, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+      return tc_launch<2, 4, 1>(sh, grid, threads, smem, Cst, D, tmapV, Sb, s, skip, err, X3T);
     case (1 * 8 + 3) * 8 + 4:
-      return tc_launch<3, 4, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+      return tc_launch<3, 4, 1>(sh, grid, threads, smem, Cst, D, tmapV, Sb, s, skip, err, X3T);
     case (1 * 8 + 4) * 8 + 4:
-      return tc_launch<4, 4, 1>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
-    case (3 * 8 + 1) * 8 + 1:
-      return tc_launch<1, 1, 3>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
-    case (3 * 8 + 2) * 8 + 1:
-      return tc_launch<2, 1, 3>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
-    case (3 * 8 + 3) * 8 + 1:
-      return tc_launch<3, 1, 3>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
-    case (3 * 8 + 4) * 8 + 1:
-      return tc_launch<4, 1, 3>(sh, grid, threads, smem, X1T, X2T, D, tmapV, Sb, s, skip, err, X3T);
+      return tc_launch<4, 4, 1>(sh, grid, threads, smem, Cst, D, tmapV, Sb, s, skip, err, X3T);
+    case (3 * 8 + 1) * 8 + 2:
+      return tc_launch<1, 2, 3>(sh, grid, threads, smem, Cst, D, tmapV, Sb, s, skip, err, X3T);
+    case (3 * 8 + 2) * 8 + 2:
+      return tc_launch<2, 2, 3>(sh, grid, threads, smem, Cst, D, tmapV, Sb, s, skip, err, X3T);
+    case (3 * 8 + 3) * 8 + 2:
+      return tc_launch<3, 2, 3>(sh, grid, threads, smem, Cst, D, tmapV, Sb, s, skip, err, X3T);
+    case (3 * 8 + 4) * 8 + 2:
+      return tc_launch<4, 2, 3>(sh, grid, threads, smem, Cst, D, tmapV, Sb, s, skip, err, X3T);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -98,15 +98,19 @@ cudaError_t fused_prepare();
 
 // The same product on tensor cores with FP32 accumulation, always forming T_a = X_3 d from the
 // correction D (p3 x p2p1): split = 1 rounds every operand to TF32; split = 3 is the 3xTF32
-// form (each operand as hi + lo, three MMAs per product: about FP32 accuracy).
-// fused_tc_supported tells whether the shape is in the kernel's domain for that form.
-cudaError_t launch_fused_slab_tc(int n1, int n2, int n3, int p1, int p2, int p3, const float* X1T,
-                                 const float* X2T, const float* D, const float* V, float* Sb,
-                                 cudaStream_t s, const int* skip, int* err, const float* X3T,
-                                 int split);
+// form (each operand as hi + lo, three MMAs per product: about FP32 accuracy).  Cst is the
+// constant block of fused_tc_const_floats floats written by launch_fused_tc_const from X_1^T and
+// X_2^T (once per set of designs).  fused_tc_supported tells whether the shape is in the
+// kernel's domain for that form.
+cudaError_t launch_fused_slab_tc(int n1, int n2, int n3, int p1, int p2, int p3, const float* Cst,
+                                 const float* D, const float* V, float* Sb, cudaStream_t s,
+                                 const int* skip, int* err, const float* X3T, int split);
+cudaError_t launch_fused_tc_const(int n1, int n2, int p1, int p2, const float* X1T, const float* X2T,
+                                  float* Cst, int split, cudaStream_t s);
+int64_t fused_tc_const_floats(int n1, int n2, int p1, int p2);
 int fused_tc_supported(int n1, int n2, int n3, int p1, int p2, int p3, int split);
-// the kernel bulk-copies X_1^T, X_2^T, D and V: each must start on a 16-byte boundary
-int fused_tc_pointers_ok(const float* X1T, const float* X2T, const float* D, const float* V);
+// Cst, D and V are bulk-copied by the kernel: each must start on a 16-byte boundary
+int fused_tc_pointers_ok(const float* Cst, const float* D, const float* V);
 cudaError_t fused_tc_prepare();
 
 // ------------------------------------------------------------------------------------
