@@ -225,8 +225,10 @@ int64_t glam_launch_count(void);
 /* Time the kernels of one inner PG iteration of glam_fit_path, as the fit launches them, on the
  * plan's stream with CUDA events: ms[0] the fused per-slab G(V (.) H(.)) kernel, which also forms
  * the first H stage X_3 d of the correction d (0 if the shape uses the unfused chain); ms[1] the
- * separate mode-3 product of the unfused chain (0 when the fused kernel is used); ms[2] the split
- * mode-3 adjoint product; ms[3] the proximal step.  Each kernel runs 2 + reps times back to
+ * separate mode-3 product of the unfused chain (0 when the fused kernel is used); ms[2] the
+ * mode-3 adjoint product: the split GEMM, or, where the fit path fuses it with the proximal step
+ * (FP32 and TF32 plans whose p2 p1 and n3 are multiples of 4), that one kernel; ms[3] the
+ * proximal step (0 when it is part of ms[2]).  Each kernel runs 2 + reps times back to
  * back; ms (HOST, 4 doubles) receives the mean of the last reps launches in milliseconds.  Uses
  * q->V as the weights and the plan's FP64 state of the last fit (values do not change the work).
  * Synchronizes the plan's stream. */

@@ -1,0 +1,269 @@
+// The last G stage and the inner PG step of the fit path in one kernel.
+//
+// After the fused slab kernel has left S_b (n3 x p2p1, FP32), one inner iteration of Sec. 3.2
+// still needs Q = X_3^T S_b (mode 3 of Eq. nineteen) and the prox step on every coordinate
+// m = (j3, n):  g = g_k + Q / n,  y = x + omega_l (x - x_prev),  x+ = soft(y - delta g,
+// delta lambda w_m)  (Sec. 6.3), the next correction x+ + omega_{l+1} (x+ - x) - theta_k, and the
+// stop criterion max |x+ - y|.  Each CTA owns a tile of TJ rows j3 x 32 columns n of Q and sums
+// it over every i3 itself, so no split partials go through memory and no second kernel is
+// launched.  The i3 range streams through shared memory in chunks of up to 256 rows: a 2-D
+// tensor copy of S_b (box 32 x KC) and one of X_3^T (box KC x TJ) per chunk, double-buffered,
+// with bounded mbarrier waits.  Lane = column, warp = an eighth of each chunk's rows; the eight
+// warp partials are added in warp order in FP64 (the same bits on every run).  The operands of
+// the prox step and the loop state are loaded at kernel start, behind the chunk copies.  The
+// criterion ends in the last-block-done protocol of the prox kernel (glam_elementwise.cu) on the
+// same control block.
+#include <cuda.h>
+
+#include <cstdint>
+
+#include "glam_internal.cuh"
+#include "glam_tma.cuh"
+
+namespace glam {
+namespace {
+
+using namespace tma;
+
+constexpr int kAPThreads = 256;
+constexpr int kAPWarps = kAPThreads / 32;
+constexpr int kAPMaxRows = 8;   // rows j3 of a tile, at most
+constexpr int kAPMaxChunk = 256;  // rows i3 of a chunk, at most (tensor-copy box limit)
+constexpr int kAPMaxSmem = 2 * (kAPMaxChunk * 32 + kAPMaxChunk * kAPMaxRows) * 4;
+
+struct APShape {
+  int n3, p3, P21;
+  int TJ;      // rows j3 of a tile
+  int nx;      // column tiles
+  int KC;      // rows i3 per chunk (a multiple of 8 warps x 4)
+  int nchunk;  // chunks of the i3 range
+};
+
+__device__ double ap_block_max(double v) {
+  __shared__ double sh[kAPWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double m = 0.0;
+  for (int w = 0; w < kAPWarps; ++w) m = fmax(m, sh[w]);
+  return m;
+}
+
+template <int TJ>
+__global__ void __launch_bounds__(kAPThreads)
+adjprox_kernel(APShape sh, const __grid_constant__ CUtensorMap mapS, const __grid_constant__ CUtensorMap mapX,
+               const double* __restrict__ gk, const double* __restrict__ x, const double* xp,
+               const double* __restrict__ pen, double* out, float* __restrict__ dnext,
+               const double* __restrict__ anchor, double inv_n, InnerCtl* ctl, int* err) {
+  if (ctl->done) return;  // written by the preceding kernels: the same value in every thread
+  // the loop state of this iteration; the last CTA changes it only after every CTA has arrived
+  const int l = ctl->l;
+  const double delta = ctl->delta, lam = ctl->lambda;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ uint64_t mbar[2];
+  __shared__ int timed_out;
+  __shared__ bool is_last;
+  float* const base = reinterpret_cast<float*>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int KC = sh.KC, nchunk = sh.nchunk, P21 = sh.P21;
+  const int tn = blockIdx.x % sh.nx, tj = blockIdx.x / sh.nx;
+  const int n0 = 32 * tn, j0 = TJ * tj;
+  const int stage = KC * 32 + KC * TJ;  // floats per buffer: S chunk [KC][32], X chunk [TJ][KC]
+  const uint32_t bytes = (uint32_t)stage * 4u;
+  if (tid == 0) {
+    timed_out = 0;
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto issue = [&](int c, int b) {  // called by thread 0
+    float* dst = base + (int64_t)b * stage;
+    fence_proxy_async();
+    mbar_expect_tx(&mbar[b], bytes);
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(&mapS)), "r"(n0), "r"(c * KC), "r"(smem_u32(&mbar[b]))
+        : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst + KC * 32)),
+        "l"(reinterpret_cast<uint64_t>(&mapX)), "r"(c * KC), "r"(j0), "r"(smem_u32(&mbar[b]))
+        : "memory");
+  };
+  if (tid == 0) {
+    issue(0, 0);
+    if (nchunk > 1) issue(1, 1);
+  }
+  // the prox operands of this thread's coordinate (at most one: TJ x 32 <= 256), loaded now
+  const int jo = tid / 32, co = tid - jo * 32;
+  const int j3o = j0 + jo, no = n0 + co;
+  const bool mine = tid < TJ * 32 && j3o < sh.p3 && no < P21;
+  const int64_t mo = (int64_t)j3o * P21 + no;
+  double xm = 0.0, xpm = 0.0, gm = 0.0, pm = 0.0, am = 0.0;
+  if (mine) {
+    xm = x[mo];
+    xpm = xp[mo];
+    gm = gk[mo];
+    pm = pen[mo];
+    am = anchor[mo];
+  }
+  // ---- Q(j0 + j, n0 + lane) over this warp's rows of every chunk (rows past n3 read zeros) ----
+  float acc[TJ];
+#pragma unroll
+  for (int j = 0; j < TJ; ++j) acc[j] = 0.f;
+  const int RW = KC / kAPWarps;  // rows of a chunk per warp (a multiple of 4)
+  for (int c = 0; c < nchunk; ++c) {
+    const int b = c & 1;
+    if (!mbar_wait_bounded(&mbar[b], (uint32_t)((c >> 1) & 1))) atomicOr(&timed_out, 1);
+    __syncthreads();
+    if (timed_out) break;  // read after the barrier that follows every write to it
+    const float* Sc = base + (int64_t)b * stage;
+    const float* Xc = Sc + KC * 32;
+    const int r0 = warp * RW;
+    // four rows i3 per step: their S_b values for this lane's column, and for each j3 the four
+    // X_3 entries as one broadcast float4; the sums run in row order
+#pragma unroll 2
+    for (int r = r0; r < r0 + RW; r += 4) {
+      const float s0 = Sc[r * 32 + lane], s1 = Sc[(r + 1) * 32 + lane];
+      const float s2 = Sc[(r + 2) * 32 + lane], s3 = Sc[(r + 3) * 32 + lane];
+#pragma unroll
+      for (int j = 0; j < TJ; ++j) {
+        const float4 xv = *reinterpret_cast<const float4*>(Xc + j * KC + r);
+        acc[j] = fmaf(xv.x, s0, acc[j]);
+        acc[j] = fmaf(xv.y, s1, acc[j]);
+        acc[j] = fmaf(xv.z, s2, acc[j]);
+        acc[j] = fmaf(xv.w, s3, acc[j]);
+      }
+    }
+    __syncthreads();  // every warp is done with buffer b
+    if (tid == 0 && c + 2 < nchunk) issue(c + 2, b);
+  }
+  // ---- the warp partials, added in warp order (FP64), then the prox step per coordinate ----
+  float* red = base;  // [warp][TJ][32], over buffer 0 (free after the loop's last barrier)
+#pragma unroll
+  for (int j = 0; j < TJ; ++j) red[(warp * TJ + j) * 32 + lane] = acc[j];
+  __syncthreads();
+  const double omega = double(l - 1) / double(l + 2), omega_next = double(l) / double(l + 3);
+  double crit = 0.0;
+  if (!timed_out && mine) {
+    double q = 0.0;
+    for (int w = 0; w < kAPWarps; ++w) q += (double)red[(w * TJ + jo) * 32 + co];
+    const double g = gm + q * inv_n;            // gradient of the quadratic model
+    const double y = xm + omega * (xm - xpm);   // extrapolation, Sec. 3.2
+    const double z = y - delta * g;
+    const double az = fabs(z) - delta * lam * pm;  // soft threshold, Sec. 6.3
+    const double xn = az > 0.0 ? copysign(az, z) : 0.0;
+    out[mo] = xn;
+    dnext[mo] = (float)(xn + omega_next * (xn - xm) - am);
+    crit = fabs(xn - y);
+  }
+  // ---- stop criterion: the prox kernel's last-block-done protocol on the same control block ----
+  const double bm = ap_block_max(crit);
+  if (tid == 0) {
+    if (timed_out) atomicOr(err, 1);
+    atomicMax(&ctl->crit_bits, (unsigned long long)__double_as_longlong(bm));
+    __threadfence();
+    is_last = (atomicAdd(&ctl->counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (is_last && tid == 0) {
+    const double cv = __longlong_as_double((long long)atomicAdd(&ctl->crit_bits, 0ull));
+    ctl->crit = cv;
+    ctl->iters_run += 1;
+    if (cv <= ctl->stop_abs) {
+      ctl->done = 1;
+      ctl->stop_reason = 1;
+    } else if (ctl->l >= ctl->max_iter) {
+      ctl->done = 1;
+      ctl->stop_reason = 2;
+    }
+    ctl->l += 1;
+    ctl->crit_bits = 0ull;
+    ctl->counter = 0u;
+  }
+  if (timed_out && tid == 0) {  // copies still in flight land before the CTA leaves
+    mbar_wait_bounded(&mbar[0], 0u);
+    mbar_wait_bounded(&mbar[1], 0u);
+  }
+}
+
+bool ap_configure(int n3, int p3, int P21, APShape& sh, size_t& smem) {
+  if (n3 < 1 || p3 < 1 || P21 < 1 || P21 % 4 != 0 || n3 % 4 != 0) return false;
+  sh.n3 = n3;
+  sh.p3 = p3;
+  sh.P21 = P21;
+  sh.nx = (P21 + 31) / 32;
+  int gy = (num_sms() + sh.nx - 1) / sh.nx;  // about one tile per SM
+  if (gy > p3) gy = p3;
+  if (gy < 1) gy = 1;
+  sh.TJ = (p3 + gy - 1) / gy;
+  if (sh.TJ > kAPMaxRows) sh.TJ = kAPMaxRows;
+  const int kc = ((n3 + 31) / 32) * 32;  // 32 rows per warp step keeps every warp's share whole
+  sh.KC = kc < kAPMaxChunk ? kc : kAPMaxChunk;
+  sh.nchunk = (n3 + sh.KC - 1) / sh.KC;
+  smem = (size_t)2 * (sh.KC * 32 + sh.KC * sh.TJ) * 4;
+  return true;
+}
+
+int g_ap_ready = 0;
+
+template <int TJ>
+cudaError_t ap_prepare_one() {
+  return cudaFuncSetAttribute(adjprox_kernel<TJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAPMaxSmem);
+}
+
+}  // namespace
+
+int adjprox_supported(int n3, int p3, int P21, const float* X3T, const float* Sb) {
+  APShape sh;
+  size_t smem;
+  auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) % 16) == 0; };
+  return ap_configure(n3, p3, P21, sh, smem) && al16(X3T) && al16(Sb) ? 1 : 0;
+}
+
+cudaError_t launch_adjprox(int n3, int p3, int P21, const float* X3T, const float* Sb, const double* gk,
+                           const double* x, const double* xp, const double* pen, double* out,
+                           float* dnext, const double* anchor, double inv_n, InnerCtl* ctl, int* err,
+                           cudaStream_t s) {
+  APShape sh;
+  size_t smem;
+  if (!adjprox_supported(n3, p3, P21, X3T, Sb) || !ap_configure(n3, p3, P21, sh, smem))
+    return cudaErrorInvalidValue;
+  if (!g_ap_ready) {  // the largest tile any shape can ask for: two chunks of 256 rows, 8 rows j3
+    cudaError_t e = ap_prepare_one<1>();
+    if (e == cudaSuccess) e = ap_prepare_one<2>();
+    if (e == cudaSuccess) e = ap_prepare_one<3>();
+    if (e == cudaSuccess) e = ap_prepare_one<4>();
+    if (e == cudaSuccess) e = ap_prepare_one<5>();
+    if (e == cudaSuccess) e = ap_prepare_one<6>();
+    if (e == cudaSuccess) e = ap_prepare_one<7>();
+    if (e == cudaSuccess) e = ap_prepare_one<8>();
+    if (e != cudaSuccess) return e;
+    g_ap_ready = 1;
+  }
+  alignas(64) CUtensorMap mapS, mapX;
+  // S_b: rows i3 of p2p1 floats, boxes of 32 columns x KC rows; X_3^T: rows j3 of n3 floats,
+  // boxes of KC columns x TJ rows
+  if (!encode_map_2d(&mapS, Sb, (uint64_t)P21, (uint64_t)n3, (uint64_t)P21 * 4, 32, (uint32_t)sh.KC) ||
+      !encode_map_2d(&mapX, X3T, (uint64_t)n3, (uint64_t)p3, (uint64_t)n3 * 4, (uint32_t)sh.KC,
+                     (uint32_t)sh.TJ))
+    return cudaErrorInvalidValue;
+  const int blocks = sh.nx * ((p3 + sh.TJ - 1) / sh.TJ);
+  switch (sh.TJ) {
+#define GLAM_AP(tj)                                                                                \
+  case tj:                                                                                         \
+    adjprox_kernel<tj><<<blocks, kAPThreads, smem, s>>>(sh, mapS, mapX, gk, x, xp, pen, out, dnext, \
+                                                        anchor, inv_n, ctl, err);                  \
+    break;
+    GLAM_AP(1) GLAM_AP(2) GLAM_AP(3) GLAM_AP(4) GLAM_AP(5) GLAM_AP(6) GLAM_AP(7) GLAM_AP(8)
+#undef GLAM_AP
+    default: return cudaErrorInvalidValue;
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace glam

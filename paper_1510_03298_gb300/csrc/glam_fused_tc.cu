@@ -783,6 +783,21 @@ int fused_tc_supported(int n1, int n2, int n3, int p1, int p2, int p3, int split
   return tc_configure(n1, n2, n3, p1, p2, p3, grid, split, sh, threads, smem, NB, NCT) ? 1 : 0;
 }
 
+int encode_map_2d(CUtensorMap* m, const float* base, uint64_t dim0, uint64_t dim1, uint64_t stride1,
+                  uint32_t box0, uint32_t box1) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
+  if (fn == nullptr) return 0;
+  const cuuint64_t dims[2] = {dim0, dim1};
+  const cuuint64_t strides[1] = {stride1};
+  const cuuint32_t box[2] = {box0, box1};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS
+             ? 1
+             : 0;
+}
+
 int fused_tc_pointers_ok(const float* Cst, const float* D, const float* V) {
   auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) % 16) == 0; };
   return al16(Cst) && al16(D) && al16(V) ? 1 : 0;

@@ -5,6 +5,7 @@
 // (column-major n_j x p_j).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -112,6 +113,24 @@ int fused_tc_supported(int n1, int n2, int n3, int p1, int p2, int p3, int split
 // Cst, D and V are bulk-copied by the kernel: each must start on a 16-byte boundary
 int fused_tc_pointers_ok(const float* Cst, const float* D, const float* V);
 cudaError_t fused_tc_prepare();
+
+// A 2-D FP32 tensor map without swizzle (dims {dim0, dim1}, row stride stride1 bytes, box
+// {box0, box1}; elements outside the tensor read as zero); 1 on success, 0 otherwise.
+int encode_map_2d(CUtensorMap* m, const float* base, uint64_t dim0, uint64_t dim1, uint64_t stride1,
+                  uint32_t box0, uint32_t box1);
+
+// ------------------------------------------------------------------------------------
+// Last G stage (mode 3 of Eq. nineteen) and the inner PG step of Sec. 3.2 in one kernel, for the
+// FP32 products of the fit path: Q = X_3^T S_b (p3 x p2p1, every i3 summed in the CTA that owns
+// the entry), then the prox step of launch_prox with lin = g_k, lin_scale = 1 and the anchor
+// theta_k (x, xp, out, gk, pen, anchor FP64; dnext FP32).  adjprox_supported tells whether the
+// shape and pointers allow its tensor copies.
+// ------------------------------------------------------------------------------------
+int adjprox_supported(int n3, int p3, int P21, const float* X3T, const float* Sb);
+cudaError_t launch_adjprox(int n3, int p3, int P21, const float* X3T, const float* Sb, const double* gk,
+                           const double* x, const double* xp, const double* pen, double* out,
+                           float* dnext, const double* anchor, double inv_n, InnerCtl* ctl, int* err,
+                           cudaStream_t s);
 
 // ------------------------------------------------------------------------------------
 // Elementwise / reduction kernels.
