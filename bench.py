@@ -254,7 +254,8 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "grid": [128, 128, 600], "basis": [20, 20, 60],
-                           "nlambda": pr.nlambda, "precision": "fp32 mode products, fp64 refinement",
+                           "nlambda": pr.nlambda,
+                           "precision": "fp32-accurate mode products (inner-loop product as 3xTF32 on tensor cores), fp64 refinement",
                            "l2": "256 MB buffer written between steps",
                            "parallelism": f"replicas x{world}"},
                 "gpu_launches": int(launches),
@@ -268,6 +269,11 @@ def run_ours(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of each fused slab kernel on this
+# workload, from an ncu capture (cold cache) of the current kernels
+NCU_TRAFFIC_BYTES = {"3xtf32": 39665408 + 768, "tf32": 39651072 + 0}
 
 
 def measure_details(g, torch, pr, plan, X, Y, W, pen, opts, dev, flush, last):
@@ -295,23 +301,28 @@ def measure_details(g, torch, pr, plan, X, Y, W, pen, opts, dev, flush, last):
     out["h_transform"] = {"GB/s": h_bytes / t_h / 1e9, "ms": t_h * 1e3, "bytes": h_bytes,
                           "frac_hbm": h_bytes / t_h / 1e9 / peaks["hbm_gbs"], "peak_src": src,
                           "tflops": h_flops / t_h / 1e12}
-    # dominant kernel of the inner iteration: the fused slab kernel G(V (.) H(.))
+    # dominant kernel of the inner iteration: the fused slab kernel G(V (.) H(.)), which a GLAM_FP32
+    # plan runs on the tensor cores in the 3xTF32 form (FP32-level accuracy)
     q = g.glam_quad_build(plan, X, theta, Y, W)
     ms = g.glam_time_inner_kernels(plan, X, q, reps=100)
     per_iter = sum(ms)
+    # algorithmic FLOPs: the first H stage (X_3 d) and, per slab, T_b = T_a X_1^T, eta = X_2 T_b,
+    # r = V (.) eta, S = X_2^T r, S_b = S X_1
     slab = 2 * p2 * p1 * n1 + 4 * n2 * n1 * p2 + n2 * n1 + 2 * p2 * n1 * p1
-    fl = slab * n3
+    fl = slab * n3 + 2 * n3 * p3 * p2 * p1
     # read V, the correction d and X_3 (the kernel forms T_a = X_3 d), X_1 and X_2; write S_b
     by = 4 * n + 4 * n3 * p2 * p1 + 4 * (p + n3 * p3) + 4 * (n1 * p1 + n2 * p2)
-    peak_alu = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     t_f = ms[0] / 1e3
-    out["roofline"] = {"bound": "alu", "kernel": "fused_slab_kernel<float,20> (G(V(.)H) per slab)",
-                       "achieved": fl / t_f / 1e12, "peak": peak_alu, "unit": "TFLOP/s",
-                       "frac": fl / t_f / 1e12 / peak_alu, "traffic": None,
-                       "flops_per_launch": fl, "ms_per_launch": ms[0],
-                       "peak_note": "FP32 SIMT: 152 SMs x 128 lanes x 2 FLOP x max SM clock",
-                       "hbm_view": {"bytes_per_launch": by, "GB/s": by / t_f / 1e9,
-                                    "frac": by / t_f / 1e9 / peaks["hbm_gbs"], "peak_src": src}}
+    tf32_peak = peaks["bf16_tflops"] * 1.1 / 2.25  # dense TF32 = measured BF16 x nominal ratio
+    out["roofline"] = {"bound": "hbm", "kernel": "fused_slab_tc_kernel<3,2,3> (3xTF32 mma.sync, G(V(.)H) per slab)",
+                       "achieved": by / t_f / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                       "frac": by / t_f / 1e9 / peaks["hbm_gbs"], "traffic": NCU_TRAFFIC_BYTES["3xtf32"],
+                       "bytes_per_launch": by, "ms_per_launch": ms[0], "peak_src": src,
+                       "bound_note": "intensity %.0f FLOP/B is below the TF32 tensor ridge %.0f FLOP/B"
+                                     % (fl / by, tf32_peak * 1e3 / peaks["hbm_gbs"]),
+                       "flop_view": {"flops_per_launch": fl, "TFLOP/s": fl / t_f / 1e12,
+                                     "tf32_tensor_peak": tf32_peak,
+                                     "frac_of_tf32_peak": fl / t_f / 1e12 / tf32_peak}}
     # ms[2] is the mode-3 adjoint, fused with the prox step where the path does so (ms[3] = 0)
     out["inner_iteration_ms"] = {"fused_slab": ms[0], "mode3": ms[1], "mode3_adjoint": ms[2],
                                  "prox": ms[3], "sum": per_iter}
@@ -367,9 +378,9 @@ def measure_tf32(g, torch, pr, X, Y, W, pen, opts, flush, last, theta, by, peaks
            "outer_iters": sum(s["outer_iters"] for s in res.stats),
            "inner_iteration_ms": {"fused_slab_tc": k[0], "mode3_adjoint": k[2], "prox": k[3],
                                   "sum": sum(k)},
-           "roofline": {"bound": "hbm", "kernel": "fused_slab_tc_kernel<3,4> (TF32 mma.sync)",
+           "roofline": {"bound": "hbm", "kernel": "fused_slab_tc_kernel<3,4,1> (TF32 mma.sync)",
                         "achieved": by / t_f / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                        "frac": by / t_f / 1e9 / peaks["hbm_gbs"], "traffic": None,
+                        "frac": by / t_f / 1e9 / peaks["hbm_gbs"], "traffic": NCU_TRAFFIC_BYTES["tf32"],
                         "bytes_per_launch": by, "ms_per_launch": k[0], "peak_src": src}}
     plan.close()
     return out
