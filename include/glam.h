@@ -195,6 +195,23 @@ int glam_fit_path(glam_plan* plan, const void* const X[3], const void* Y, const 
                   const void* pen_w, int nlambda, double* lambda, const glam_opts* opts,
                   const double* Theta0, double* Theta_path, glam_stats* stats, int* nfit);
 
+/* Penalized negative log-likelihood F(Theta) = f(Theta) + lambda sum_m pen_w[m] |theta_m| (the
+ * PMLE objective of Sec. 2, Eq. five, scaled by 1/n as stated above) and its vector-Jacobian
+ * product, the adjoint used by automatic differentiation:
+ *   grad_Theta = g (grad f(Theta) + lambda pen_w (.) sign(Theta)),  grad f = -(1/n) G(u) with u
+ *                the score of App. B, Eq. (four), at eta = H(Theta) (Eqs. three, eighteen,
+ *                nineteen); sign(0) = 0 (the zero element of the subdifferential);
+ *   grad_Y     = g df/dY: (1/n) a (y - eta) (Gaussian) or -(1/n) a eta (Poisson), the derivative
+ *                of the loss constants stated above;
+ * g = *gout (a DEVICE double, the upstream derivative of a scalar function of F) or 1 when gout
+ * is NULL.  Theta, pen_w, grad_Theta: p elements; Y, W, grad_Y: n elements (plan element type).
+ * F: DEVICE double or NULL; grad_Theta, grad_Y: written when not NULL (at least one output must
+ * be requested).  lambda >= 0.  Asynchronous; FP64 accumulation for F.
+ * Errors: GLAM_EINVAL (NULL inputs, no output, bad lambda), GLAM_ECUDA. */
+int glam_penalized_nll(glam_plan* plan, const void* const X[3], const void* Theta, const void* Y,
+                       const void* W, double lambda, const void* pen_w, const double* gout,
+                       double* F, void* grad_Theta, void* grad_Y);
+
 /* ---- allocation-free entry point (the paper has no counterpart) ----
  *
  * f(eta) = (1/n) sum_i a_i l_i(eta_i, y_i), the loss of glam_loss (constants as stated at the

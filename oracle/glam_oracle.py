@@ -198,6 +198,16 @@ def loss(family, eta, y, a) -> float:
     return f
 
 
+def loss_grad_y(family, eta, y, a) -> np.ndarray:
+    """df/dy_i of `loss` at fixed eta: Eq. (two) is linear in y with coefficient a_i theta(eta_i),
+    so -(1/n) a_i eta_i (canonical link), plus (1/n) a_i y_i from the Gaussian constant of R3."""
+    n = np.asarray(eta).size
+    g = -a * eta / n
+    if family == GAUSSIAN:
+        g = g + a * y / n
+    return g
+
+
 # --------------------------------------------------------------------------------------
 # Penalty and proximal operator (Sec. 6.3)
 # --------------------------------------------------------------------------------------
@@ -286,6 +296,13 @@ def gradient(data: GlamData, theta) -> np.ndarray:
     eta = H(data.Xs, theta)
     u = score(data.family, eta, data.Y, data.a)
     return -G(data.Xs, u) / data.n
+
+
+def penalized_gradient(data: GlamData, theta, lam) -> np.ndarray:
+    """grad f(theta) + lambda omega (.) sign(theta): the gradient of F (Eq. five) in every
+    coordinate with theta_m != 0; where theta_m = 0 it takes sign(0) = 0, one element of the
+    subdifferential of the l1 term."""
+    return gradient(data, theta) + lam * data.pen_w * np.sign(theta)
 
 
 def lambda_max(data: GlamData) -> float:

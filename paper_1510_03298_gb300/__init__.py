@@ -25,7 +25,7 @@ __all__ = [
     "GLAM_TF32", "GLAM_BF16", "GlamError", "Plan", "Quad", "FitResult", "library_path", "load_library",
     "glam_opts_default", "glam_plan_create", "glam_plan_destroy", "glam_predict", "glam_gradient",
     "glam_loss", "glam_quad_build", "glam_prox_step", "glam_fit_path", "glam_launch_count",
-    "glam_time_inner_kernels",
+    "glam_time_inner_kernels", "glam_penalized_nll", "PenalizedNLL", "penalized_nll",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -113,6 +113,7 @@ def load_library():
         "glam_fit_path": (C.c_int, [_VP, _X3, _VP, _VP, _VP, C.c_int, C.POINTER(C.c_double),
                                     C.POINTER(GlamOpts), _VP, _VP, C.POINTER(GlamStats),
                                     C.POINTER(C.c_int)]),
+        "glam_penalized_nll": (C.c_int, [_VP, _X3, _VP, _VP, _VP, C.c_double, _VP, _VP, _VP, _VP, _VP]),
         "glam_launch_count": (C.c_int64, []),
         "glam_time_inner_kernels": (C.c_int, [_VP, _X3, C.POINTER(GlamQuadC), C.c_int,
                                               C.POINTER(C.c_double)]),
@@ -396,3 +397,69 @@ def glam_time_inner_kernels(plan: Plan, X, quad: Quad, reps: int = 50):
     qc = quad.c()
     _check(load_library().glam_time_inner_kernels(plan.handle, xs, C.byref(qc), int(reps), ms), plan.handle)
     return list(ms)
+
+
+def glam_penalized_nll(plan: Plan, X, Theta, Y, W, lam: float, pen_w, gout=None, want_F=True,
+                       grad_Theta=None, grad_Y=None, want_grads=False):
+    """F(Theta) = f(Theta) + lam * sum pen_w |Theta| (Sec. 2, Eq. five, 1/n scaling) and, with
+    want_grads, the vector-Jacobian product with the upstream scalar gout (0-d float64 CUDA tensor,
+    or None for 1): gout * dF/dTheta and gout * dF/dY.  Returns (F or None, grad_Theta, grad_Y)."""
+    plan._sync_stream()
+    x = plan._X(X)
+    plan._arr(Theta, plan.coef_shape(), "Theta")
+    plan._arr(Y, plan.cells_shape(), "Y")
+    plan._arr(W, plan.cells_shape(), "W")
+    plan._arr(pen_w, plan.coef_shape(), "pen_w")
+    dev = Theta.device
+    if gout is not None:
+        if (not isinstance(gout, torch.Tensor) or gout.dtype != torch.float64 or gout.numel() != 1
+                or gout.device.type != "cuda"):
+            raise TypeError("gout must be a one-element float64 CUDA tensor")
+        gout = gout.contiguous()
+    F = torch.empty((), dtype=torch.float64, device=dev) if want_F else None
+    if want_grads:
+        if grad_Theta is None:
+            grad_Theta = torch.empty(plan.coef_shape(), dtype=plan.dtype, device=dev)
+        if grad_Y is None:
+            grad_Y = torch.empty(plan.cells_shape(), dtype=plan.dtype, device=dev)
+    if grad_Theta is not None:
+        plan._arr(grad_Theta, plan.coef_shape(), "grad_Theta")
+    if grad_Y is not None:
+        plan._arr(grad_Y, plan.cells_shape(), "grad_Y")
+    _check(load_library().glam_penalized_nll(plan.handle, x, _ptr(Theta), _ptr(Y), _ptr(W), float(lam),
+                                             _ptr(pen_w), _ptr(gout), _ptr(F), _ptr(grad_Theta),
+                                             _ptr(grad_Y)), plan.handle)
+    return F, grad_Theta, grad_Y
+
+
+class PenalizedNLL(torch.autograd.Function):
+    """The penalized negative log-likelihood F(Theta, Y) = f + lam * J as a differentiable torch
+    function of Theta and Y.  Both passes run in libglam: the forward pass is H (Eq. eighteen), the
+    family loss (App. B) and the penalty; the backward pass is the hand-written adjoint (the
+    transposed H-transform G of Eq. nineteen applied to the score, plus the derivative of the
+    loss in Y and lam * pen_w * sign(Theta), with sign(0) = 0) scaled by the upstream gradient."""
+
+    @staticmethod
+    def forward(ctx, Theta, Y, plan, X, W, lam, pen_w):
+        F, _, _ = glam_penalized_nll(plan, X, Theta.detach(), Y.detach(), W, lam, pen_w)
+        ctx.plan, ctx.X, ctx.W, ctx.lam, ctx.pen_w = plan, X, W, lam, pen_w
+        ctx.save_for_backward(Theta.detach(), Y.detach())
+        return F
+
+    @staticmethod
+    def backward(ctx, gF):
+        Theta, Y = ctx.saved_tensors
+        need_t, need_y = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        if not (need_t or need_y):
+            return (None,) * 7
+        plan = ctx.plan
+        gT = torch.empty(plan.coef_shape(), dtype=plan.dtype, device=Theta.device) if need_t else None
+        gY = torch.empty(plan.cells_shape(), dtype=plan.dtype, device=Theta.device) if need_y else None
+        glam_penalized_nll(plan, ctx.X, Theta, Y, ctx.W, ctx.lam, ctx.pen_w,
+                           gout=gF.to(torch.float64), want_F=False, grad_Theta=gT, grad_Y=gY)
+        return gT, gY, None, None, None, None, None
+
+
+def penalized_nll(plan: Plan, X, Theta, Y, W, lam: float, pen_w):
+    """Differentiable F(Theta, Y) (0-d float64 CUDA tensor); see PenalizedNLL."""
+    return PenalizedNLL.apply(Theta, Y, plan, X, W, float(lam), pen_w)

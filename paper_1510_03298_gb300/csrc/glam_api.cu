@@ -536,6 +536,39 @@ int glam_loss(glam_plan* pl, const void* const X[3], const void* Theta, const vo
 }
 
 namespace {
+template <typename T>
+int nll_impl(glam_plan* pl, const void* const X[3], const T* Theta, const T* Y, const T* W,
+             double lambda, const T* pen_w, const double* gout, double* F, T* gTheta, T* gY) {
+  Ops<T> op(pl, pl->stream, X);
+  const bool vjp_theta = gTheta != nullptr;
+  CKS(op.H(Theta, op.w.eta));
+  CK(launch_nll_cells<T>(pl->family, pl->n, op.w.eta, Y, W, gout, vjp_theta ? op.w.U : nullptr, gY,
+                         pl->sc, pl->red, pl->stream));
+  if (vjp_theta) CKS(op.G(op.w.U, op.w.grad));
+  CK(launch_nll_coef<T>(pl->p, Theta, pen_w, lambda, gout, op.w.grad, gTheta, F, pl->sc, pl->red,
+                        pl->stream));
+  return GLAM_OK;
+}
+}  // namespace
+
+int glam_penalized_nll(glam_plan* pl, const void* const X[3], const void* Theta, const void* Y,
+                       const void* W, double lambda, const void* pen_w, const double* gout,
+                       double* F, void* grad_Theta, void* grad_Y) {
+  CKS(check_plan(pl));
+  CKS(validate_X(pl, X));
+  if (!Theta || !Y || !W || !pen_w) return fail(pl, GLAM_EINVAL, "glam_penalized_nll: NULL array");
+  if (!F && !grad_Theta && !grad_Y)
+    return fail(pl, GLAM_EINVAL, "glam_penalized_nll: no output requested");
+  if (!(lambda >= 0.0) || !std::isfinite(lambda))
+    return fail(pl, GLAM_EINVAL, "glam_penalized_nll: lambda must be finite and >= 0");
+  if (pl->precision == GLAM_FP64)
+    return nll_impl<double>(pl, X, (const double*)Theta, (const double*)Y, (const double*)W, lambda,
+                            (const double*)pen_w, gout, F, (double*)grad_Theta, (double*)grad_Y);
+  return nll_impl<float>(pl, X, (const float*)Theta, (const float*)Y, (const float*)W, lambda,
+                         (const float*)pen_w, gout, F, (float*)grad_Theta, (float*)grad_Y);
+}
+
+namespace {
 
 
 template <typename T>

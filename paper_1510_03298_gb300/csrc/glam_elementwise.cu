@@ -225,6 +225,98 @@ loss_kernel(int family, int64_t n, const T* __restrict__ eta, const T* __restric
   }
 }
 
+// ---------------------------------------------------------------- penalized NLL and its VJP
+// Cells pass of the penalized negative log-likelihood (Sec. 2, Eqs. two/three; App. B): reduces
+// f(eta) and, for the vector-Jacobian product with the upstream scalar g (*gout, 1 if NULL),
+// writes U = -(g/n) u (so that G(U) = g grad_theta f, Eq. nineteen) and
+// GY = g df/dy: (1/n) a (y - eta) for the Gaussian loss, -(1/n) a eta for the Poisson loss.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+nll_cells_kernel(int family, int64_t n, const T* __restrict__ eta, const T* __restrict__ Y,
+                 const T* __restrict__ A, const double* __restrict__ gout, T* __restrict__ U,
+                 T* __restrict__ GY, DevScalars* sc, RedScratch red) {
+  const double g = gout ? *gout : 1.0;
+  const T su = T(-g / (double)n), sy = T(g / (double)n);
+  double lsum = 0.0;
+  int bad = 0;
+  const int64_t tile = (int64_t)gridDim.x * blockDim.x * kEPT;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kEPT; base < n; base += tile) {
+    T lpart = T(0);
+#pragma unroll
+    for (int k = 0; k < kEPT; ++k) {
+      const int64_t i = base + (int64_t)k * blockDim.x + threadIdx.x;
+      if (i >= n) break;
+      const T e = eta[i], y = Y[i], a = A[i];
+      T u, dy;
+      if (family == GLAM_GAUSSIAN_IDENTITY) {
+        const T r = y - e;
+        u = a * r;
+        dy = a * r;
+        lpart += T(0.5) * a * r * r;
+      } else {
+        T ec = e;
+        if (ec > poisson_clamp<T>()) {
+          ec = poisson_clamp<T>();
+          bad = 1;
+        }
+        const T mu = t_exp<T>(ec);
+        u = a * (y - mu);
+        dy = -a * e;
+        lpart += a * (mu - y * e);
+      }
+      if (!(isfinite(e) && isfinite(y) && isfinite(a))) bad = 1;
+      if (U != nullptr) U[i] = su * u;
+      if (GY != nullptr) GY[i] = sy * dy;
+    }
+    lsum += (double)lpart;
+  }
+  double v[1] = {lsum};
+  block_sum<1>(v);
+  if (threadIdx.x == 0) {
+    red.partial[blockIdx.x] = v[0];
+    if (bad) atomicOr(&sc->nonfinite, 1);
+  }
+  if (last_block(red.counter)) {
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (unsigned int b = 0; b < gridDim.x; ++b) s += __ldcg(&red.partial[b]);
+      sc->loss = s / (double)n;
+      *red.counter = 0u;
+    }
+  }
+}
+
+// Coefficient pass: J(theta) = sum_m w_m |theta_m| (FP64), F = f + lambda J, and the penalty part
+// of the VJP, grad[m] = Q[m] + g lambda w_m sign(theta_m) (sign(0) = 0; Q = g grad f from G).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+nll_coef_kernel(int64_t p, const T* __restrict__ th, const T* __restrict__ pw, double lambda,
+                const double* __restrict__ gout, const T* __restrict__ Q, T* __restrict__ grad,
+                double* F, DevScalars* sc, RedScratch red) {
+  const double g = gout ? *gout : 1.0;
+  double acc[1] = {0.0};
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < p;
+       m += (int64_t)gridDim.x * blockDim.x) {
+    const double t = (double)th[m], w = (double)pw[m];
+    acc[0] += w * fabs(t);
+    if (grad != nullptr) {
+      const double sg = t > 0.0 ? 1.0 : (t < 0.0 ? -1.0 : 0.0);
+      grad[m] = T((double)Q[m] + g * lambda * w * sg);
+    }
+  }
+  block_sum<1>(acc);
+  if (threadIdx.x == 0) red.partial[blockIdx.x] = acc[0];
+  if (last_block(red.counter)) {
+    if (threadIdx.x == 0) {
+      double pen = 0.0;
+      for (unsigned int b = 0; b < gridDim.x; ++b) pen += __ldcg(&red.partial[b]);
+      sc->pen = pen;
+      if (F != nullptr) *F = sc->loss + lambda * pen;
+      *red.counter = 0u;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- scale / convert / finite
 template <typename T>
 __global__ void scale_kernel(int64_t n, const T* __restrict__ in, T* __restrict__ out, T scale) {
@@ -653,6 +745,26 @@ cudaError_t launch_loss_only(int family, int64_t n, const T* eta, const T* Y, co
 }
 
 template <typename T>
+cudaError_t launch_nll_cells(int family, int64_t n, const T* eta, const T* Y, const T* A,
+                             const double* gout, T* U, T* GY, DevScalars* sc, RedScratch red,
+                             cudaStream_t s) {
+  nll_cells_kernel<T><<<red_blocks(n, kEPT), kThreads, 0, s>>>(family, n, eta, Y, A, gout, U, GY,
+                                                               sc, red);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_nll_coef(int64_t p, const T* theta, const T* pen_w, double lambda,
+                            const double* gout, const T* Q, T* grad, double* F, DevScalars* sc,
+                            RedScratch red, cudaStream_t s) {
+  nll_coef_kernel<T><<<red_blocks(p, 1), kThreads, 0, s>>>(p, theta, pen_w, lambda, gout, Q, grad,
+                                                           F, sc, red);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_scale(int64_t n, const T* in, T* out, double scale, cudaStream_t s) {
   scale_kernel<T><<<grid_for(n), kThreads, 0, s>>>(n, in, out, T(scale));
   count_launches(1);
@@ -782,6 +894,12 @@ cudaError_t launch_gram(int nj, int pj, const double* XT, double* gram, cudaStre
   template cudaError_t launch_loss_only<T>(int, int64_t, const T*, const T*, const T*, double*,   \
                                            RedScratch, cudaStream_t);                             \
   template cudaError_t launch_scale<T>(int64_t, const T*, T*, double, cudaStream_t);              \
+  template cudaError_t launch_nll_cells<T>(int, int64_t, const T*, const T*, const T*,           \
+                                           const double*, T*, T*, DevScalars*, RedScratch,         \
+                                           cudaStream_t);                                          \
+  template cudaError_t launch_nll_coef<T>(int64_t, const T*, const T*, double, const double*,     \
+                                          const T*, T*, double*, DevScalars*, RedScratch,          \
+                                          cudaStream_t);                                           \
   template cudaError_t launch_check_finite<T>(int64_t, const T*, DevScalars*, cudaStream_t);      \
   template cudaError_t launch_vmul<T>(int64_t, const T*, T*, const int*, cudaStream_t);           \
   template cudaError_t launch_sum_splits<T>(int64_t, int, const T*, T*, cudaStream_t);            \

@@ -195,6 +195,18 @@ cudaError_t launch_vmul(int64_t n, const T* V, T* x, const int* skip, cudaStream
 template <typename T>
 cudaError_t launch_check_finite(int64_t n, const T* x, DevScalars* sc, cudaStream_t s);
 
+// Penalized negative log-likelihood and its vector-Jacobian product (glam_penalized_nll): the
+// cells pass (loss f into sc->loss, U = -(g/n) u, GY = g df/dy) and the coefficient pass
+// (J(theta) into sc->pen, F = f + lambda J, grad = Q + g lambda w sign(theta)); g = *gout or 1.
+template <typename T>
+cudaError_t launch_nll_cells(int family, int64_t n, const T* eta, const T* Y, const T* A,
+                             const double* gout, T* U, T* GY, DevScalars* sc, RedScratch red,
+                             cudaStream_t s);
+template <typename T>
+cudaError_t launch_nll_coef(int64_t p, const T* theta, const T* pen_w, double lambda,
+                            const double* gout, const T* Q, T* grad, double* F, DevScalars* sc,
+                            RedScratch red, cudaStream_t s);
+
 template <typename T>
 cudaError_t launch_loss_only(int family, int64_t n, const T* eta, const T* Y, const T* A,
                              double* out, RedScratch red, cudaStream_t s);
