@@ -169,6 +169,14 @@ struct Ops {
 
   // eta = H(<X_j>, Theta)   (Sec. 6.1, Eq. eighteen)
   int H(const T* theta, T* eta) {
+    if constexpr (sizeof(T) == 4) {
+      if (predict_tiles_supported((int)pl->p1, (int)pl->p2) && mode3_rows_supported((int)pl->p3)) {
+        CK(launch_mode3_rows((int)pl->n3, (int)pl->p3, (int)(pl->p2 * pl->p1), X[2], theta, w.Ta, s));
+        CK(launch_predict_tiles((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2,
+                                X[0], X[1], w.Ta, eta, s));
+        return GLAM_OK;
+      }
+    }
     CK(launch_gemm<T, T>(d_mode3_fwd(pl), X[2], theta, w.Ta, s));
     CK(launch_gemm<T, T>(d_mode1_fwd(pl), w.Ta, X[0], w.Tb, s));
     CK(launch_gemm<T, T>(d_mode2_fwd(pl), X[1], w.Tb, eta, s));

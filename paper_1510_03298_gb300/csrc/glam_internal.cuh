@@ -114,6 +114,16 @@ int fused_tc_supported(int n1, int n2, int n3, int p1, int p2, int p3, int split
 int fused_tc_pointers_ok(const float* Cst, const float* D, const float* V);
 cudaError_t fused_tc_prepare();
 
+// The last two stages of H for FP32 (modes 1 and 2, Sec. 6.1, Eq. eighteen) in one kernel:
+// eta[i3] = X_2 (T_a[i3] X_1^T) per slab, T_a (n3 x p2p1) from the mode-3 product.
+int predict_tiles_supported(int p1, int p2);
+cudaError_t launch_predict_tiles(int n1, int n2, int n3, int p1, int p2, const float* XT1,
+                                 const float* XT2, const float* Ta, float* eta, cudaStream_t s);
+// Its first stage, T_a (n3 x P21) = X_3 (n3 x p3) . Theta (p3 x P21), for p3 <= 64.
+int mode3_rows_supported(int p3);
+cudaError_t launch_mode3_rows(int n3, int p3, int P21, const float* XT3, const float* Theta,
+                              float* Ta, cudaStream_t s);
+
 // A 2-D FP32 tensor map without swizzle (dims {dim0, dim1}, row stride stride1 bytes, box
 // {box0, box1}; elements outside the tensor read as zero); 1 on success, 0 otherwise.
 int encode_map_2d(CUtensorMap* m, const float* base, uint64_t dim0, uint64_t dim1, uint64_t stride1,

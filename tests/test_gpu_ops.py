@@ -26,8 +26,16 @@ def _problem(seed, n, p, fam=gen.GAUSSIAN, mask=0.0):
     return gen.random_problem(seed, n, p, fam, mask_frac=mask, basis="normal")
 
 
+# extra shapes for H: several 128-row blocks in i2 with a ragged n1 (scalar stores), p1 = p3
+# limits of the FP32 slab kernels, and p3 = 65 (the mode-3 GEMM path)
+PREDICT_SHAPES = SHAPES + [
+    ((131, 257, 5), (32, 31, 64)),
+    ((132, 130, 6), (3, 32, 65)),
+]
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("n,p", SHAPES)
+@pytest.mark.parametrize("n,p", PREDICT_SHAPES)
 def test_predict(prec, n, p):
     torch, g = gpu_or_skip()
     pr = _problem(1, n, p)
