@@ -6,7 +6,9 @@ Armijo line search, FP64 KKT test to 1e-6 at every lambda) on the synthetic work
 cubic B-spline bases p = (20, 20, 60), FP32 mode products.  The headline value is prox-grad
 (inner PG) iterations per second over the timed steps; the line also carries the H-transform
 GB/s of glam_predict, the FP64 GPU path on a bounded sample of the same path, the roofline of
-the dominant kernel, the FP64 CPU oracle baseline and an end-to-end figure with host buffers.
+the dominant kernel, the FP64 CPU oracle baseline, an end-to-end figure with host buffers, and
+the batched form: 64 independent fits of uneven shapes through glam_fit_path_batched against the
+plain FP32 path fitting them one after another.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -244,6 +246,8 @@ def run_ours(args):
     if rank == 0:
         extra = measure_details(g, torch, pr, plan, X, Y, W, pen, opts, dev, flush, results[-1])
         extra["e2e"] = measure_e2e(g, torch, pr, plan, opts, dev, args.steps)
+        if args.batched > 0:
+            extra["batched"] = measure_batched(g, torch, args.batched, args.batched_baseline)
         if world == 1 and not args.no_cpu:
             extra["cpu_baseline"] = cpu_baseline()
     if dist is not None:
@@ -428,6 +432,42 @@ def measure_e2e(g, torch, pr, plan, opts, dev, steps):
     return {"value": iters / t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
 
+def measure_batched(g, torch, nfit, nbase):
+    """The 64-fit workload (grid sides U{32..96}, p_j U{8..24}, Gaussian or Poisson, 20-lambda
+    paths to KKT 1e-6, FP32 plans) through glam_fit_path_batched, against the plain FP32 path fitting
+    the first nbase of the same problems one after another.  Throughput in fits/s and in inner PG
+    iterations/s (the sequential leg covers a subset, so the speedup is taken on iterations/s)."""
+    import gen
+    probs = gen.make_workload(4, nfit=nfit)
+    f32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+    bps = [g.BatchProblem(g.Plan(pr.n, pr.p, pr.family, g.GLAM_FP32), [f32(x) for x in pr.XT], f32(pr.Y),
+                          f32(pr.W), torch.tensor(pr.pen_w, dtype=torch.float64, device="cuda"),
+                          nlambda=pr.nlambda) for pr in probs]
+    opts = g.glam_opts_default(tol=1e-6, lambda_min_ratio=1e-3)
+
+    def run(items, threads):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = g.glam_fit_path_batched(items, opts=opts, max_threads=threads)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        its = sum(sum(st["inner_iters"] for st in r.stats) for r in res)
+        kkt = max(max(st["kkt"] for st in r.stats) for r in res)
+        ok = all(r.status == g.GLAM_OK for r in res)
+        return dt, its, kkt, ok
+
+    dt_b, it_b, kkt_b, ok_b = run(bps, 16)
+    nb = max(1, min(nbase, nfit))
+    dt_s, it_s, kkt_s, ok_s = run(bps[:nb], 1)
+    return {"fits": nfit, "nlambda": probs[0].nlambda, "threads": 16, "wall_s": dt_b,
+            "fits_per_s": nfit / dt_b, "inner_iters": it_b, "inner_iters_per_s": it_b / dt_b,
+            "max_kkt": kkt_b, "converged": ok_b,
+            "sequential_fp32_path": {"fits": nb, "wall_s": dt_s, "fits_per_s": nb / dt_s,
+                                     "inner_iters_per_s": it_s / dt_s, "max_kkt": kkt_s, "converged": ok_s},
+            "speedup_iters_per_s": (it_b / dt_b) / (it_s / dt_s),
+            "form": "each fit on its own plan and stream, 16 native host worker threads"}
+
+
 def run_kernels(reps, precision="fp32"):
     """Diagnostic mode for profilers: build the 128x128x600 plan and launch the four kernels of
     one inner iteration 2 + reps times each (glam_time_inner_kernels); prints their mean times.
@@ -457,6 +497,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
+    ap.add_argument("--batched", type=int, default=64, metavar="NFIT",
+                    help="fits of the batched-path measurement (0: skip it)")
+    ap.add_argument("--batched-baseline", type=int, default=8, metavar="NFIT",
+                    help="fits of its sequential plain-FP32-path baseline")
     ap.add_argument("--kernels", type=int, default=0, metavar="REPS",
                     help="diagnostic: launch the inner-iteration kernels REPS times for a profiler")
     ap.add_argument("--kernels-precision", choices=["fp32", "tf32"], default="fp32",

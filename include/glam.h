@@ -100,8 +100,19 @@ typedef struct {
   int32_t max_linesearch;  /* Armijo trials per outer iteration (default 30) */
   int32_t check_every;     /* inner iterations per captured CUDA graph chunk, i.e. between host
                               reads of the device stop flag (default 32, rounded up to even) */
-  int32_t reserved[6];
+  int32_t iwls;            /* weights of the inner problem (the package's iwls option, Sec. 6.4):
+                              GLAM_IWLS_EXACT (default) uses the IRLS weights of App. B as they are;
+                              GLAM_IWLS_KRON uses their tensor-product form (Sec. 6.2, Eq.
+                              kronweight): X^T W X theta = H(<X_j^T W_j X_j>, theta), so the inner
+                              loop touches p-sized arrays only.  GLAM_IWLS_KRON is exact, and
+                              accepted, for the Gaussian family with an observation-weight array W
+                              that is a tensor product w1 (x) w2 (x) w3 with W(0,0,0) > 0 (W = 1
+                              included); otherwise glam_fit_path returns GLAM_EINVAL */
+  int32_t reserved[5];
 } glam_opts;
+
+#define GLAM_IWLS_EXACT 0
+#define GLAM_IWLS_KRON 1
 
 /* Per-lambda record written by glam_fit_path (HOST array of nlambda entries). */
 typedef struct {
@@ -211,6 +222,36 @@ int glam_fit_path(glam_plan* plan, const void* const X[3], const void* Y, const 
 int glam_penalized_nll(glam_plan* plan, const void* const X[3], const void* Theta, const void* Y,
                        const void* W, double lambda, const void* pen_w, const double* gout,
                        double* F, void* grad_Theta, void* grad_Y);
+
+/* One problem of a batch: the arguments of glam_fit_path for one plan (same meaning, layout and
+ * ownership), plus its two outputs. */
+typedef struct {
+  const void* X[3];
+  const void* Y;
+  const void* W;
+  const void* pen_w;       /* DOUBLE, p elements */
+  int32_t nlambda;
+  double* lambda;          /* HOST, nlambda (in/out as in glam_fit_path) */
+  const double* Theta0;    /* p doubles or NULL */
+  double* Theta_path;      /* nlambda * p doubles (written) */
+  glam_stats* stats;       /* HOST, nlambda records, or NULL */
+  int32_t nfit;            /* out: completed lambdas */
+  int32_t status;          /* out: the status glam_fit_path returned for this problem */
+} glam_batch_item;
+
+/* Many independent penalized GLAM fits (cross-validation folds, bootstrap replicates, separate
+ * data sets; each a warm-started lambda path of Alg. 1 / Sec. 6.4) run concurrently on one GPU:
+ * item i is fitted with plans[i], whose shape, family and precision it must match, by up to
+ * max_threads host worker threads (max_threads <= 0: one per item, at most the number of host
+ * cores), each fit on its plan's private stream, so the small kernels of different fits overlap
+ * on the device.  plans: HOST array of nitems distinct plans (a plan serves one fit at a time).
+ * items: HOST array of nitems records (outputs nfit and status written).  opts: HOST, NULL for
+ * defaults, shared by every item.  Returns when every fit has finished: GLAM_OK if every item's
+ * status is GLAM_OK, else the status of the lowest-numbered failing item (its message:
+ * glam_last_error(plans[i])).  Errors: GLAM_EINVAL (NULL arrays, nitems < 0, a repeated plan;
+ * message from glam_last_error(NULL)). */
+int glam_fit_path_batched(int nitems, glam_plan* const* plans, glam_batch_item* items,
+                          const glam_opts* opts, int max_threads);
 
 /* ---- allocation-free entry point (the paper has no counterpart) ----
  *

@@ -246,6 +246,29 @@ def lipschitz_exact(Xs, w) -> float:
 
 
 # --------------------------------------------------------------------------------------
+# Tensor-product weights (Sec. 6.2, Eq. kronweight): W = w_1 (x) ... (x) w_d
+# --------------------------------------------------------------------------------------
+
+def tensor_weight_grams(Xs, ws):
+    """The p_j x p_j matrices X_j^T diag(w_j) X_j of Eq. (kronweight)."""
+    return [np.asarray(X, dtype=np.float64).T @ (np.asarray(w, dtype=np.float64)[:, None] * X)
+            for X, w in zip(Xs, ws)]
+
+
+def xtwx_tensor(Xs, ws, theta) -> np.ndarray:
+    """X^T W X theta for W = w_1 (x) ... (x) w_d, as H(<X_j^T W_j X_j>, theta) (Eq. kronweight):
+    the array transform of Eq. (eighteen) with the marginal matrices replaced by the weighted
+    Gram matrices, so that only p-sized arrays are touched."""
+    return H(tensor_weight_grams(Xs, ws), theta)
+
+
+def lipschitz_tensor(Xs, ws, n) -> float:
+    """The exact L = ||X^T W X||_2 / n for tensor-product W: (1/n) prod_j varrho(X_j^T W_j X_j),
+    since the spectrum of a Kronecker product is the set of products of the factors' spectra."""
+    return math.prod(float(np.max(np.abs(np.linalg.eigvalsh(M)))) for M in tensor_weight_grams(Xs, ws)) / n
+
+
+# --------------------------------------------------------------------------------------
 # Problem container in paper layout
 # --------------------------------------------------------------------------------------
 

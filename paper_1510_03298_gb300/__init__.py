@@ -22,10 +22,11 @@ import torch
 __all__ = [
     "GLAM_OK", "GLAM_EINVAL", "GLAM_ENOMEM", "GLAM_ECUDA", "GLAM_ENONFINITE", "GLAM_ENOCONV",
     "GLAM_ETIMEOUT", "GLAM_GAUSSIAN_IDENTITY", "GLAM_POISSON_LOG", "GLAM_FP64", "GLAM_FP32",
-    "GLAM_TF32", "GLAM_BF16", "GlamError", "Plan", "Quad", "FitResult", "library_path", "load_library",
+    "GLAM_TF32", "GLAM_BF16", "GLAM_IWLS_EXACT", "GLAM_IWLS_KRON", "GlamError", "Plan", "Quad", "FitResult", "library_path", "load_library",
     "glam_opts_default", "glam_plan_create", "glam_plan_destroy", "glam_predict", "glam_gradient",
     "glam_loss", "glam_quad_build", "glam_prox_step", "glam_fit_path", "glam_launch_count",
     "glam_time_inner_kernels", "glam_penalized_nll", "PenalizedNLL", "penalized_nll",
+    "BatchProblem", "glam_fit_path_batched",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -56,6 +57,8 @@ GLAM_FP64 = _K["GLAM_FP64"]
 GLAM_FP32 = _K["GLAM_FP32"]
 GLAM_TF32 = _K["GLAM_TF32"]
 GLAM_BF16 = _K["GLAM_BF16"]
+GLAM_IWLS_EXACT = _K["GLAM_IWLS_EXACT"]
+GLAM_IWLS_KRON = _K["GLAM_IWLS_KRON"]
 
 
 class GlamDims(C.Structure):
@@ -70,7 +73,15 @@ class GlamOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("lambda_min_ratio", C.c_double), ("inner_forcing", C.c_double),
                 ("inner_floor", C.c_double), ("armijo_alpha0", C.c_double), ("armijo_b", C.c_double),
                 ("armijo_v", C.c_double), ("max_inner", C.c_int32), ("max_outer", C.c_int32),
-                ("max_linesearch", C.c_int32), ("check_every", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("max_linesearch", C.c_int32), ("check_every", C.c_int32), ("iwls", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
+
+
+class GlamBatchItem(C.Structure):
+    _fields_ = [("X", C.c_void_p * 3), ("Y", C.c_void_p), ("W", C.c_void_p), ("pen_w", C.c_void_p),
+                ("nlambda", C.c_int32), ("lambda_", C.POINTER(C.c_double)), ("Theta0", C.c_void_p),
+                ("Theta_path", C.c_void_p), ("stats", C.c_void_p), ("nfit", C.c_int32),
+                ("status", C.c_int32)]
 
 
 class GlamStats(C.Structure):
@@ -114,6 +125,8 @@ def load_library():
                                     C.POINTER(GlamOpts), _VP, _VP, C.POINTER(GlamStats),
                                     C.POINTER(C.c_int)]),
         "glam_penalized_nll": (C.c_int, [_VP, _X3, _VP, _VP, _VP, C.c_double, _VP, _VP, _VP, _VP, _VP]),
+        "glam_fit_path_batched": (C.c_int, [C.c_int, C.POINTER(_VP), C.POINTER(GlamBatchItem),
+                                            C.POINTER(GlamOpts), C.c_int]),
         "glam_launch_count": (C.c_int64, []),
         "glam_time_inner_kernels": (C.c_int, [_VP, _X3, C.POINTER(GlamQuadC), C.c_int,
                                               C.POINTER(C.c_double)]),
@@ -463,3 +476,73 @@ class PenalizedNLL(torch.autograd.Function):
 def penalized_nll(plan: Plan, X, Theta, Y, W, lam: float, pen_w):
     """Differentiable F(Theta, Y) (0-d float64 CUDA tensor); see PenalizedNLL."""
     return PenalizedNLL.apply(Theta, Y, plan, X, W, float(lam), pen_w)
+
+
+@dataclass
+class BatchProblem:
+    """One fit of a batch: its plan and the arguments of glam_fit_path (device tensors)."""
+    plan: Plan
+    X: list
+    Y: torch.Tensor
+    W: torch.Tensor
+    pen_w: torch.Tensor
+    nlambda: int = 10
+    lambdas: Optional[list] = None
+    Theta0: Optional[torch.Tensor] = None
+
+
+def _stats_list(st):
+    return [dict(lam=s.lambda_, objective=s.objective, kkt=s.kkt, time_ms=s.time_ms,
+                 outer_iters=s.outer_iters, inner_iters=s.inner_iters, fp64_passes=s.fp64_passes,
+                 armijo_backtracks=s.armijo_backtracks, nnz=s.nnz, status=s.status) for s in st]
+
+
+def glam_fit_path_batched(problems: Sequence[BatchProblem], opts: Optional[GlamOpts] = None,
+                          max_threads: int = 0) -> List[FitResult]:
+    """Independent lambda paths of many problems run concurrently (glam_fit_path_batched).  Each
+    problem needs its own plan.  Returns one FitResult per problem (status GLAM_ENOCONV results
+    included); raises GlamError for argument errors and for failures other than ENOCONV."""
+    lib = load_library()
+    n = len(problems)
+    items = (GlamBatchItem * n)()
+    plans = (_VP * n)()
+    keep = []
+    for i, pb in enumerate(problems):
+        pl = pb.plan
+        pl._sync_stream()
+        x = pl._X(pb.X)
+        pl._arr(pb.Y, pl.cells_shape(), "Y")
+        pl._arr(pb.W, pl.cells_shape(), "W")
+        _p64(pb.pen_w, pl.coef_shape(), "pen_w")
+        if pb.Theta0 is not None:
+            _p64(pb.Theta0, pl.coef_shape(), "Theta0")
+        nl = len(pb.lambdas) if pb.lambdas is not None else pb.nlambda
+        lam = (C.c_double * nl)(*([-1.0] * nl if pb.lambdas is None else [float(v) for v in pb.lambdas]))
+        path = torch.empty((nl,) + pl.coef_shape(), dtype=torch.float64, device=pb.Y.device)
+        st = (GlamStats * nl)()
+        keep.append((lam, path, st))
+        it = items[i]
+        for j in range(3):
+            it.X[j] = x[j]
+        it.Y, it.W, it.pen_w = _ptr(pb.Y), _ptr(pb.W), _ptr(pb.pen_w)
+        it.nlambda = nl
+        it.lambda_ = C.cast(lam, C.POINTER(C.c_double))
+        it.Theta0 = _ptr(pb.Theta0)
+        it.Theta_path = path.data_ptr()
+        it.stats = C.cast(st, C.c_void_p)
+        plans[i] = pl.handle
+    o = opts if opts is not None else glam_opts_default()
+    status = lib.glam_fit_path_batched(n, plans, items, C.byref(o), int(max_threads))
+    if status == GLAM_EINVAL and all(it.status == 0 and it.nfit == 0 for it in items):
+        msg = lib.glam_last_error(None)
+        raise GlamError(status, msg.decode() if msg else "")
+    out = []
+    for i, pb in enumerate(problems):
+        lam, path, st = keep[i]
+        it = items[i]
+        msg = lib.glam_last_error(pb.plan.handle)
+        msg = msg.decode() if msg else ""
+        if it.status not in (GLAM_OK, GLAM_ENOCONV):
+            raise GlamError(it.status, f"problem {i}: {msg}")
+        out.append(FitResult(list(lam), path, _stats_list(st), it.nfit, it.status, msg))
+    return out

@@ -15,6 +15,7 @@
 // same control block.
 #include <cuda.h>
 
+#include <atomic>
 #include <cstdint>
 
 #include "glam_internal.cuh"
@@ -208,7 +209,7 @@ bool ap_configure(int n3, int p3, int P21, APShape& sh, size_t& smem) {
   return true;
 }
 
-int g_ap_ready = 0;
+std::atomic<int> g_ap_ready{0};
 
 template <int TJ>
 cudaError_t ap_prepare_one() {

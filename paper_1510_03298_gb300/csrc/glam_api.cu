@@ -32,6 +32,10 @@ struct Work {
   T* one = nullptr;                        // the 1 x 1 design of a d = 2 problem
   T* dn = nullptr;                         // y - theta_k of the next inner iteration (p)
   T* yx = nullptr;                         // extrapolated point of a standalone prox step (p)
+  // tensor-product weights (Sec. 6.2): M_j = X_j^T W_j X_j in the working precision and the
+  // p-space intermediates of H(<M_j>, d)
+  T* Mk[3] = {nullptr, nullptr, nullptr};
+  T *kTa = nullptr, *kTb = nullptr, *kQ = nullptr;
   bool ready = false;
 };
 
@@ -64,6 +68,9 @@ struct glam_plan {
   DevScalars* h_sc = nullptr;
   double* h_gram = nullptr;
   double* d_gram = nullptr;        // p_j x p_j Gram scratch (p_j <= 64)
+  double* kfac[3] = {nullptr, nullptr, nullptr};  // factors of a tensor-product W (n_j each)
+  double* kgram = nullptr;         // the FP64 weighted Gram matrices, p1^2 + p2^2 + p3^2
+  unsigned long long* kcheck = nullptr;
   std::vector<void*> allocs;
 };
 
@@ -145,6 +152,21 @@ GemmDesc d_mode3_adj(const glam_plan* pl, int ksplit) {
   const int64_t P21 = pl->p2 * pl->p1;
   return mk((int)pl->p3, (int)P21, (int)pl->n3, 1, ksplit, 0, pl->n3, 1, 0, P21, 1, 0, P21, 1,
             pl->p3 * P21);
+}
+
+// H(<M_j>, d) with the p_j x p_j matrices M_j of tensor-product weights: the three forward
+// stages above with every n_j replaced by p_j (M_j is stored like a design, as (p_j, p_j))
+GemmDesc k_mode3_fwd(const glam_plan* pl) {
+  const int64_t P21 = pl->p2 * pl->p1;
+  return mk((int)pl->p3, (int)P21, (int)pl->p3, 1, 1, 0, 1, pl->p3, 0, P21, 1, 0, P21, 1, 0);
+}
+GemmDesc k_mode1_fwd(const glam_plan* pl) {
+  return mk((int)(pl->p3 * pl->p2), (int)pl->p1, (int)pl->p1, 1, 1, 0, pl->p1, 1, 0, pl->p1, 1, 0,
+            pl->p1, 1, 0);
+}
+GemmDesc k_mode2_fwd(const glam_plan* pl) {
+  return mk((int)pl->p2, (int)pl->p1, (int)pl->p2, (int)pl->p3, 1, 0, 1, pl->p2, pl->p2 * pl->p1,
+            pl->p1, 1, pl->p2 * pl->p1, pl->p1, 1, 0);
 }
 
 template <typename T>
@@ -717,6 +739,7 @@ struct Fit {
   const double* W64 = nullptr;
   cudaGraphExec_t graph = nullptr;
   int64_t graph_kernels = 0;
+  bool kron = false;  // inner loop on the tensor-product form H(<M_j>, .) (Sec. 6.2)
   ~Fit() {
     if (graph) cudaGraphExecDestroy(graph);
   }
@@ -758,6 +781,24 @@ int capture_chunk(Fit<T>& f) {
   for (int it = 0; it < C && st == GLAM_OK; ++it) {
     double* x = (it % 2 == 0) ? pl->x0 : pl->x1;
     double* xp = (it % 2 == 0) ? pl->x1 : pl->x0;
+    if (f.kron) {
+      // X^T W X d = H(<M_j>, d) on p-sized arrays (Sec. 6.2, Eq. kronweight), then the prox step
+      Work<T>& w = op.w;
+      const int* skip = &pl->ctl->done;
+      cudaError_t e = launch_gemm<T, T>(k_mode3_fwd(pl), w.Mk[2], w.dn, w.kTa, f.s, nullptr, nullptr,
+                                        nullptr, 0.0, skip);
+      if (e == cudaSuccess)
+        e = launch_gemm<T, T>(k_mode1_fwd(pl), w.kTa, w.Mk[0], w.kTb, f.s, nullptr, nullptr, nullptr,
+                              0.0, skip);
+      if (e == cudaSuccess)
+        e = launch_gemm<T, T>(k_mode2_fwd(pl), w.Mk[1], w.kTb, w.kQ, f.s, nullptr, nullptr, nullptr,
+                              0.0, skip);
+      if (e == cudaSuccess)
+        e = launch_prox<T, double>(pl->p, 1, w.kQ, pl->gk, 1.0, x, xp, pl->pen, xp, 1.0 / (double)pl->n,
+                                   pl->ctl, 0.0, 0.0, 0.0, nullptr, f.s, w.dn, pl->th);
+      if (e != cudaSuccess) st = fail(pl, GLAM_ECUDA, std::string("inner iteration launch: ") + cudaGetErrorString(e));
+      continue;
+    }
     bool use_tc = false, use_ap = false;
     if constexpr (sizeof(T) == 4) {
       use_tc = pl->tc_split && fused_tc_pointers_ok(pl->tc_cst, op.w.dn, op.w.V);
@@ -903,6 +944,58 @@ int solve_lambda(Fit<T>& f, double lambda, LamOut& lo) {
   }
 }
 
+// Set-up of the tensor-product form (Sec. 6.2): checks that the weight array of the inner problem
+// is a tensor product (for the Gaussian family it is W itself), forms M_j = X_j^T diag(w_j) X_j in
+// FP64 and in the working precision, and returns prod_j varrho(M_j), which times 1/n is the exact
+// Lipschitz constant of the inner problem (Sec. 5, the case of tensor-product weights).
+template <typename T>
+int kron_setup(Fit<T>& f, const T* W, double& rho_kron, double& wmax) {
+  glam_plan* pl = f.pl;
+  if (pl->family != GLAM_GAUSSIAN_IDENTITY)
+    return fail(pl, GLAM_EINVAL, "iwls = GLAM_IWLS_KRON needs tensor-product IRLS weights: the Gaussian family");
+  Work<T>& w = work_of<T>(pl);
+  const int64_t pj[3] = {pl->p1, pl->p2, pl->p3};
+  const int64_t nj[3] = {pl->n1, pl->n2, pl->n3};
+  if (pl->kgram == nullptr) {
+    for (int j = 0; j < 3; ++j) CKS(dalloc(pl, &pl->kfac[j], nj[j]));
+    CKS(dalloc(pl, &pl->kgram, pj[0] * pj[0] + pj[1] * pj[1] + pj[2] * pj[2]));
+    CKS(dalloc(pl, &pl->kcheck, 2));
+  }
+  if (w.kQ == nullptr) {
+    for (int j = 0; j < 3; ++j) CKS(dalloc(pl, &w.Mk[j], pj[j] * pj[j]));
+    CKS(dalloc(pl, &w.kTa, pl->p));
+    CKS(dalloc(pl, &w.kTb, pl->p));
+    CKS(dalloc(pl, &w.kQ, pl->p));
+  }
+  CK(launch_kron_factors<T>(pl->n1, pl->n2, pl->n3, W, pl->kfac[0], pl->kfac[1], pl->kfac[2],
+                            pl->kcheck, f.s));
+  unsigned long long chk[2] = {0ull, 0ull};
+  double w000 = 0.0;
+  CK(cudaMemcpyAsync(chk, pl->kcheck, sizeof(chk), cudaMemcpyDeviceToHost, f.s));
+  CK(cudaMemcpyAsync(&w000, f.W64, sizeof(double), cudaMemcpyDeviceToHost, f.s));
+  CK(cudaStreamSynchronize(f.s));
+  double dev_max, w_max;
+  std::memcpy(&dev_max, &chk[0], sizeof(double));
+  std::memcpy(&w_max, &chk[1], sizeof(double));
+  if (!(w000 > 0.0) || !(dev_max <= 1e-6 * w_max))
+    return fail(pl, GLAM_EINVAL, "iwls = GLAM_IWLS_KRON needs W = w1 (x) w2 (x) w3 with W(0,0,0) > 0");
+  wmax = w_max;
+  rho_kron = 1.0;
+  int64_t off = 0;
+  for (int j = 0; j < 3; ++j) {
+    const double* Xd = (const double*)f.X64[j];
+    if (Xd == nullptr) Xd = pl->wd.one;  // d = 2: the 1 x 1 design
+    CK(launch_weighted_gram((int)nj[j], (int)pj[j], Xd, pl->kfac[j], pl->kgram + off, f.s));
+    CK(launch_convert<double, T>(pj[j] * pj[j], pl->kgram + off, w.Mk[j], f.s));
+    std::vector<double> M((size_t)(pj[j] * pj[j]));
+    CK(cudaMemcpyAsync(M.data(), pl->kgram + off, sizeof(double) * M.size(), cudaMemcpyDeviceToHost, f.s));
+    CK(cudaStreamSynchronize(f.s));
+    rho_kron *= jacobi_spectral_radius(M, (int)pj[j]);
+    off += pj[j] * pj[j];
+  }
+  return GLAM_OK;
+}
+
 template <typename T>
 int fit_impl(glam_plan* pl, const void* const X[3], const T* Y, const T* W, const double* pen,
              int nlambda, double* lambda, const glam_opts& o, const double* Theta0, double* path,
@@ -947,6 +1040,14 @@ int fit_impl(glam_plan* pl, const void* const X[3], const T* Y, const T* W, cons
     const double* Xd[3] = {(const double*)f.X64[0], (const double*)f.X64[1], (const double*)f.X64[2]};
     if (Xd[2] == nullptr) Xd[2] = pl->wd.one;
     CKS(rho_product_from<double>(pl, Xd, f.s, f.rho_prod));
+  }
+  if (o.iwls == GLAM_IWLS_KRON) {
+    // the family pass sets L_hat = max(w)/n * rho_prod; with rho_prod = prod_j varrho(M_j) / max(w)
+    // it is the exact constant prod_j varrho(M_j) / n of tensor-product weights
+    double rho_kron = 1.0, wmax = 1.0;
+    CKS(kron_setup<T>(f, W, rho_kron, wmax));
+    f.kron = true;
+    f.rho_prod = rho_kron / wmax;
   }
   // lambda_max (Sec. 6.4): g(0) = -(1/n) G(U(eta = 0)), in FP64
   {
@@ -1033,7 +1134,8 @@ int glam_fit_path(glam_plan* pl, const void* const X[3], const void* Y, const vo
   if (o.check_every % 2) o.check_every += 1;
   if (o.max_inner < 1 || o.max_outer < 1 || o.max_linesearch < 1 || !(o.tol > 0) ||
       !(o.inner_forcing > 0) || !(o.inner_floor > 0) || !(o.armijo_b > 0 && o.armijo_b < 1) ||
-      !(o.armijo_v > 0 && o.armijo_v < 1) || !(o.armijo_alpha0 > 0))
+      !(o.armijo_v > 0 && o.armijo_v < 1) || !(o.armijo_alpha0 > 0) ||
+      !(o.iwls == GLAM_IWLS_EXACT || o.iwls == GLAM_IWLS_KRON))
     return fail(pl, GLAM_EINVAL, "glam_fit_path: bad options");
   if (lambda[0] >= 0)
     for (int k = 0; k < nlambda; ++k)

@@ -706,14 +706,15 @@ int grid_for(int64_t n) {
 
 namespace {
 std::atomic<int64_t> g_launches{0};
-std::atomic<int> g_capturing{0};
+// a stream capture runs in one host thread; fits of a batch capture from several threads at once
+thread_local int g_capturing = 0;
 }  // namespace
 
 void count_launches(int64_t k) {
-  if (g_capturing.load(std::memory_order_relaxed) == 0) g_launches.fetch_add(k, std::memory_order_relaxed);
+  if (g_capturing == 0) g_launches.fetch_add(k, std::memory_order_relaxed);
 }
 int64_t launch_count() { return g_launches.load(); }
-void set_capturing(bool on) { g_capturing.store(on ? 1 : 0); }
+void set_capturing(bool on) { g_capturing = on ? 1 : 0; }
 
 int num_sms() {
   static int cached = 0;

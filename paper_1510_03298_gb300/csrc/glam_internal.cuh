@@ -142,6 +142,15 @@ cudaError_t launch_adjprox(int n3, int p3, int P21, const float* X3T, const floa
                            float* dnext, const double* anchor, double inv_n, InnerCtl* ctl, int* err,
                            cudaStream_t s);
 
+// Tensor-product weights (Sec. 6.2, Eq. kronweight): the factors w1 (n1), w2 (n2), w3 (n3) of W
+// read off its first row, column and tube, and check[0] = max |W - w1 w2 w3|, check[1] = max |W|
+// (doubles as bits); the FP64 weighted Gram matrix M = X_j^T diag(w) X_j (pj x pj).
+template <typename T>
+cudaError_t launch_kron_factors(int64_t n1, int64_t n2, int64_t n3, const T* W, double* w1, double* w2,
+                                double* w3, unsigned long long* check, cudaStream_t s);
+cudaError_t launch_weighted_gram(int nj, int pj, const double* XT, const double* w, double* M,
+                                 cudaStream_t s);
+
 // ------------------------------------------------------------------------------------
 // Elementwise / reduction kernels.
 // ------------------------------------------------------------------------------------

@@ -81,3 +81,17 @@ def test_no_cpu_fallback_without_gpu():
         pytest.skip("a GPU is present")
     with pytest.raises(RuntimeError):
         g.Plan((5, 5, 5), (4, 4, 4), g.GLAM_GAUSSIAN_IDENTITY, g.GLAM_FP32)
+
+
+def test_batched_fit_checks_its_arguments_without_a_gpu(lib):
+    import paper_1510_03298_gb300 as g
+    assert lib.glam_fit_path_batched(0, None, None, None, 0) == g.GLAM_OK
+    assert lib.glam_fit_path_batched(-1, None, None, None, 0) == g.GLAM_EINVAL
+    assert lib.glam_fit_path_batched(2, None, None, None, 0) == g.GLAM_EINVAL
+    items = (g.GlamBatchItem * 2)()
+    plans = (C.c_void_p * 2)(None, None)
+    assert lib.glam_fit_path_batched(2, plans, items, None, 0) == g.GLAM_EINVAL
+    assert b"NULL plan" in lib.glam_last_error(None)
+    plans = (C.c_void_p * 2)(4096, 4096)  # never dereferenced: the repeat is found first
+    assert lib.glam_fit_path_batched(2, plans, items, None, 0) == g.GLAM_EINVAL
+    assert b"twice" in lib.glam_last_error(None)
