@@ -360,6 +360,7 @@ def measure_details(g, torch, pr, plan, X, Y, W, pen, opts, dev, flush, last):
                             "status": r64.status, "max_kkt": max(s["kkt"] for s in r64.stats),
                             "fp32_iters_same_lambdas": it32, "fp64_iters": it64}
     plan64.close()
+    out["kron_path"] = measure_kron(g, torch, pr, X, Y, W, pen, opts, flush, last)
     out["tf32_path"] = measure_tf32(g, torch, pr, X, Y, W, pen, opts, flush, last, theta, by, peaks, src)
     return out
 
@@ -399,6 +400,43 @@ def measure_tf32(g, torch, pr, X, Y, W, pen, opts, flush, last, theta, by, peaks
                         "achieved": by / t_f / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                         "frac": by / t_f / 1e9 / peaks["hbm_gbs"], "traffic": NCU_TRAFFIC_BYTES["tf32"],
                         "bytes_per_launch": by, "ms_per_launch": k[0], "peak_src": src}}
+    plan.close()
+    return out
+
+
+def measure_kron(g, torch, pr, X, Y, W, pen, opts, flush, last):
+    """The tensor-product-weight form of the inner loop (iwls kron, Sec. 6.2): W = 1 here, so
+    X^T W X = (x)_j X_j^T X_j exactly and every inner iteration works on p-sized arrays.  The
+    same 50-lambda path with an FP32 plan, timed like a bench step, against the exact-weight FP32
+    path at the same KKT tolerance."""
+    import ctypes
+    plan = g.Plan(pr.n, pr.p, pr.family, g.GLAM_FP32)
+    ko = g.GlamOpts()
+    ctypes.pointer(ko)[0] = opts
+    ko.iwls = g.GLAM_IWLS_KRON
+    g.glam_fit_path(plan, X, Y, W, pen, nlambda=pr.nlambda, opts=ko)  # warm-up
+    times, res = [], None
+    for _ in range(2):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        res = g.glam_fit_path(plan, X, Y, W, pen, nlambda=pr.nlambda, opts=ko)
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    ms = min(times)
+    iters = sum(s["inner_iters"] for s in res.stats)
+    ms32 = sum(s["time_ms"] for s in last.stats)
+    F32 = [s["objective"] for s in last.stats]
+    Fk = [s["objective"] for s in res.stats]
+    out = {"ms_per_path": ms, "inner_iters": iters, "inner_iters_per_s": iters / (ms / 1e3),
+           "exact_fp32_ms_per_path": ms32, "speedup_vs_exact_path": ms32 / ms,
+           "converged": res.status == g.GLAM_OK, "max_kkt": max(s["kkt"] for s in res.stats),
+           "max_rel_objective_diff_vs_exact": max(abs(a - b) / abs(b) for a, b in zip(Fk, F32)),
+           "outer_iters": sum(s["outer_iters"] for s in res.stats),
+           "fp64_passes": sum(s["fp64_passes"] for s in res.stats),
+           "form": "inner product H(<X_j^T X_j>, d) on p-sized arrays; FP64 gradient and KKT per outer iteration"}
     plan.close()
     return out
 
