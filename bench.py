@@ -409,10 +409,8 @@ def measure_kron(g, torch, pr, X, Y, W, pen, opts, flush, last):
     X^T W X = (x)_j X_j^T X_j exactly and every inner iteration works on p-sized arrays.  The
     same 50-lambda path with an FP32 plan, timed like a bench step, against the exact-weight FP32
     path at the same KKT tolerance."""
-    import ctypes
     plan = g.Plan(pr.n, pr.p, pr.family, g.GLAM_FP32)
-    ko = g.GlamOpts()
-    ctypes.pointer(ko)[0] = opts
+    ko = g.GlamOpts.from_buffer_copy(opts)
     ko.iwls = g.GLAM_IWLS_KRON
     g.glam_fit_path(plan, X, Y, W, pen, nlambda=pr.nlambda, opts=ko)  # warm-up
     times, res = [], None

@@ -7,8 +7,8 @@
 // stop criterion max |x+ - y|.  Each CTA owns a tile of TJ rows j3 x 32 columns n of Q and sums
 // it over every i3 itself, so no split partials go through memory and no second kernel is
 // launched.  The i3 range streams through shared memory in chunks of up to 256 rows: a 2-D
-// tensor copy of S_b (box 32 x KC) and one of X_3^T (box KC x TJ) per chunk, double-buffered,
-// with bounded mbarrier waits.  Lane = column, warp = an eighth of each chunk's rows; the eight
+// tensor copy of S_b (box 32 x KC) and one of X_3^T (box KC x TJ) per chunk, three buffers (up to
+// three chunks in flight from the start), with bounded mbarrier waits.  Lane = column, warp = an eighth of each chunk's rows; the eight
 // warp partials are added in warp order in FP64 (the same bits on every run).  The operands of
 // the prox step and the loop state are loaded at kernel start, behind the chunk copies.  The
 // criterion ends in the last-block-done protocol of the prox kernel (glam_elementwise.cu) on the
@@ -30,7 +30,8 @@ constexpr int kAPThreads = 256;
 constexpr int kAPWarps = kAPThreads / 32;
 constexpr int kAPMaxRows = 8;   // rows j3 of a tile, at most
 constexpr int kAPMaxChunk = 256;  // rows i3 of a chunk, at most (tensor-copy box limit)
-constexpr int kAPMaxSmem = 2 * (kAPMaxChunk * 32 + kAPMaxChunk * kAPMaxRows) * 4;
+constexpr int kAPBufs = 3;        // chunk buffers: up to three chunks in flight at once
+constexpr int kAPMaxSmem = kAPBufs * (kAPMaxChunk * 32 + kAPMaxChunk * kAPMaxRows) * 4;
 
 struct APShape {
   int n3, p3, P21;
@@ -57,12 +58,14 @@ adjprox_kernel(APShape sh, const __grid_constant__ CUtensorMap mapS, const __gri
                const double* __restrict__ gk, const double* __restrict__ x, const double* xp,
                const double* __restrict__ pen, double* out, float* __restrict__ dnext,
                const double* __restrict__ anchor, double inv_n, InnerCtl* ctl, int* err) {
-  if (ctl->done) return;  // written by the preceding kernels: the same value in every thread
+  // written by the preceding kernels: the same value in every thread; tested once the first
+  // copies are under way, so its load overlaps their issue
+  const int done = ctl->done;
   // the loop state of this iteration; the last CTA changes it only after every CTA has arrived
   const int l = ctl->l;
   const double delta = ctl->delta, lam = ctl->lambda;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ uint64_t mbar[2];
+  __shared__ uint64_t mbar[kAPBufs];
   __shared__ int timed_out;
   __shared__ bool is_last;
   float* const base = reinterpret_cast<float*>(smem_raw);
@@ -74,8 +77,7 @@ adjprox_kernel(APShape sh, const __grid_constant__ CUtensorMap mapS, const __gri
   const uint32_t bytes = (uint32_t)stage * 4u;
   if (tid == 0) {
     timed_out = 0;
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
+    for (int b = 0; b < kAPBufs; ++b) mbar_init(&mbar[b], 1);
     fence_mbar_init();
   }
   __syncthreads();
@@ -94,9 +96,13 @@ adjprox_kernel(APShape sh, const __grid_constant__ CUtensorMap mapS, const __gri
         "l"(reinterpret_cast<uint64_t>(&mapX)), "r"(c * KC), "r"(j0), "r"(smem_u32(&mbar[b]))
         : "memory");
   };
-  if (tid == 0) {
-    issue(0, 0);
-    if (nchunk > 1) issue(1, 1);
+  const int nfirst = nchunk < kAPBufs ? nchunk : kAPBufs;
+  if (tid == 0)
+    for (int c = 0; c < nfirst; ++c) issue(c, c);
+  if (done) {  // the loop has stopped: nothing to compute; the copies land before the CTA leaves
+    if (tid == 0)
+      for (int c = 0; c < nfirst; ++c) mbar_wait_bounded(&mbar[c], 0u);
+    return;
   }
   // the prox operands of this thread's coordinate (at most one: TJ x 32 <= 256), loaded now
   const int jo = tid / 32, co = tid - jo * 32;
@@ -117,8 +123,8 @@ adjprox_kernel(APShape sh, const __grid_constant__ CUtensorMap mapS, const __gri
   for (int j = 0; j < TJ; ++j) acc[j] = 0.f;
   const int RW = KC / kAPWarps;  // rows of a chunk per warp (a multiple of 4)
   for (int c = 0; c < nchunk; ++c) {
-    const int b = c & 1;
-    if (!mbar_wait_bounded(&mbar[b], (uint32_t)((c >> 1) & 1))) atomicOr(&timed_out, 1);
+    const int b = c % kAPBufs;
+    if (!mbar_wait_bounded(&mbar[b], (uint32_t)((c / kAPBufs) & 1))) atomicOr(&timed_out, 1);
     __syncthreads();
     if (timed_out) break;  // read after the barrier that follows every write to it
     const float* Sc = base + (int64_t)b * stage;
@@ -140,7 +146,7 @@ adjprox_kernel(APShape sh, const __grid_constant__ CUtensorMap mapS, const __gri
       }
     }
     __syncthreads();  // every warp is done with buffer b
-    if (tid == 0 && c + 2 < nchunk) issue(c + 2, b);
+    if (tid == 0 && c + kAPBufs < nchunk) issue(c + kAPBufs, b);
   }
   // ---- the warp partials, added in warp order (FP64), then the prox step per coordinate ----
   float* red = base;  // [warp][TJ][32], over buffer 0 (free after the loop's last barrier)
@@ -185,10 +191,8 @@ adjprox_kernel(APShape sh, const __grid_constant__ CUtensorMap mapS, const __gri
     ctl->crit_bits = 0ull;
     ctl->counter = 0u;
   }
-  if (timed_out && tid == 0) {  // copies still in flight land before the CTA leaves
-    mbar_wait_bounded(&mbar[0], 0u);
-    mbar_wait_bounded(&mbar[1], 0u);
-  }
+  if (timed_out && tid == 0)  // copies still in flight land before the CTA leaves
+    for (int b = 0; b < nfirst; ++b) mbar_wait_bounded(&mbar[b], 0u);
 }
 
 bool ap_configure(int n3, int p3, int P21, APShape& sh, size_t& smem) {
@@ -202,10 +206,12 @@ bool ap_configure(int n3, int p3, int P21, APShape& sh, size_t& smem) {
   if (gy < 1) gy = 1;
   sh.TJ = (p3 + gy - 1) / gy;
   if (sh.TJ > kAPMaxRows) sh.TJ = kAPMaxRows;
-  const int kc = ((n3 + 31) / 32) * 32;  // 32 rows per warp step keeps every warp's share whole
+  // chunks of a multiple of 32 rows (every warp's share stays whole), as few as the buffers allow
+  const int per = (n3 + kAPBufs - 1) / kAPBufs;
+  const int kc = ((per + 31) / 32) * 32;
   sh.KC = kc < kAPMaxChunk ? kc : kAPMaxChunk;
   sh.nchunk = (n3 + sh.KC - 1) / sh.KC;
-  smem = (size_t)2 * (sh.KC * 32 + sh.KC * sh.TJ) * 4;
+  smem = (size_t)kAPBufs * (sh.KC * 32 + sh.KC * sh.TJ) * 4;
   return true;
 }
 
@@ -213,7 +219,14 @@ std::atomic<int> g_ap_ready{0};
 
 template <int TJ>
 cudaError_t ap_prepare_one() {
-  return cudaFuncSetAttribute(adjprox_kernel<TJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAPMaxSmem);
+  cudaError_t e =
+      cudaFuncSetAttribute(adjprox_kernel<TJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAPMaxSmem);
+  // the largest shared-memory carveout, so that two CTAs fit on an SM and the grid (about one
+  // tile per SM, a few more than the SMs) runs as one wave
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(adjprox_kernel<TJ>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  return e;
 }
 
 }  // namespace
@@ -233,7 +246,7 @@ cudaError_t launch_adjprox(int n3, int p3, int P21, const float* X3T, const floa
   size_t smem;
   if (!adjprox_supported(n3, p3, P21, X3T, Sb) || !ap_configure(n3, p3, P21, sh, smem))
     return cudaErrorInvalidValue;
-  if (!g_ap_ready) {  // the largest tile any shape can ask for: two chunks of 256 rows, 8 rows j3
+  if (!g_ap_ready) {  // the largest tile any shape can ask for: three chunks of 256 rows, 8 rows j3
     cudaError_t e = ap_prepare_one<1>();
     if (e == cudaSuccess) e = ap_prepare_one<2>();
     if (e == cudaSuccess) e = ap_prepare_one<3>();

@@ -23,12 +23,27 @@ namespace {
 constexpr int kTile = 128;  // tile side: rows i2 and columns i1
 constexpr int kPMax = 32;   // p1, p2 at most this (shared-memory operand tiles)
 
-// Operand blocks, T_b, T_a, then (bulk-store form) the staged eta tile, 16-byte aligned.
-__host__ __device__ inline size_t predict_operand_floats(int p1, int p2) {
-  return ((size_t)(p1 + 2 * p2) * kTile + (size_t)p1 * p2 + 3) / 4 * 4;
-}
-size_t predict_smem_bytes(int p1, int p2, bool bulk) {
-  return sizeof(float) * (predict_operand_floats(p1, p2) + (bulk ? (size_t)kTile * kTile : 0));
+// Shared-memory layout of predict_tile_kernel<MODE>: X_1^T, X_2^T and T_b blocks of LD = kTile
+// columns, T_a, then (MODE 1) the staged eta tile (kTile x kTile, dense, so that a tile whose rows
+// are contiguous in eta leaves in one bulk copy), every part 16-byte aligned.
+struct PredLayout {
+  int64_t x1s, x2s, tbs, tas, es, total;  // floats
+};
+__host__ __device__ inline PredLayout pred_layout(int p1, int p2, int mode) {
+  PredLayout L;
+  int64_t off = 0;
+  L.x1s = off;
+  off += (int64_t)p1 * kTile;
+  L.x2s = off;
+  off += (int64_t)p2 * kTile;
+  L.tbs = off;
+  off += (int64_t)p2 * kTile;
+  L.tas = off;  // two buffers: the current work item's T_a and the next one's, in flight
+  off += 2 * (((int64_t)p1 * p2 + 3) / 4 * 4);
+  L.es = off;
+  if (mode >= 1) off += (int64_t)kTile * kTile;
+  L.total = off;
+  return L;
 }
 
 // Mode-3 product T_a (n3 x P21) = X_3 (n3 x p3) . Theta (p3 x P21), the first stage of H.  A CTA
@@ -41,6 +56,9 @@ mode3_rows_kernel(int n3, int p3, int P21, const float* __restrict__ XT3,
                   const float* __restrict__ Theta, float* __restrict__ Ta) {
   __shared__ float Th[kM3KMax][kM3Cols];
   __shared__ float X3s[kM3KMax][kM3Rows];
+  // the tile kernel that consumes T_a may be launched now (it waits for this grid's results
+  // before reading them)
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int tid = threadIdx.x;
   const int r0 = blockIdx.y * kM3Rows, m0 = blockIdx.x * kM3Cols;
   constexpr int kThLoads = kM3KMax * kM3Cols / 256, kXLoads = kM3KMax * kM3Rows / 256;
@@ -86,67 +104,83 @@ mode3_rows_kernel(int n3, int p3, int P21, const float* __restrict__ XT3,
   }
 }
 
-// BULK: eta tiles are staged in shared memory and written by bulk copies (n1 % 4 == 0, eta
-// 16-byte aligned), so the stores of one tile proceed while the next one is computed; otherwise
-// every thread stores its outputs directly.
-template <bool BULK>
+// MODE 0: every thread stores its outputs directly.  MODE 1: eta tiles staged in shared memory
+// and written by bulk copies (n1 % 4 == 0, eta 16-byte aligned), so the stores of one tile
+// proceed while the next one is computed.
+template <int MODE>
 __global__ void __launch_bounds__(256, 2)
 predict_tile_kernel(int n1, int n2, int n3, int p1, int p2, const float* __restrict__ XT1,
                     const float* __restrict__ XT2, const float* __restrict__ Ta,
                     float* __restrict__ eta) {
+  constexpr bool BULK = MODE >= 1;
   extern __shared__ float4 smem_f4[];
-  float* X1s = reinterpret_cast<float*>(smem_f4);  // [p1][kTile]  X_1^T columns of the block
-  float* X2s = X1s + p1 * kTile;                   // [p2][kTile]  X_2^T columns of the block
-  float* Tbs = X2s + p2 * kTile;                   // [p2][kTile]  T_b of the tile
-  float* Tas = Tbs + p2 * kTile;                   // [p2][p1]     T_a of the slab
-  float* Es = X1s + predict_operand_floats(p1, p2);  // [kTile][kTile] eta tile (BULK)
+  const PredLayout L = pred_layout(p1, p2, MODE);
+  constexpr int LD = kTile;
+  float* sm = reinterpret_cast<float*>(smem_f4);
+  float* X1s = sm + L.x1s;  // [p1][LD]   X_1^T columns of the block
+  float* X2s = sm + L.x2s;  // [p2][LD]   X_2^T columns of the block
+  float* Tbs = sm + L.tbs;  // [p2][LD]   T_b of the tile
+  float* Tas0 = sm + L.tas;  // [2][p2][p1] T_a of the slab (double-buffered)
+  float* Es = sm + L.es;    // [kTile][kTile] eta tile (BULK)
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int nb1 = (n1 + kTile - 1) / kTile, nb2 = (n2 + kTile - 1) / kTile;
   const int64_t ntiles = (int64_t)n3 * nb1 * nb2;
   const int P21 = p1 * p2;
-  // T_a of the next work item is fetched into registers while the current one is computed
-  constexpr int kTaRegs = kPMax * kPMax / 256;
-  float tan[kTaRegs];
-  auto fetch_ta = [&](int64_t t) {
-    const int i3 = (int)(t % n3);
+  const int TaStride = (P21 + 3) / 4 * 4;
+  // T_a of work item t into buffer b by asynchronous 4-byte copies (completed by cp.async.wait_all)
+  auto fetch_ta = [&](int64_t t, int b) {
+    if (t >= ntiles) return;
+    const float* src = Ta + (t % n3) * (int64_t)P21;
+    float* dst = Tas0 + b * TaStride;
+    for (int idx = tid; idx < P21; idx += 256)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(tma::smem_u32(dst + idx)),
+                   "l"(src + idx)
+                   : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  // every load of the two operand blocks of block blk is issued before the first store, so a
+  // block costs one memory round trip
+  auto load_blocks = [&](int blk) {
+    const int r0 = (blk / nb1) * kTile, c0 = (blk - (blk / nb1) * nb1) * kTile;
+    constexpr int kBlkRegs = kPMax * kTile / 256;
+    float v1[kBlkRegs], v2[kBlkRegs];
 #pragma unroll
-    for (int q = 0; q < kTaRegs; ++q) {
-      const int idx = tid + q * 256;
-      tan[q] = (t < ntiles && idx < P21) ? Ta[(int64_t)i3 * P21 + idx] : 0.f;
+    for (int q = 0; q < kBlkRegs; ++q) {
+      const int idx = tid + q * 256, k = idx / kTile, c = idx - k * kTile;
+      v1[q] = (k < p1 && c0 + c < n1) ? XT1[(int64_t)k * n1 + c0 + c] : 0.f;
+      v2[q] = (k < p2 && r0 + c < n2) ? XT2[(int64_t)k * n2 + r0 + c] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < kBlkRegs; ++q) {
+      const int idx = tid + q * 256, k = idx / kTile, c = idx - k * kTile;
+      if (k < p1) X1s[k * LD + c] = v1[q];
+      if (k < p2) X2s[k * LD + c] = v2[q];
     }
   };
-  fetch_ta(blockIdx.x);
   int cur_blk = -1;
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  if ((int64_t)blockIdx.x < ntiles) {
+    cur_blk = (int)((int64_t)blockIdx.x / n3);
+    load_blocks(cur_blk);
+  }
+  // T_a is written by the mode-3 kernel launched just before: with a programmatic launch this
+  // kernel starts early, loads its operand blocks, and waits here for that grid's results
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  fetch_ta(blockIdx.x, 0);
+  int buf = 0;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1) {
     const int blk = (int)(t / n3);
     const int i3 = (int)(t - (int64_t)blk * n3);
     const int b2 = blk / nb1, b1 = blk - b2 * nb1;
     const int r0 = b2 * kTile, c0 = b1 * kTile;
     __syncthreads();  // every reader of the previous work item's shared arrays is done
     if (blk != cur_blk) {
-      // every load of the two operand blocks is issued before the first store, so the block
-      // costs one memory round trip
-      constexpr int kBlkRegs = kPMax * kTile / 256;
-      float v1[kBlkRegs], v2[kBlkRegs];
-#pragma unroll
-      for (int q = 0; q < kBlkRegs; ++q) {
-        const int idx = tid + q * 256, k = idx / kTile, c = idx - k * kTile;
-        v1[q] = (k < p1 && c0 + c < n1) ? XT1[(int64_t)k * n1 + c0 + c] : 0.f;
-        v2[q] = (k < p2 && r0 + c < n2) ? XT2[(int64_t)k * n2 + r0 + c] : 0.f;
-      }
-#pragma unroll
-      for (int q = 0; q < kBlkRegs; ++q) {
-        const int idx = tid + q * 256, k = idx / kTile;
-        if (k < p1) X1s[idx] = v1[q];
-        if (k < p2) X2s[idx] = v2[q];
-      }
+      load_blocks(blk);
       cur_blk = blk;
     }
-#pragma unroll
-    for (int q = 0; q < kTaRegs; ++q)
-      if (tid + q * 256 < P21) Tas[tid + q * 256] = tan[q];
-    __syncthreads();
-    fetch_ta(t + gridDim.x);
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();  // T_a of this work item is in buffer buf; the other buffer is free
+    fetch_ta(t + gridDim.x, buf ^ 1);
+    const float* Tas = Tas0 + buf * TaStride;
 
     // mode 1: T_b[k2][c] = sum_k1 T_a[k2][k1] X_1[c][k1]; a thread owns rows k2 = 2kp, 2kp + 1
     // and the columns 4cx.. and 64 + 4cx.. (float4 operand loads, conflict-free)
@@ -161,8 +195,8 @@ predict_tile_kernel(int n1, int n2, int n3, int p1, int p2, const float* __restr
         for (int j = 0; j < 8; ++j) s0[j] = s1[j] = 0.f;
 #pragma unroll 4
         for (int k1 = 0; k1 < p1; ++k1) {
-          const float4 u0 = *reinterpret_cast<const float4*>(X1s + k1 * kTile + 4 * cx);
-          const float4 u1 = *reinterpret_cast<const float4*>(X1s + k1 * kTile + 64 + 4 * cx);
+          const float4 u0 = *reinterpret_cast<const float4*>(X1s + k1 * LD + 4 * cx);
+          const float4 u1 = *reinterpret_cast<const float4*>(X1s + k1 * LD + 64 + 4 * cx);
           const float x[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
           const float w0 = ta0[k1], w1 = ta1[k1];
 #pragma unroll
@@ -171,11 +205,11 @@ predict_tile_kernel(int n1, int n2, int n3, int p1, int p2, const float* __restr
             s1[j] = fmaf(w1, x[j], s1[j]);
           }
         }
-        float* tb0 = Tbs + 2 * kp * kTile;
+        float* tb0 = Tbs + 2 * kp * LD;
         *reinterpret_cast<float4*>(tb0 + 4 * cx) = make_float4(s0[0], s0[1], s0[2], s0[3]);
         *reinterpret_cast<float4*>(tb0 + 64 + 4 * cx) = make_float4(s0[4], s0[5], s0[6], s0[7]);
         if (two) {
-          float* tb1 = tb0 + kTile;
+          float* tb1 = tb0 + LD;
           *reinterpret_cast<float4*>(tb1 + 4 * cx) = make_float4(s1[0], s1[1], s1[2], s1[3]);
           *reinterpret_cast<float4*>(tb1 + 64 + 4 * cx) = make_float4(s1[4], s1[5], s1[6], s1[7]);
         }
@@ -183,6 +217,7 @@ predict_tile_kernel(int n1, int n2, int n3, int p1, int p2, const float* __restr
     }
     __syncthreads();
 
+    float* out = eta + (int64_t)i3 * n2 * n1;
     // mode 2: eta[r][c] = sum_k2 X_2[r][k2] T_b[k2][c] for the thread's 8 x 8 outputs
     float acc[8][8];
 #pragma unroll
@@ -191,10 +226,10 @@ predict_tile_kernel(int n1, int n2, int n3, int p1, int p2, const float* __restr
       for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
 #pragma unroll 4
     for (int k = 0; k < p2; ++k) {
-      const float4 a0 = *reinterpret_cast<const float4*>(X2s + k * kTile + ty * 8);
-      const float4 a1 = *reinterpret_cast<const float4*>(X2s + k * kTile + ty * 8 + 4);
-      const float4 v0 = *reinterpret_cast<const float4*>(Tbs + k * kTile + tx * 4);
-      const float4 v1 = *reinterpret_cast<const float4*>(Tbs + k * kTile + 64 + tx * 4);
+      const float4 a0 = *reinterpret_cast<const float4*>(X2s + k * LD + ty * 8);
+      const float4 a1 = *reinterpret_cast<const float4*>(X2s + k * LD + ty * 8 + 4);
+      const float4 v0 = *reinterpret_cast<const float4*>(Tbs + k * LD + tx * 4);
+      const float4 v1 = *reinterpret_cast<const float4*>(Tbs + k * LD + 64 + tx * 4);
       const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
       const float b[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
@@ -202,8 +237,6 @@ predict_tile_kernel(int n1, int n2, int n3, int p1, int p2, const float* __restr
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
     }
-
-    float* out = eta + (int64_t)i3 * n2 * n1;
     if (BULK) {
       if (tid < 32) tma::bulk_wait_read_all();  // the previous tile's copies have read Es
       __syncthreads();
@@ -213,19 +246,6 @@ predict_tile_kernel(int n1, int n2, int n3, int p1, int p2, const float* __restr
         *reinterpret_cast<float4*>(er) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
         *reinterpret_cast<float4*>(er + 64) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
       }
-      tma::fence_proxy_async();
-      __syncthreads();
-      if (tid < 32) {
-        const int rows = min(kTile, n2 - r0), cols = min(kTile, n1 - c0);
-        if (cols == kTile && n1 == kTile) {
-          // the tile's rows are contiguous in eta: one copy
-          if (tid == 0) tma::bulk_s2g(out + (int64_t)r0 * n1, Es, (uint32_t)(rows * kTile * 4));
-        } else {
-          for (int r = tid; r < rows; r += 32)
-            tma::bulk_s2g(out + (int64_t)(r0 + r) * n1 + c0, Es + r * kTile, (uint32_t)(cols * 4));
-        }
-        tma::bulk_commit();
-      }
     } else {
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
@@ -234,11 +254,26 @@ predict_tile_kernel(int n1, int n2, int n3, int p1, int p2, const float* __restr
         float* row = out + (int64_t)r * n1;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const int c = c0 + h * 64 + tx * 4;
+          const int cc = c0 + h * 64 + tx * 4;
 #pragma unroll
           for (int j = 0; j < 4; ++j)
-            if (c + j < n1) row[c + j] = acc[i][4 * h + j];
+            if (cc + j < n1) row[cc + j] = acc[i][4 * h + j];
         }
+      }
+    }
+    if (BULK) {
+      tma::fence_proxy_async();
+      __syncthreads();
+      if (tid < 32) {
+        const int rows = min(kTile, n2 - r0), cols = min(kTile, n1 - c0);
+        if (cols == kTile && n1 == kTile) {
+          // the tile's rows are contiguous in eta and in Es: one copy
+          if (tid == 0) tma::bulk_s2g(out + (int64_t)r0 * n1, Es, (uint32_t)(rows * kTile * 4));
+        } else {
+          for (int r = tid; r < rows; r += 32)
+            tma::bulk_s2g(out + (int64_t)(r0 + r) * n1 + c0, Es + r * kTile, (uint32_t)(cols * 4));
+        }
+        tma::bulk_commit();
       }
     }
   }
@@ -270,8 +305,9 @@ cudaError_t launch_predict_tiles(int n1, int n2, int n3, int p1, int p2, const f
   const int64_t ntiles = (int64_t)n3 * ((n1 + kTile - 1) / kTile) * ((n2 + kTile - 1) / kTile);
   if (ntiles <= 0) return cudaSuccess;
   const bool bulk = (n1 % 4 == 0) && ((reinterpret_cast<uintptr_t>(eta) & 15) == 0);
-  const size_t smem = predict_smem_bytes(p1, p2, bulk);
-  auto kern = bulk ? predict_tile_kernel<true> : predict_tile_kernel<false>;
+  const int mode = bulk ? 1 : 0;
+  const size_t smem = sizeof(float) * (size_t)pred_layout(p1, p2, mode).total;
+  auto kern = mode == 1 ? predict_tile_kernel<1> : predict_tile_kernel<0>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -279,7 +315,20 @@ cudaError_t launch_predict_tiles(int n1, int n2, int n3, int p1, int p2, const f
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   const int grid = (int)std::min<int64_t>(ntiles, (int64_t)per_sm * num_sms());
-  kern<<<grid, 256, smem, s>>>(n1, n2, n3, p1, p2, XT1, XT2, Ta, eta);
+  // programmatic dependent launch: the kernel may start while the mode-3 kernel before it on the
+  // stream finishes; it waits (griddepcontrol.wait) before it reads T_a
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, kern, n1, n2, n3, p1, p2, XT1, XT2, Ta, eta);
+  if (e != cudaSuccess) return e;
   count_launches(1);
   return cudaGetLastError();
 }

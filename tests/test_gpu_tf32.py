@@ -165,3 +165,4 @@ def test_tf32_workload_path_agrees_with_fp32():
         assert abs(Ftf - F32) <= 1e-6 * abs(F32), (k, Ftf, F32)
     th = O.paper_array(host(res[g.GLAM_TF32].path[5]))
     assert O.kkt_residual(d, th, lams[5], lmax) <= 3e-6
+
