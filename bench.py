@@ -526,6 +526,30 @@ def run_kernels(reps, precision="fp32"):
     return 0
 
 
+def run_predict(reps):
+    """Diagnostic mode for profilers: glam_predict (the H-transform) on the 128x128x600 workload
+    with an FP32 plan, reps times; prints the mean time per call.  It produces no bench line."""
+    import torch
+    import gen
+    import paper_1510_03298_gb300 as g
+    from paper_1510_03298_gb300 import build as gb
+    if not os.path.exists(g.library_path()):
+        gb.build()
+    pr = gen.make_workload(1)
+    f32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+    plan = g.Plan(pr.n, pr.p, pr.family, g.GLAM_FP32)
+    X = [f32(x) for x in pr.XT]
+    theta = f32(np.random.default_rng(0).standard_normal((pr.p[2], pr.p[1], pr.p[0])))
+    eta = torch.empty((pr.n[2], pr.n[1], pr.n[0]), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        g.glam_predict(plan, X, theta, eta)
+    torch.cuda.synchronize()
+    print(json.dumps({"predict_ms_per_call": (time.perf_counter() - t0) * 1e3 / reps}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -541,7 +565,11 @@ def main():
                     help="diagnostic: launch the inner-iteration kernels REPS times for a profiler")
     ap.add_argument("--kernels-precision", choices=["fp32", "tf32"], default="fp32",
                     help="plan precision of the --kernels diagnostic")
+    ap.add_argument("--predict", type=int, default=0, metavar="REPS",
+                    help="diagnostic: run glam_predict REPS times for a profiler")
     args = ap.parse_args()
+    if args.predict > 0:
+        return run_predict(args.predict)
     if args.kernels > 0:
         return run_kernels(args.kernels, args.kernels_precision)
     if args.warmup < 3:
