@@ -27,6 +27,8 @@ SEED_BASE = 1510_03298
 
 GAUSSIAN = 0  # Gaussian family, identity link
 POISSON = 1   # Poisson family, log link
+BINOMIAL = 2  # binomial proportions with a_i trials, logit link
+GAMMA = 3     # Gamma family (shape 2), log link
 
 
 def cubic_bspline_basis(n_j: int, p_j: int) -> np.ndarray:
@@ -216,14 +218,27 @@ def random_problem(seed: int, n, p, family=GAUSSIAN, mask_frac=0.0, basis="splin
         XT = [cubic_bspline_basis(n[j], p[j]).T.copy() for j in range(3)]
     else:
         XT = [rng.standard_normal((n[j], p[j])).T.copy() / np.sqrt(max(n[j], 1)) for j in range(3)]
+    W = None
     if family == GAUSSIAN:
         theta = rng.standard_normal((p[2], p[1], p[0])) * (rng.random((p[2], p[1], p[0])) < 0.3)
         eta = _spline_surface(XT, theta)
         Y = eta + 0.5 * rng.standard_normal(eta.shape)
     else:
         eta = 1.5 * np.tanh(_spline_surface(XT, rng.standard_normal((p[2], p[1], p[0])) * 0.7))
-        Y = rng.poisson(np.exp(eta)).astype(np.float64)
-    W = np.ones_like(Y)
+        if family == POISSON:
+            Y = rng.poisson(np.exp(eta)).astype(np.float64)
+        elif family == BINOMIAL:
+            # proportions of m_i in {1..8} trials with success probability 1 / (1 + exp(-eta))
+            m = rng.integers(1, 9, eta.shape)
+            Y = rng.binomial(m, 1.0 / (1.0 + np.exp(-eta))) / m
+            W = m.astype(np.float64)
+        elif family == GAMMA:
+            # Gamma draws of shape 2 and mean exp(eta)
+            Y = rng.gamma(2.0, np.exp(eta) / 2.0)
+        else:
+            raise ValueError(family)
+    if W is None:
+        W = np.ones_like(Y)
     N = Y.size
     m = int(round(mask_frac * N))
     if m > 0:

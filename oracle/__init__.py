@@ -4,4 +4,4 @@ Only the test suite, `__graft_entry__.smoke()` and the CPU-baseline leg of `benc
 import this package; the product path never does.
 """
 from .glam_oracle import *  # noqa: F401,F403
-from .glam_oracle import GAUSSIAN, POISSON  # noqa: F401
+from .glam_oracle import BINOMIAL, GAMMA, GAUSSIAN, POISSON  # noqa: F401

@@ -42,8 +42,10 @@ from typing import List, Optional, Sequence
 
 import numpy as np
 
-GAUSSIAN = 0
-POISSON = 1
+GAUSSIAN = 0   # Gaussian, identity link (canonical)
+POISSON = 1    # Poisson, log link (canonical)
+BINOMIAL = 2   # binomial proportions y in [0, 1] with a_i trials, logit link (canonical)
+GAMMA = 3      # Gamma (dispersion 1), log link (not canonical)
 
 
 # --------------------------------------------------------------------------------------
@@ -124,17 +126,33 @@ def design_col(Xs, midx) -> np.ndarray:
 # App. B: exponential-family quantities (canonical links only: theta(eta) = eta)
 # --------------------------------------------------------------------------------------
 
+def _theta(family, eta):
+    """The canonical parameter theta(eta) of App. B: eta itself for a canonical link; for the
+    Gamma family with log link theta = -1/mu = -exp(-eta)."""
+    if family in (GAUSSIAN, POISSON, BINOMIAL):
+        return np.asarray(eta, dtype=np.float64).copy()
+    if family == GAMMA:
+        return -np.exp(-eta)
+    raise ValueError(family)
+
+
 def _canonical_derivative(family, eta):
-    """theta'(eta): 1 for the canonical Gaussian-identity and Poisson-log links."""
-    return np.ones_like(eta)
+    """theta'(eta): 1 for the canonical links; exp(-eta) for the Gamma family with log link."""
+    if family in (GAUSSIAN, POISSON, BINOMIAL):
+        return np.ones_like(eta)
+    if family == GAMMA:
+        return np.exp(-eta)
+    raise ValueError(family)
 
 
 def _mean(family, eta):
     """g^{-1}(eta)."""
     if family == GAUSSIAN:
         return eta.copy()
-    if family == POISSON:
+    if family in (POISSON, GAMMA):
         return np.exp(eta)
+    if family == BINOMIAL:
+        return 1.0 / (1.0 + np.exp(-eta))
     raise ValueError(family)
 
 
@@ -142,8 +160,11 @@ def _mean_derivative(family, eta):
     """(g^{-1})'(eta)."""
     if family == GAUSSIAN:
         return np.ones_like(eta)
-    if family == POISSON:
+    if family in (POISSON, GAMMA):
         return np.exp(eta)
+    if family == BINOMIAL:
+        mu = _mean(family, eta)
+        return mu * (1.0 - mu)
     raise ValueError(family)
 
 
@@ -151,18 +172,30 @@ def _link_derivative(family, mu):
     """g'(mu)."""
     if family == GAUSSIAN:
         return np.ones_like(mu)
-    if family == POISSON:
+    if family in (POISSON, GAMMA):
         return 1.0 / mu
+    if family == BINOMIAL:
+        return 1.0 / (mu * (1.0 - mu))
     raise ValueError(family)
 
 
 def _b(family, th):
-    """Log-normaliser b(theta) of the density in App. B."""
+    """Log-normaliser b(theta) of the density in App. B (for the Gamma family with dispersion 1,
+    b(theta) = -log(-theta))."""
     if family == GAUSSIAN:
         return 0.5 * th * th
     if family == POISSON:
         return np.exp(th)
+    if family == BINOMIAL:
+        return np.logaddexp(0.0, th)
+    if family == GAMMA:
+        return -np.log(-th)
     raise ValueError(family)
+
+
+def mean_response(family, eta):
+    """mu = g^{-1}(eta), the mean of y at the linear predictor eta."""
+    return _mean(family, eta)
 
 
 def score(family, eta, y, a):
@@ -184,13 +217,15 @@ def working_response(family, eta, y, a):
 
 
 def loglik(family, eta, y, a):
-    """l(eta) = sum_i a_i (y_i theta(eta_i) - b(theta(eta_i))), Eq. (two) (canonical link)."""
-    th = eta
+    """l(eta) = sum_i a_i (y_i theta(eta_i) - b(theta(eta_i))), Eq. (two)."""
+    th = _theta(family, eta)
     return float(np.sum(a * (y * th - _b(family, th))))
 
 
 def loss(family, eta, y, a) -> float:
-    """f(eta) = -(1/n) l(eta) + c, with c = sum a y^2/(2n) for the Gaussian family (reading R3)."""
+    """f(eta) = -(1/n) l(eta) + c, with c = sum a y^2/(2n) for the Gaussian family (reading R3);
+    the constants of the other densities (log y!, the binomial coefficients, the Gamma terms in y
+    alone) are dropped."""
     n = np.asarray(eta).size
     f = -loglik(family, eta, y, a) / n
     if family == GAUSSIAN:
@@ -200,9 +235,9 @@ def loss(family, eta, y, a) -> float:
 
 def loss_grad_y(family, eta, y, a) -> np.ndarray:
     """df/dy_i of `loss` at fixed eta: Eq. (two) is linear in y with coefficient a_i theta(eta_i),
-    so -(1/n) a_i eta_i (canonical link), plus (1/n) a_i y_i from the Gaussian constant of R3."""
+    so -(1/n) a_i theta(eta_i), plus (1/n) a_i y_i from the Gaussian constant of R3."""
     n = np.asarray(eta).size
-    g = -a * eta / n
+    g = -a * _theta(family, eta) / n
     if family == GAUSSIAN:
         g = g + a * y / n
     return g

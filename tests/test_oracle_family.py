@@ -22,8 +22,12 @@ def _data(rng, fam, n=(5, 4, 3), p=(3, 2, 3), mask=False):
     eta = rng.uniform(-1.5, 1.5, n)
     if fam == O.GAUSSIAN:
         y = eta + rng.standard_normal(n)
-    else:
+    elif fam == O.POISSON:
         y = rng.poisson(np.exp(eta)).astype(float)
+    elif fam == O.BINOMIAL:
+        y = rng.binomial(6, 1.0 / (1.0 + np.exp(-eta))) / 6.0
+    else:
+        y = rng.gamma(2.0, np.exp(eta) / 2.0)
     a = rng.uniform(0.5, 2.0, n)
     if mask:
         a[rng.random(n) < 0.3] = 0.0
@@ -48,7 +52,10 @@ def test_gaussian_loss_is_negative_loglik():
     assert np.isclose(O.loss(O.GAUSSIAN, eta, d.Y, d.a), expected, rtol=1e-13)
 
 
-@pytest.mark.parametrize("fam", [O.GAUSSIAN, O.POISSON])
+ALL = [O.GAUSSIAN, O.POISSON, O.BINOMIAL, O.GAMMA]
+
+
+@pytest.mark.parametrize("fam", ALL)
 def test_score_is_derivative_of_loglik(fam):
     rng = np.random.default_rng(12)
     d, eta = _data(rng, fam, mask=True)
@@ -62,23 +69,31 @@ def test_score_is_derivative_of_loglik(fam):
         assert np.isclose(u[idx], fd, rtol=1e-6, atol=1e-8)
 
 
-@pytest.mark.parametrize("fam", [O.GAUSSIAN, O.POISSON])
+@pytest.mark.parametrize("fam", ALL)
 def test_weight_is_fisher_information(fam):
+    """w = E[-du/deta]: -du/deta with y replaced by its mean g^{-1}(eta) (for a canonical link
+    du/deta does not depend on y at all)."""
     rng = np.random.default_rng(13)
     d, eta = _data(rng, fam, mask=True)
     w = O.irls_weight(fam, eta, d.a)
     h = 1e-6
-    du = (O.score(fam, eta + h, d.Y, d.a) - O.score(fam, eta - h, d.Y, d.a)) / (2 * h)
+    mu = O.mean_response(fam, eta)
+    du = (O.score(fam, eta + h, mu, d.a) - O.score(fam, eta - h, mu, d.a)) / (2 * h)
     np.testing.assert_allclose(w, -du, rtol=1e-6, atol=1e-9)
     assert np.all(w[d.a == 0] == 0) and np.all(w[d.a > 0] > 0)
 
 
-@pytest.mark.parametrize("fam", [O.GAUSSIAN, O.POISSON])
+@pytest.mark.parametrize("fam", ALL)
 def test_quadratic_model_matches_f_to_second_order(fam):
+    """grad h = grad f at the anchor; the Hessians agree where the Fisher weight is the observed
+    curvature: always for a canonical link, and for the Gamma family's log link where y equals
+    its mean at the anchor (the data are set so)."""
     rng = np.random.default_rng(14)
     d, _ = _data(rng, fam, mask=True)
     theta_k = rng.standard_normal(d.pshape) * 0.2
     eta_k = O.H(d.Xs, theta_k)
+    if fam == O.GAMMA:
+        d = O.GlamData(fam, d.Xs, O.mean_response(fam, eta_k), d.a, d.pen_w)
     w = O.irls_weight(fam, eta_k, d.a)
     z = O.working_response(fam, eta_k, d.Y, d.a)
 
@@ -128,3 +143,38 @@ def test_prop1_bound():
     # W = c I: the bound is exact (spectral radius of a Kronecker product is the product)
     w = np.full(n, 2.5)
     assert np.isclose(O.lipschitz_exact(Xs, w), O.lipschitz_bound(Xs, w), rtol=1e-10)
+
+
+def test_binomial_loss_is_negative_loglik():
+    rng = np.random.default_rng(15)
+    m = rng.integers(1, 9, (5, 4, 3))
+    eta = rng.uniform(-2, 2, m.shape)
+    k = rng.binomial(m, 1.0 / (1.0 + np.exp(-eta)))
+    y, a = k / m, m.astype(float)
+    logpmf = scipy_stats.binom.logpmf(k, m, 1.0 / (1.0 + np.exp(-eta)))
+    from scipy.special import comb
+    expected = -np.sum(logpmf - np.log(comb(m, k))) / eta.size
+    assert np.isclose(O.loss(O.BINOMIAL, eta, y, a), expected, rtol=1e-12)
+
+
+def test_gamma_loss_is_negative_loglik():
+    """Dispersion 1 (shape 1): the exponential density with mean exp(eta)."""
+    rng = np.random.default_rng(16)
+    eta = rng.uniform(-1, 2, (5, 4, 3))
+    y = rng.exponential(np.exp(eta))
+    a = rng.uniform(0.5, 2.0, eta.shape)
+    logpdf = scipy_stats.expon.logpdf(y, scale=np.exp(eta))
+    assert np.isclose(O.loss(O.GAMMA, eta, y, a), -np.sum(a * logpdf) / eta.size, rtol=1e-12)
+
+
+def test_planted_gamma_canonical_slip_is_caught():
+    """Treating the Gamma log link as canonical (theta'(eta) = 1) breaks the score pin."""
+    rng = np.random.default_rng(17)
+    d, eta = _data(rng, O.GAMMA)
+    wrong = d.a * (d.Y - np.exp(eta))
+    h = 1e-6
+    e1, e2 = eta.copy(), eta.copy()
+    e1[0, 0, 0] += h
+    e2[0, 0, 0] -= h
+    fd = (O.loglik(O.GAMMA, e1, d.Y, d.a) - O.loglik(O.GAMMA, e2, d.Y, d.a)) / (2 * h)
+    assert not np.isclose(wrong[0, 0, 0], fd, rtol=1e-3)
