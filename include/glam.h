@@ -25,11 +25,15 @@
  * Errors.  Every function returns a status (GLAM_OK = 0).  No exception crosses the ABI.
  *   On failure glam_last_error(plan) returns a message (for glam_plan_create failures, and
  *   for calls given a NULL plan, use glam_last_error(NULL): the calling thread's last error).
- * Families.  GLAM_GAUSSIAN_IDENTITY and GLAM_POISSON_LOG (App. B; canonical links).
+ * Families.  GLAM_GAUSSIAN_IDENTITY, GLAM_POISSON_LOG, GLAM_BINOMIAL_LOGIT (canonical links) and
+ *   GLAM_GAMMA_LOG (Gamma with dispersion 1 and log link, not canonical; Sec. 6.4 names the four).
+ *   Binomial: y_i is a proportion in [0, 1] of a_i trials (a_i the observation weight).
  * Objective.  F(theta) = f(theta) + lambda * sum_m w_m |theta_m| with f = -(1/n) l, l the
  *   weighted log-likelihood of Sec. 2, Eq. (two), n = n1 n2 n3 counting every cell (masked
  *   ones included).  Constants: Gaussian f = (1/2n) sum a_i (y_i - eta_i)^2; Poisson
- *   f = (1/n) sum a_i (exp(eta_i) - y_i eta_i) (the sum of a_i log y_i! is dropped).
+ *   f = (1/n) sum a_i (exp(eta_i) - y_i eta_i) (the sum of a_i log y_i! is dropped); binomial
+ *   f = (1/n) sum a_i (log(1 + exp(eta_i)) - y_i eta_i) (binomial coefficients dropped); Gamma
+ *   f = (1/n) sum a_i (y_i exp(-eta_i) + eta_i) (terms in y alone dropped).
  * Observation weights W (the paper's a_i, Sec. 6.4 "Weights") are >= 0; a_i = 0 masks a cell
  *   (Sec. 4.3).  Penalty weights pen_w (omega_m) must be > 0.
  */
@@ -54,6 +58,8 @@ extern "C" {
 /* ---- families (App. B) ---- */
 #define GLAM_GAUSSIAN_IDENTITY 0
 #define GLAM_POISSON_LOG 1
+#define GLAM_BINOMIAL_LOGIT 2
+#define GLAM_GAMMA_LOG 3
 
 /* ---- arithmetic of the mode products ---- */
 #define GLAM_FP64 0
@@ -105,9 +111,10 @@ typedef struct {
                               GLAM_IWLS_KRON uses their tensor-product form (Sec. 6.2, Eq.
                               kronweight): X^T W X theta = H(<X_j^T W_j X_j>, theta), so the inner
                               loop touches p-sized arrays only.  GLAM_IWLS_KRON is exact, and
-                              accepted, for the Gaussian family with an observation-weight array W
-                              that is a tensor product w1 (x) w2 (x) w3 with W(0,0,0) > 0 (W = 1
-                              included); otherwise glam_fit_path returns GLAM_EINVAL */
+                              accepted, for the families whose IRLS weight is the observation weight
+                              itself (Gaussian; Gamma with log link) with an observation-weight
+                              array W that is a tensor product w1 (x) w2 (x) w3 with W(0,0,0) > 0
+                              (W = 1 included); otherwise glam_fit_path returns GLAM_EINVAL */
   int32_t reserved[5];
 } glam_opts;
 
@@ -132,8 +139,8 @@ typedef struct {
 /* Fill *opts with the defaults listed in glam_opts.  Returns GLAM_EINVAL for NULL. */
 int glam_opts_default(glam_opts* opts);
 
-/* Create a plan for one problem shape.  dims: HOST pointer (copied).  family: GLAM_GAUSSIAN_IDENTITY
- * or GLAM_POISSON_LOG.  precision: GLAM_FP64, GLAM_FP32 or GLAM_TF32 (GLAM_BF16 returns
+/* Create a plan for one problem shape.  dims: HOST pointer (copied).  family: one of the four
+ * GLAM_* families above.  precision: GLAM_FP64, GLAM_FP32 or GLAM_TF32 (GLAM_BF16 returns
  * GLAM_EINVAL).  A GLAM_TF32 plan is a GLAM_FP32 plan whose bottleneck product
  * G(V (.) H(y)) (Sec. 6.2, Eq. twentysixnew: the inner-loop product of glam_prox_step and
  * glam_fit_path) runs on the tensor cores with TF32 operands (10-bit mantissa, round to

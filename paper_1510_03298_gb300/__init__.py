@@ -21,7 +21,7 @@ import torch
 
 __all__ = [
     "GLAM_OK", "GLAM_EINVAL", "GLAM_ENOMEM", "GLAM_ECUDA", "GLAM_ENONFINITE", "GLAM_ENOCONV",
-    "GLAM_ETIMEOUT", "GLAM_GAUSSIAN_IDENTITY", "GLAM_POISSON_LOG", "GLAM_FP64", "GLAM_FP32",
+    "GLAM_ETIMEOUT", "GLAM_GAUSSIAN_IDENTITY", "GLAM_POISSON_LOG", "GLAM_BINOMIAL_LOGIT", "GLAM_GAMMA_LOG", "GLAM_FP64", "GLAM_FP32",
     "GLAM_TF32", "GLAM_BF16", "GLAM_IWLS_EXACT", "GLAM_IWLS_KRON", "GlamError", "Plan", "Quad", "FitResult", "library_path", "load_library",
     "glam_opts_default", "glam_plan_create", "glam_plan_destroy", "glam_predict", "glam_gradient",
     "glam_loss", "glam_quad_build", "glam_prox_step", "glam_fit_path", "glam_launch_count",
@@ -53,6 +53,8 @@ GLAM_ENOCONV = _K["GLAM_ENOCONV"]
 GLAM_ETIMEOUT = _K["GLAM_ETIMEOUT"]
 GLAM_GAUSSIAN_IDENTITY = _K["GLAM_GAUSSIAN_IDENTITY"]
 GLAM_POISSON_LOG = _K["GLAM_POISSON_LOG"]
+GLAM_BINOMIAL_LOGIT = _K["GLAM_BINOMIAL_LOGIT"]
+GLAM_GAMMA_LOG = _K["GLAM_GAMMA_LOG"]
 GLAM_FP64 = _K["GLAM_FP64"]
 GLAM_FP32 = _K["GLAM_FP32"]
 GLAM_TF32 = _K["GLAM_TF32"]

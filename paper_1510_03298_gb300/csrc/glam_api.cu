@@ -377,7 +377,8 @@ int glam_plan_create(const glam_dims* dims, int family, int precision, void* str
       return fail(nullptr, GLAM_EINVAL, "dims: every n_j and p_j must be >= 1");
   if (dims->d == 2 && (dims->n[2] != 1 || dims->p[2] != 1))
     return fail(nullptr, GLAM_EINVAL, "dims: d = 2 needs n3 = p3 = 1");
-  if (family != GLAM_GAUSSIAN_IDENTITY && family != GLAM_POISSON_LOG)
+  if (family != GLAM_GAUSSIAN_IDENTITY && family != GLAM_POISSON_LOG && family != GLAM_BINOMIAL_LOGIT &&
+      family != GLAM_GAMMA_LOG)
     return fail(nullptr, GLAM_EINVAL, "unknown family");
   if (precision != GLAM_FP64 && precision != GLAM_FP32 && precision != GLAM_TF32)
     return fail(nullptr, GLAM_EINVAL, "precision: only GLAM_FP64, GLAM_FP32 and GLAM_TF32 are available");
@@ -951,8 +952,11 @@ int solve_lambda(Fit<T>& f, double lambda, LamOut& lo) {
 template <typename T>
 int kron_setup(Fit<T>& f, const T* W, double& rho_kron, double& wmax) {
   glam_plan* pl = f.pl;
-  if (pl->family != GLAM_GAUSSIAN_IDENTITY)
-    return fail(pl, GLAM_EINVAL, "iwls = GLAM_IWLS_KRON needs tensor-product IRLS weights: the Gaussian family");
+  // the IRLS weight is the observation weight itself for the Gaussian family and for the Gamma
+  // family with log link; for the others it varies with eta and is not a tensor product
+  if (pl->family != GLAM_GAUSSIAN_IDENTITY && pl->family != GLAM_GAMMA_LOG)
+    return fail(pl, GLAM_EINVAL,
+                "iwls = GLAM_IWLS_KRON needs tensor-product IRLS weights: the Gaussian or Gamma family");
   Work<T>& w = work_of<T>(pl);
   const int64_t pj[3] = {pl->p1, pl->p2, pl->p3};
   const int64_t nj[3] = {pl->n1, pl->n2, pl->n3};
@@ -1042,8 +1046,9 @@ int fit_impl(glam_plan* pl, const void* const X[3], const T* Y, const T* W, cons
     CKS(rho_product_from<double>(pl, Xd, f.s, f.rho_prod));
   }
   if (o.iwls == GLAM_IWLS_KRON) {
-    // the family pass sets L_hat = max(w)/n * rho_prod; with rho_prod = prod_j varrho(M_j) / max(w)
-    // it is the exact constant prod_j varrho(M_j) / n of tensor-product weights
+    // the family pass sets L_hat = max(w)/n * rho_prod with w = W here; with rho_prod =
+    // prod_j varrho(M_j) / max(W) it is the exact constant prod_j varrho(M_j) / n of
+    // tensor-product weights
     double rho_kron = 1.0, wmax = 1.0;
     CKS(kron_setup<T>(f, W, rho_kron, wmax));
     f.kron = true;

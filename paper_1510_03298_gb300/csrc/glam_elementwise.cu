@@ -1,6 +1,7 @@
 // Entrywise steps and reductions of GD-PG.
 //
-//  * family pass (Sec. 6.1 step 2; App. B Eqs. four, weights, tennew): from eta, Y and the
+//  * family pass (Sec. 6.1 step 2; App. B Eqs. four, weights, tennew; Gaussian, Poisson, binomial
+//    and Gamma families, family_cell): from eta, Y and the
 //    observation weights a it writes V = w, V (.) Z = u + w eta and optionally U, and reduces the
 //    loss f(eta) (FP64 accumulation) and max(w) (for the step size of Prop. 1);
 //  * proximal step (Sec. 3.2, Sec. 6.3): y = x + omega (x - x_prev), g = (Q - b)/n,
@@ -114,6 +115,71 @@ __device__ __forceinline__ double t_expm1<double>(double x) {
   return expm1(x);
 }
 
+template <typename T>
+__device__ __forceinline__ T t_log1p(T x);
+template <>
+__device__ __forceinline__ float t_log1p<float>(float x) {
+  return log1pf(x);
+}
+template <>
+__device__ __forceinline__ double t_log1p<double>(double x) {
+  return log1p(x);
+}
+
+// The per-cell quantities of App. B at eta = e for response y and observation weight a:
+//   u  the score a theta'(e) (y - g^-1(e))                       (Eq. four)
+//   w  the IRLS weight a theta'(e) (g^-1)'(e)                     (Eq. weights, times a)
+//   l  the cell's term of n f, f = -(1/n) l(eta) + constants      (Eq. two)
+//   dy the derivative of l in y
+// Gaussian/identity, Poisson/log, binomial/logit (y a proportion of a trials) and Gamma/log
+// (dispersion 1; the link is not canonical: theta(e) = -exp(-e)).  bad is set where e had to be
+// clamped to keep the mean finite.
+template <typename T>
+struct CellTerms {
+  T u, w, l, dy;
+};
+template <typename T>
+__device__ __forceinline__ CellTerms<T> family_cell(int family, T e, T y, T a, int& bad) {
+  CellTerms<T> c;
+  if (family == GLAM_GAUSSIAN_IDENTITY) {
+    const T r = y - e;              // identity link: mu = eta
+    c.u = a * r;
+    c.w = a;                        // theta' = (g^-1)' = 1
+    c.l = T(0.5) * a * r * r;
+    c.dy = a * r;
+  } else if (family == GLAM_POISSON_LOG) {
+    T ec = e;
+    if (ec > poisson_clamp<T>()) {
+      ec = poisson_clamp<T>();
+      bad = 1;
+    }
+    const T mu = t_exp<T>(ec);      // log link: mu = exp(eta)
+    c.u = a * (y - mu);
+    c.w = a * mu;                   // (g^-1)' = exp(eta)
+    c.l = a * (mu - y * e);
+    c.dy = -a * e;
+  } else if (family == GLAM_BINOMIAL_LOGIT) {
+    const T ex = t_exp<T>(-fabs(e));  // in (0, 1]: no overflow on either side
+    const T mu = e >= T(0) ? T(1) / (T(1) + ex) : ex / (T(1) + ex);
+    c.u = a * (y - mu);
+    c.w = a * mu * (T(1) - mu);     // (g^-1)' = mu (1 - mu)
+    c.l = a * (fmax(e, T(0)) + t_log1p<T>(ex) - y * e);  // log(1 + e^eta) - y eta
+    c.dy = -a * e;
+  } else {                          // GLAM_GAMMA_LOG
+    T ec = e;
+    if (ec < -poisson_clamp<T>()) {
+      ec = -poisson_clamp<T>();
+      bad = 1;
+    }
+    const T ie = t_exp<T>(-ec);     // 1 / mu
+    c.u = a * (y * ie - T(1));      // theta'(eta) = exp(-eta)
+    c.w = a;                        // theta' (g^-1)' = exp(-eta) exp(eta)
+    c.l = a * (y * ie + e);
+    c.dy = a * ie;
+  }
+  return c;
+}
+
 int red_blocks(int64_t n, int per_thread) {
   const int64_t per_block = (int64_t)kThreads * per_thread;
   int64_t b = (n + per_block - 1) / per_block;
@@ -140,23 +206,8 @@ family_kernel(int family, int64_t n, const T* __restrict__ eta, const T* __restr
       const int64_t i = base + (int64_t)k * blockDim.x + threadIdx.x;
       if (i >= n) break;
       const T e = eta[i], y = Y[i], a = A[i];
-      T u, w, l;
-      if (family == GLAM_GAUSSIAN_IDENTITY) {
-        const T r = y - e;          // identity link: mu = eta
-        u = a * r;                  // Eq. (four)
-        w = a;                      // theta' = (g^-1)' = 1
-        l = T(0.5) * a * r * r;
-      } else {
-        T ec = e;
-        if (ec > poisson_clamp<T>()) {
-          ec = poisson_clamp<T>();
-          bad = 1;
-        }
-        const T mu = t_exp<T>(ec);  // log link: mu = exp(eta)
-        u = a * (y - mu);
-        w = a * mu;                 // (g^-1)' = exp(eta)
-        l = a * (mu - y * e);
-      }
+      const CellTerms<T> c = family_cell<T>(family, e, y, a, bad);
+      const T u = c.u, w = c.w, l = c.l;
       if (!(isfinite(e) && isfinite(y) && isfinite(a))) bad = 1;
       if (V != nullptr) V[i] = TV(w);
       if (VZ != nullptr) VZ[i] = u + w * e;  // V (.) Z with Z = W^-1 u + eta (Eq. ten)
@@ -202,13 +253,8 @@ loss_kernel(int family, int64_t n, const T* __restrict__ eta, const T* __restric
     for (int k = 0; k < kEPT; ++k) {
       const int64_t i = base + (int64_t)k * blockDim.x + threadIdx.x;
       if (i >= n) break;
-      const T e = eta[i], y = Y[i], a = A[i];
-      if (family == GLAM_GAUSSIAN_IDENTITY) {
-        const T r = y - e;
-        lpart += T(0.5) * a * r * r;
-      } else {
-        lpart += a * (t_exp<T>(e) - y * e);
-      }
+      int bad = 0;
+      lpart += family_cell<T>(family, eta[i], Y[i], A[i], bad).l;
     }
     lsum += (double)lpart;
   }
@@ -228,8 +274,8 @@ loss_kernel(int family, int64_t n, const T* __restrict__ eta, const T* __restric
 // ---------------------------------------------------------------- penalized NLL and its VJP
 // Cells pass of the penalized negative log-likelihood (Sec. 2, Eqs. two/three; App. B): reduces
 // f(eta) and, for the vector-Jacobian product with the upstream scalar g (*gout, 1 if NULL),
-// writes U = -(g/n) u (so that G(U) = g grad_theta f, Eq. nineteen) and
-// GY = g df/dy: (1/n) a (y - eta) for the Gaussian loss, -(1/n) a eta for the Poisson loss.
+// writes U = -(g/n) u (so that G(U) = g grad_theta f, Eq. nineteen) and GY = g df/dy, with the
+// per-cell terms of family_cell.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 nll_cells_kernel(int family, int64_t n, const T* __restrict__ eta, const T* __restrict__ Y,
@@ -247,26 +293,11 @@ nll_cells_kernel(int family, int64_t n, const T* __restrict__ eta, const T* __re
       const int64_t i = base + (int64_t)k * blockDim.x + threadIdx.x;
       if (i >= n) break;
       const T e = eta[i], y = Y[i], a = A[i];
-      T u, dy;
-      if (family == GLAM_GAUSSIAN_IDENTITY) {
-        const T r = y - e;
-        u = a * r;
-        dy = a * r;
-        lpart += T(0.5) * a * r * r;
-      } else {
-        T ec = e;
-        if (ec > poisson_clamp<T>()) {
-          ec = poisson_clamp<T>();
-          bad = 1;
-        }
-        const T mu = t_exp<T>(ec);
-        u = a * (y - mu);
-        dy = -a * e;
-        lpart += a * (mu - y * e);
-      }
+      const CellTerms<T> c = family_cell<T>(family, e, y, a, bad);
+      lpart += c.l;
       if (!(isfinite(e) && isfinite(y) && isfinite(a))) bad = 1;
-      if (U != nullptr) U[i] = su * u;
-      if (GY != nullptr) GY[i] = sy * dy;
+      if (U != nullptr) U[i] = su * c.u;
+      if (GY != nullptr) GY[i] = sy * c.dy;
     }
     lsum += (double)lpart;
   }
@@ -495,6 +526,8 @@ armijo_stream_kernel(int family, int64_t n, const TE* __restrict__ eta, const T*
       if (i >= n) break;
       const T e = T(eta[i]), y = T(Y[i]), a = T(A[i]);
       const T d = deta[i];  // eta(theta~) - eta(theta) = H(theta~ - theta)
+      // part[0]: <u, d>; part[1 + j]: the cell's loss change at the step alpha_j d, each written
+      // as a difference that keeps its digits for small steps (expm1, log1p)
       if (family == GLAM_GAUSSIAN_IDENTITY) {
         const T r = T(Y[i] - eta[i]);
         part[0] += a * r * d;
@@ -503,13 +536,31 @@ armijo_stream_kernel(int family, int64_t n, const TE* __restrict__ eta, const T*
           const T t = alpha[j] * d;
           part[1 + j] += a * (t * (T(0.5) * t - r));
         }
-      } else {
+      } else if (family == GLAM_POISSON_LOG) {
         const T mu = t_exp<T>(e);
         part[0] += a * (y - mu) * d;
 #pragma unroll
         for (int j = 0; j < kTrials; ++j) {
           const T t = alpha[j] * d;
           part[1 + j] += a * (mu * t_expm1<T>(t) - y * t);
+        }
+      } else if (family == GLAM_BINOMIAL_LOGIT) {
+        // log(1 + e^(eta + t)) - log(1 + e^eta) = log1p(mu expm1(t))
+        const T ex = t_exp<T>(-fabs(e));
+        const T mu = e >= T(0) ? T(1) / (T(1) + ex) : ex / (T(1) + ex);
+        part[0] += a * (y - mu) * d;
+#pragma unroll
+        for (int j = 0; j < kTrials; ++j) {
+          const T t = alpha[j] * d;
+          part[1 + j] += a * (t_log1p<T>(mu * t_expm1<T>(t)) - y * t);
+        }
+      } else {  // Gamma, log link: l = y e^-eta + eta
+        const T ie = t_exp<T>(-e);
+        part[0] += a * (y * ie - T(1)) * d;
+#pragma unroll
+        for (int j = 0; j < kTrials; ++j) {
+          const T t = alpha[j] * d;
+          part[1 + j] += a * (y * ie * t_expm1<T>(-t) + t);
         }
       }
     }

@@ -150,7 +150,7 @@ def test_autograd_every_coordinate_first_draws(setup):
         assert checked >= 0.9 * theta.size
 
 
-@pytest.mark.parametrize("fam", [gen.GAUSSIAN, gen.POISSON])
+@pytest.mark.parametrize("fam", [gen.GAUSSIAN, gen.POISSON, gen.BINOMIAL, gen.GAMMA])
 def test_gradcheck_fp64_plan(fam):
     """torch.autograd.gradcheck (its own finite differences in FP64) on a small ragged problem
     with an FP64 plan, masked cells and non-unit penalty weights."""
@@ -174,7 +174,7 @@ def test_gradcheck_fp64_plan(fam):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("fam", [gen.GAUSSIAN, gen.POISSON])
+@pytest.mark.parametrize("fam", [gen.GAUSSIAN, gen.POISSON, gen.BINOMIAL, gen.GAMMA])
 def test_penalized_nll_ragged_against_oracle(prec, fam):
     """Ragged shapes spanning several GEMM tiles, masked cells, random penalty weights; the raw
     entry point with an explicit upstream gradient g = 2.5 (the VJP scales by it)."""

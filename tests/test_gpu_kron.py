@@ -8,7 +8,8 @@ the oracle and against the exact-weight path.
   the exact-weight path and the oracle's KKT conditions hold;
 * the 128 x 128 x 600 workload: every lambda of the kron path meets KKT 1e-6 and its objectives
   equal the exact path's;
-* the option is refused where the weights are not a tensor product (Poisson; a masked W).
+* the option is refused where the weights are not a tensor product (Poisson; a masked W);
+* the Gamma family (log link: IRLS weight = observation weight) takes the same form.
 """
 import os
 
@@ -48,10 +49,12 @@ def test_kron_gauss20_path_matches_oracle(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_kron_tensor_weights_match_exact_path(prec):
+@pytest.mark.parametrize("fam", [gen.GAUSSIAN, gen.GAMMA])
+def test_kron_tensor_weights_match_exact_path(prec, fam):
+    """Gaussian and Gamma/log: both have IRLS weight = observation weight, a tensor product here."""
     torch, g = gpu_or_skip()
     n, p = (37, 29, 13), (9, 7, 6)
-    pr = gen.random_problem(21, n, p, gen.GAUSSIAN, basis="normal", pen_w="random")
+    pr = gen.random_problem(21, n, p, fam, basis="normal", pen_w="random")
     rng = np.random.default_rng(22)
     ws = [rng.uniform(0.3, 1.8, n[j]) for j in range(3)]
     W = np.einsum("k,j,i->kji", ws[2], ws[1], ws[0])  # C-order (n3, n2, n1)
@@ -59,14 +62,15 @@ def test_kron_tensor_weights_match_exact_path(prec):
     cast = (lambda a: np.asarray(a, np.float64)) if prec == "fp64" else (
         lambda a: np.asarray(a, np.float32).astype(np.float64))
     XT, Y, Wc = [cast(x) for x in pr.XT], cast(pr.Y), cast(W)
-    d = O.GlamData.from_c(gen.GAUSSIAN, XT, Y, Wc, pr.pen_w)
-    tol = 1e-9 if prec == "fp64" else 1e-6
+    d = O.GlamData.from_c(fam, XT, Y, Wc, pr.pen_w)
+    tol = (1e-8 if fam == gen.GAMMA else 1e-9) if prec == "fp64" else 1e-6
     paths = []
     for iwls in (g.GLAM_IWLS_EXACT, g.GLAM_IWLS_KRON):
-        plan = g.Plan(n, p, gen.GAUSSIAN, plan_prec(g, prec))
+        plan = g.Plan(n, p, fam, plan_prec(g, prec))
         res = g.glam_fit_path(plan, [dev(x, dt) for x in XT], dev(Y, dt), dev(Wc, dt),
                               dev(pr.pen_w, torch.float64), nlambda=6,
-                              opts=g.glam_opts_default(tol=tol, lambda_min_ratio=1e-2, iwls=iwls))
+                              opts=g.glam_opts_default(tol=tol, lambda_min_ratio=1e-2, iwls=iwls,
+                                                       max_outer=200))
         assert res.status == g.GLAM_OK, res.message
         paths.append((res.lambdas, host(res.path)))
     lmax = O.lambda_max(d)
@@ -74,9 +78,9 @@ def test_kron_tensor_weights_match_exact_path(prec):
     assert np.allclose(lam_e, lam_k, rtol=1e-12)
     for k in range(6):
         te, tk = O.paper_array(pe[k]), O.paper_array(pk[k])
-        assert O.kkt_residual(d, tk, lam_k[k], lmax) <= (1e-9 if prec == "fp64" else 3e-6), k
+        assert O.kkt_residual(d, tk, lam_k[k], lmax) <= (3 * tol if prec == "fp64" else 3e-6), k
         Fe, Fk = O.objective(d, te, lam_e[k]), O.objective(d, tk, lam_k[k])
-        assert abs(Fe - Fk) <= (1e-11 if prec == "fp64" else 1e-7) * abs(Fe), (k, Fe, Fk)
+        assert abs(Fe - Fk) <= (1e-10 if prec == "fp64" else 1e-7) * abs(Fe), (k, Fe, Fk)
 
 
 def test_kron_full_size_gaussian_path():

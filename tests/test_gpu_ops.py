@@ -60,8 +60,11 @@ def test_predict_two_dimensional():
     assert rel_err(host(eta), ref) <= 1e-12
 
 
+FAMILIES = [gen.GAUSSIAN, gen.POISSON, gen.BINOMIAL, gen.GAMMA]
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("fam", [gen.GAUSSIAN, gen.POISSON])
+@pytest.mark.parametrize("fam", FAMILIES)
 @pytest.mark.parametrize("n,p", SHAPES[:4])
 def test_gradient_and_loss(prec, fam, n, p):
     torch, g = gpu_or_skip()
@@ -82,7 +85,7 @@ def test_gradient_and_loss(prec, fam, n, p):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("fam", [gen.GAUSSIAN, gen.POISSON])
+@pytest.mark.parametrize("fam", FAMILIES)
 @pytest.mark.parametrize("n,p", [SHAPES[0], SHAPES[1], SHAPES[4]])
 def test_quad_build_and_prox_step(prec, fam, n, p):
     torch, g = gpu_or_skip()
