@@ -508,6 +508,50 @@ def gdpg(data: GlamData, lam, theta0, lmax, tol=1e-9, tol_inner=1e-12, max_outer
     return theta, st
 
 
+# --------------------------------------------------------------------------------------
+# SCAD penalty by the multistep adaptive lasso (the package's penalty = "scad", Sec. 6.4)
+# --------------------------------------------------------------------------------------
+
+SCAD_A = 3.7
+
+
+def scad_derivative(t, lam, a=SCAD_A):
+    """p'_lambda(|t|) of the SCAD penalty: lambda for |t| <= lambda, (a lambda - |t|)_+ / (a - 1)
+    beyond."""
+    t = np.abs(np.asarray(t, dtype=np.float64))
+    return np.where(t <= lam, lam, np.maximum(a * lam - t, 0.0) / (a - 1.0))
+
+
+def msa_scad(data: GlamData, lam, theta0, lmax, steps, a=SCAD_A, **kw):
+    """One lambda of the SCAD fit by the multistep adaptive lasso: step 0 solves the weighted
+    lasso with the base weights omega (data.pen_w); step s solves it with the weights
+    omega * p'_lambda(|theta^(s-1)|) / lambda, the local linear approximation of the SCAD penalty
+    at the previous step's solution (a weighted l1 problem, so Algorithm 1 solves each step).
+    Returns (theta, FitStats of the last step, the last step's weights)."""
+    theta = np.array(theta0, dtype=np.float64)
+    w = data.pen_w
+    st = None
+    for s in range(steps):
+        if s > 0:
+            w = data.pen_w * scad_derivative(theta, lam, a) / lam
+        ds = GlamData(data.family, data.Xs, data.Y, data.a, w)
+        theta, st = gdpg(ds, lam, theta, lmax, **kw)
+    return theta, st, w
+
+
+def scad_path(data: GlamData, lambdas, steps, a=SCAD_A, theta0=None, **kw):
+    """Warm-started SCAD path: each lambda starts from the previous lambda's solution."""
+    lmax = lambda_max(data)
+    theta = np.zeros(data.pshape) if theta0 is None else np.array(theta0, dtype=np.float64)
+    thetas, stats, weights = [], [], []
+    for lam in lambdas:
+        theta, st, w = msa_scad(data, lam, theta, lmax, steps, a, **kw)
+        thetas.append(theta.copy())
+        stats.append(st)
+        weights.append(w)
+    return np.array(thetas), stats, weights, lmax
+
+
 def fit_path(data: GlamData, nlambda=10, ratio=1e-3, lambdas=None, theta0=None, **kw):
     """Warm-started lambda path (Sec. 6.4): lambda_max down to ratio*lambda_max, each fit
     started from the previous solution.  Returns (lambdas, thetas[K, p1, .., pd], stats)."""
