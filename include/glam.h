@@ -115,11 +115,22 @@ typedef struct {
                               itself (Gaussian; Gamma with log link) with an observation-weight
                               array W that is a tensor product w1 (x) w2 (x) w3 with W(0,0,0) > 0
                               (W = 1 included); otherwise glam_fit_path returns GLAM_EINVAL */
-  int32_t reserved[5];
+  int32_t penalty;         /* GLAM_PENALTY_LASSO (default): the weighted l1 penalty of Eq. (five);
+                              GLAM_PENALTY_SCAD: the SCAD penalty (a = 3.7) by the multistep
+                              adaptive lasso of the package (Sec. 6.4): per lambda, step 0 solves
+                              the weighted lasso with pen_w, step s >= 1 the lasso with weights
+                              pen_w * p'_lambda(|theta^(s-1)|) / lambda, p' the SCAD derivative
+                              (lambda up to lambda, (a lambda - t)_+ / (a - 1) beyond); the
+                              stats of a lambda then sum the steps' iterations and report the
+                              objective and KKT residual of the last weighted problem */
+  int32_t steps;           /* MSA steps per lambda for GLAM_PENALTY_SCAD (default 1, >= 1) */
+  int32_t reserved[3];
 } glam_opts;
 
 #define GLAM_IWLS_EXACT 0
 #define GLAM_IWLS_KRON 1
+#define GLAM_PENALTY_LASSO 0
+#define GLAM_PENALTY_SCAD 1
 
 /* Per-lambda record written by glam_fit_path (HOST array of nlambda entries). */
 typedef struct {

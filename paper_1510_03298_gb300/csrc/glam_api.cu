@@ -70,6 +70,7 @@ struct glam_plan {
   double* d_gram = nullptr;        // p_j x p_j Gram scratch (p_j <= 64)
   double* kfac[3] = {nullptr, nullptr, nullptr};  // factors of a tensor-product W (n_j each)
   double* kgram = nullptr;         // the FP64 weighted Gram matrices, p1^2 + p2^2 + p3^2
+  double* pen_base = nullptr;      // the caller's penalty weights during a SCAD fit (p)
   unsigned long long* kcheck = nullptr;
   std::vector<void*> allocs;
 };
@@ -363,6 +364,9 @@ int glam_opts_default(glam_opts* o) {
   o->max_outer = 50;
   o->max_linesearch = 30;
   o->check_every = 32;
+  o->iwls = GLAM_IWLS_EXACT;
+  o->penalty = GLAM_PENALTY_LASSO;
+  o->steps = 1;
   return GLAM_OK;
 }
 
@@ -1000,6 +1004,8 @@ int kron_setup(Fit<T>& f, const T* W, double& rho_kron, double& wmax) {
   return GLAM_OK;
 }
 
+constexpr double kScadA = 3.7;  // the SCAD shape parameter (Fan and Li's choice)
+
 template <typename T>
 int fit_impl(glam_plan* pl, const void* const X[3], const T* Y, const T* W, const double* pen,
              int nlambda, double* lambda, const glam_opts& o, const double* Theta0, double* path,
@@ -1030,6 +1036,11 @@ int fit_impl(glam_plan* pl, const void* const X[3], const T* Y, const T* W, cons
     f.W64 = pl->wd.Wc;
   }
   CK(cudaMemcpyAsync(pl->pen, pen, sizeof(double) * pl->p, cudaMemcpyDeviceToDevice, f.s));
+  const bool scad = o.penalty == GLAM_PENALTY_SCAD;
+  if (scad) {
+    if (pl->pen_base == nullptr) CKS(dalloc(pl, &pl->pen_base, pl->p));
+    CK(cudaMemcpyAsync(pl->pen_base, pen, sizeof(double) * pl->p, cudaMemcpyDeviceToDevice, f.s));
+  }
   // input checks
   CK(cudaMemsetAsync(&pl->sc->nonfinite, 0, sizeof(int), f.s));
   CK(launch_check_finite<double>(pl->n, f.Y64, pl->sc, f.s));
@@ -1087,7 +1098,27 @@ int fit_impl(glam_plan* pl, const void* const X[3], const T* Y, const T* W, cons
     const auto t0 = std::chrono::steady_clock::now();
     LamOut lo;
     CK(cudaMemsetAsync(&pl->sc->nonfinite, 0, sizeof(int), f.s));
-    CKS(solve_lambda<T>(f, lams[k], lo));
+    const int nsteps = scad ? o.steps : 1;
+    for (int st = 0; st < nsteps; ++st) {
+      // SCAD by the multistep adaptive lasso (Sec. 6.4): step 0 with the caller's weights, step
+      // st >= 1 with the local linear approximation at the previous step's solution
+      if (scad)
+        CK(st == 0 ? cudaMemcpyAsync(pl->pen, pl->pen_base, sizeof(double) * pl->p,
+                                     cudaMemcpyDeviceToDevice, f.s)
+                   : launch_scad_weights(pl->p, pl->th, pl->pen_base, lams[k], kScadA, pl->pen, f.s));
+      LamOut ls;
+      CKS(solve_lambda<T>(f, lams[k], ls));
+      lo.outer += ls.outer;
+      lo.inner += ls.inner;
+      lo.passes += ls.passes;
+      lo.backtracks += ls.backtracks;
+      lo.nnz = ls.nnz;
+      lo.kkt = ls.kkt;
+      lo.F = ls.F;
+      lo.converged = ls.converged;
+      lo.nonfinite = ls.nonfinite;
+      if (!ls.converged) break;
+    }
     CK(cudaMemcpyAsync(path + (size_t)k * pl->p, pl->th, sizeof(double) * pl->p, cudaMemcpyDeviceToDevice, f.s));
     CK(cudaStreamSynchronize(f.s));
     const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -1140,7 +1171,8 @@ int glam_fit_path(glam_plan* pl, const void* const X[3], const void* Y, const vo
   if (o.max_inner < 1 || o.max_outer < 1 || o.max_linesearch < 1 || !(o.tol > 0) ||
       !(o.inner_forcing > 0) || !(o.inner_floor > 0) || !(o.armijo_b > 0 && o.armijo_b < 1) ||
       !(o.armijo_v > 0 && o.armijo_v < 1) || !(o.armijo_alpha0 > 0) ||
-      !(o.iwls == GLAM_IWLS_EXACT || o.iwls == GLAM_IWLS_KRON))
+      !(o.iwls == GLAM_IWLS_EXACT || o.iwls == GLAM_IWLS_KRON) ||
+      !(o.penalty == GLAM_PENALTY_LASSO || o.penalty == GLAM_PENALTY_SCAD) || o.steps < 1)
     return fail(pl, GLAM_EINVAL, "glam_fit_path: bad options");
   if (lambda[0] >= 0)
     for (int k = 0; k < nlambda; ++k)

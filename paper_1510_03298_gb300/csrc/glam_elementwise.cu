@@ -348,6 +348,21 @@ nll_coef_kernel(int64_t p, const T* __restrict__ th, const T* __restrict__ pw, d
   }
 }
 
+// ---------------------------------------------------------------- SCAD weights
+// Weights of step s >= 1 of the multistep adaptive lasso for the SCAD penalty: the local linear
+// approximation at theta, w[m] = base[m] p'_lambda(|theta_m|) / lambda with p'_lambda(t) = lambda
+// for t <= lambda and (a lambda - t)_+ / (a - 1) beyond.
+__global__ void scad_weights_kernel(int64_t p, const double* __restrict__ th,
+                                    const double* __restrict__ base, double lambda, double a,
+                                    double* __restrict__ w) {
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < p;
+       m += (int64_t)gridDim.x * blockDim.x) {
+    const double t = fabs(th[m]);
+    const double d = t <= lambda ? lambda : fmax(a * lambda - t, 0.0) / (a - 1.0);
+    w[m] = base[m] * (d / lambda);
+  }
+}
+
 // ---------------------------------------------------------------- scale / convert / finite
 template <typename T>
 __global__ void scale_kernel(int64_t n, const T* __restrict__ in, T* __restrict__ out, T scale) {
@@ -931,6 +946,13 @@ template <typename T>
 cudaError_t launch_lambda_max(int64_t p, const double* g0, const T* pen_w, DevScalars* sc,
                               RedScratch red, cudaStream_t s) {
   lmax_kernel<T><<<red_blocks(p, 1), kThreads, 0, s>>>(p, g0, pen_w, sc, red);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scad_weights(int64_t p, const double* theta, const double* base, double lambda,
+                                double a, double* w, cudaStream_t s) {
+  scad_weights_kernel<<<grid_for(p), kThreads, 0, s>>>(p, theta, base, lambda, a, w);
   count_launches(1);
   return cudaGetLastError();
 }

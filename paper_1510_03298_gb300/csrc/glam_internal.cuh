@@ -205,6 +205,10 @@ cudaError_t launch_extrap(int64_t n, const T* x, const T* xp, double omega, T* y
 
 cudaError_t launch_gram(int nj, int pj, const double* XT, double* gram, cudaStream_t s);
 
+// Multistep-adaptive-lasso weights of the SCAD penalty: w = base * p'_lambda(|theta|) / lambda.
+cudaError_t launch_scad_weights(int64_t p, const double* theta, const double* base, double lambda,
+                                double a, double* w, cudaStream_t s);
+
 template <typename T>
 cudaError_t launch_sum_splits(int64_t p, int ksplit, const T* part, T* out, cudaStream_t s);
 

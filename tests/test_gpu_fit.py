@@ -221,3 +221,34 @@ def test_binomial_and_gamma_paths_match_oracle(prec, fam):
             assert Fref - F <= 1e-6 * abs(Fref), (k, F, Fref)
         else:
             assert abs(F - Fref) <= (1e-9 if prec == "fp64" else 1e-6) * abs(Fref), (k, F, Fref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("fam", [gen.GAUSSIAN, gen.POISSON])
+def test_scad_path_matches_oracle(prec, fam):
+    """SCAD by the multistep adaptive lasso (penalty = GLAM_PENALTY_SCAD, 3 steps per lambda)
+    against the oracle's MSA path: the solutions agree, and each meets the KKT conditions of its
+    last weighted-lasso step with the weights the oracle derives from its own previous step (the
+    two sides' previous steps agree to their KKT tolerance, and the SCAD weights are continuous
+    in theta)."""
+    torch, g = gpu_or_skip()
+    n, p = (13, 11, 9), (5, 4, 4)
+    pr = gen.random_problem(71, n, p, fam, mask_frac=0.1, basis="normal")
+    d = O.GlamData.from_c(pr.family, pr.XT, pr.Y, pr.W, pr.pen_w)
+    lmax = O.lambda_max(d)
+    lams = list(lmax * np.array([1.0, 0.4, 0.15, 0.05]))
+    thetas, stats, weights, _ = O.scad_path(d, lams, steps=3, tol=1e-11)
+    dt = dtype_of(prec)
+    plan = g.Plan(n, p, fam, plan_prec(g, prec))
+    tol = 1e-10 if prec == "fp64" else 1e-7
+    res = g.glam_fit_path(plan, [dev(x, dt) for x in pr.XT], dev(pr.Y, dt), dev(pr.W, dt),
+                          dev(pr.pen_w, torch.float64), lambdas=lams,
+                          opts=g.glam_opts_default(tol=tol, penalty=g.GLAM_PENALTY_SCAD, steps=3))
+    assert res.status == g.GLAM_OK, res.message
+    path = host(res.path)
+    for k in range(len(lams)):
+        th = O.paper_array(path[k])
+        scale = max(1.0, float(np.abs(thetas[k]).max()))
+        np.testing.assert_allclose(th, thetas[k], atol=(1e-7 if prec == "fp64" else 1e-4) * scale)
+        dk = O.GlamData(d.family, d.Xs, d.Y, d.a, weights[k])
+        assert O.kkt_residual(dk, th, lams[k], lmax) <= (1e-7 if prec == "fp64" else 1e-4), k
