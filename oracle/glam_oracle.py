@@ -247,9 +247,18 @@ def loss_grad_y(family, eta, y, a) -> np.ndarray:
 # Penalty and proximal operator (Sec. 6.3)
 # --------------------------------------------------------------------------------------
 
-def penalty(theta, pen_w) -> float:
-    """J(theta) = sum_m omega_m |theta_m| (weighted l1)."""
-    return float(np.sum(pen_w * np.abs(theta)))
+def penalty(theta, pen_w, l1=1.0, l2=0.0) -> float:
+    """J(theta) = sum_m omega_m (l1 |theta_m| + l2 theta_m^2): the weighted l1 penalty (l1 = 1,
+    l2 = 0), the elastic net ||theta||_1 + alpha ||theta||_2^2 of Sec. 6.3 (l1 = 1, l2 = alpha) and
+    the ridge penalty ||theta||_2^2 (l1 = 0, l2 = 1)."""
+    t = np.asarray(theta, dtype=np.float64)
+    return float(np.sum(pen_w * (l1 * np.abs(t) + l2 * t * t)))
+
+
+def penalty_prox(z, gamma, l1=1.0, l2=0.0):
+    """prox of gamma (l1 |.| + l2 (.)^2) per coordinate (gamma may be per coordinate): the soft
+    threshold at gamma l1, then the ridge shrinkage 1 / (1 + 2 gamma l2) (Sec. 6.3)."""
+    return soft_threshold(z, gamma * l1) / (1.0 + 2.0 * gamma * l2)
 
 
 def soft_threshold(z, gamma):
@@ -326,6 +335,8 @@ class GlamData:
     Y: np.ndarray
     a: np.ndarray
     pen_w: np.ndarray
+    l1: float = 1.0   # penalty J = sum omega (l1 |theta| + l2 theta^2), see `penalty`
+    l2: float = 0.0
 
     @property
     def n(self) -> int:
@@ -346,7 +357,7 @@ class GlamData:
 def objective(data: GlamData, theta, lam) -> float:
     """F(theta) = f(eta(theta)) + lambda J(theta), Eq. (five) with the 1/n scaling of R1."""
     eta = H(data.Xs, theta)
-    return loss(data.family, eta, data.Y, data.a) + lam * penalty(theta, data.pen_w)
+    return loss(data.family, eta, data.Y, data.a) + lam * penalty(theta, data.pen_w, data.l1, data.l2)
 
 
 def gradient(data: GlamData, theta) -> np.ndarray:
@@ -364,10 +375,12 @@ def penalized_gradient(data: GlamData, theta, lam) -> np.ndarray:
 
 
 def lambda_max(data: GlamData) -> float:
-    """The smallest lambda whose solution is zero (Sec. 6.4): max_m |g_m(0)| / omega_m with
-    g(0) the gradient of f at theta = 0 (the KKT condition of Eq. five at zero)."""
+    """The smallest lambda whose solution is zero (Sec. 6.4): max_m |g_m(0)| / (omega_m l1) with
+    g(0) the gradient of f at theta = 0 (the KKT condition of Eq. five at zero).  The ridge
+    penalty (l1 = 0) has no such lambda; its path starts from the lasso's value (reading R19)."""
     g0 = gradient(data, np.zeros(data.pshape))
-    return float(np.max(np.abs(g0) / data.pen_w))
+    l1 = data.l1 if data.l1 > 0 else 1.0
+    return float(np.max(np.abs(g0) / (data.pen_w * l1)))
 
 
 def lambda_sequence(lmax, nlambda, ratio) -> np.ndarray:
@@ -378,12 +391,14 @@ def lambda_sequence(lmax, nlambda, ratio) -> np.ndarray:
 
 
 def kkt_residual(data: GlamData, theta, lam, lmax, grad=None) -> float:
-    """Scaled lasso KKT residual of Eq. (five): r = max_m r_m / lambda_max with
-    r_m = |g_m + lambda omega_m sign(theta_m)| if theta_m != 0 and
-    r_m = max(0, |g_m| - lambda omega_m) if theta_m = 0, g = grad f(theta)."""
+    """Scaled KKT residual of Eq. (five): r = max_m r_m / lambda_max with
+    r_m = |g_m + lambda omega_m (l1 sign(theta_m) + 2 l2 theta_m)| if theta_m != 0 and
+    r_m = max(0, |g_m| - lambda omega_m l1) if theta_m = 0, g = grad f(theta) (the distance of -g
+    to lambda times the subdifferential of J)."""
     g = gradient(data, theta) if grad is None else grad
     thr = lam * data.pen_w
-    r = np.where(theta != 0, np.abs(g + thr * np.sign(theta)), np.maximum(0.0, np.abs(g) - thr))
+    r = np.where(theta != 0, np.abs(g + thr * (data.l1 * np.sign(theta) + 2.0 * data.l2 * theta)),
+                 np.maximum(0.0, np.abs(g) - thr * data.l1))
     return float(np.max(r)) / lmax
 
 
@@ -410,14 +425,14 @@ def inner_pg(data: GlamData, V, Z, theta0, delta, lam, tol=1e-12, max_iter=10000
     x_prev = np.array(theta0, dtype=np.float64)
     x = x_prev.copy()
     hist = [x.copy()] if keep_history else None
-    thr = delta * lam * data.pen_w
+    gam = delta * lam * data.pen_w
     it = 0
     for l in range(1, max_iter + 1):
         it = l
         omega = (l - 1.0) / (l + 2.0)
         y = x + omega * (x - x_prev)
         grad_h = (G(data.Xs, V * H(data.Xs, y)) - b) / n
-        x_new = soft_threshold(y - delta * grad_h, thr)
+        x_new = penalty_prox(y - delta * grad_h, gam, data.l1, data.l2)
         step = float(np.max(np.abs(x_new - x))) if x.size else 0.0
         scale = max(1.0, float(np.max(np.abs(x))) if x.size else 0.0)
         x_prev, x = x, x_new
@@ -454,7 +469,8 @@ def gdpg(data: GlamData, lam, theta0, lmax, tol=1e-9, tol_inner=1e-12, max_outer
     theta = np.array(theta0, dtype=np.float64)
     st = FitStats()
     eta = H(data.Xs, theta)
-    F = loss(fam, eta, data.Y, data.a) + lam * penalty(theta, data.pen_w)
+    J = lambda t: penalty(t, data.pen_w, data.l1, data.l2)
+    F = loss(fam, eta, data.Y, data.a) + lam * J(theta)
     st.objective_trace.append(F)
     for k in range(max_outer):
         # Step 2: U, V and Z at theta(k)
@@ -477,14 +493,13 @@ def gdpg(data: GlamData, lam, theta0, lmax, tol=1e-9, tol_inner=1e-12, max_outer
         # Step 5: Armijo line search along d = theta~ - theta
         d = theta_t - theta
         eta_t = H(data.Xs, theta_t)
-        Delta = -float(np.sum(u * (eta_t - eta))) / n + lam * (penalty(theta_t, data.pen_w)
-                                                               - penalty(theta, data.pen_w))
+        Delta = -float(np.sum(u * (eta_t - eta))) / n + lam * (J(theta_t) - J(theta))
         alpha = alpha0
         accepted = False
         for j in range(max_ls):
             th = theta + alpha * d
             eta_j = H(data.Xs, th)
-            F_j = loss(fam, eta_j, data.Y, data.a) + lam * penalty(th, data.pen_w)
+            F_j = loss(fam, eta_j, data.Y, data.a) + lam * J(th)
             if F_j <= F + alpha * v * Delta:
                 accepted = True
                 break
