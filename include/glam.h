@@ -116,6 +116,9 @@ typedef struct {
                               array W that is a tensor product w1 (x) w2 (x) w3 with W(0,0,0) > 0
                               (W = 1 included); otherwise glam_fit_path returns GLAM_EINVAL */
   int32_t penalty;         /* GLAM_PENALTY_LASSO (default): the weighted l1 penalty of Eq. (five);
+                              GLAM_PENALTY_ENET / GLAM_PENALTY_RIDGE: the elastic net and ridge
+                              penalties of Sec. 6.3 (below; the KKT residual is then the distance
+                              of -grad f to lambda times the subdifferential of J);
                               GLAM_PENALTY_SCAD: the SCAD penalty (a = 3.7) by the multistep
                               adaptive lasso of the package (Sec. 6.4): per lambda, step 0 solves
                               the weighted lasso with pen_w, step s >= 1 the lasso with weights
@@ -125,12 +128,16 @@ typedef struct {
                               objective and KKT residual of the last weighted problem */
   int32_t steps;           /* MSA steps per lambda for GLAM_PENALTY_SCAD (default 1, >= 1) */
   int32_t reserved[3];
+  double enet_alpha;       /* GLAM_PENALTY_ENET: J = sum_m w_m (|theta_m| + enet_alpha theta_m^2),
+                              the elastic net of Sec. 6.3 (default 0, >= 0) */
 } glam_opts;
 
 #define GLAM_IWLS_EXACT 0
 #define GLAM_IWLS_KRON 1
 #define GLAM_PENALTY_LASSO 0
 #define GLAM_PENALTY_SCAD 1
+#define GLAM_PENALTY_ENET 2  /* J = sum w (|theta| + alpha theta^2); prox: soft threshold, then / (1 + 2 alpha gamma) */
+#define GLAM_PENALTY_RIDGE 3 /* J = sum w theta^2; prox: / (1 + 2 gamma); lambda_max is the lasso's */
 
 /* Per-lambda record written by glam_fit_path (HOST array of nlambda entries). */
 typedef struct {

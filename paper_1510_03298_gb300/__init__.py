@@ -22,7 +22,8 @@ import torch
 __all__ = [
     "GLAM_OK", "GLAM_EINVAL", "GLAM_ENOMEM", "GLAM_ECUDA", "GLAM_ENONFINITE", "GLAM_ENOCONV",
     "GLAM_ETIMEOUT", "GLAM_GAUSSIAN_IDENTITY", "GLAM_POISSON_LOG", "GLAM_BINOMIAL_LOGIT", "GLAM_GAMMA_LOG", "GLAM_FP64", "GLAM_FP32",
-    "GLAM_TF32", "GLAM_BF16", "GLAM_IWLS_EXACT", "GLAM_IWLS_KRON", "GLAM_PENALTY_LASSO", "GLAM_PENALTY_SCAD", "GlamError", "Plan", "Quad", "FitResult", "library_path", "load_library",
+    "GLAM_TF32", "GLAM_BF16", "GLAM_IWLS_EXACT", "GLAM_IWLS_KRON", "GLAM_PENALTY_LASSO", "GLAM_PENALTY_SCAD", "GLAM_PENALTY_ENET",
+    "GLAM_PENALTY_RIDGE", "GlamError", "Plan", "Quad", "FitResult", "library_path", "load_library",
     "glam_opts_default", "glam_plan_create", "glam_plan_destroy", "glam_predict", "glam_gradient",
     "glam_loss", "glam_quad_build", "glam_prox_step", "glam_fit_path", "glam_launch_count",
     "glam_time_inner_kernels", "glam_penalized_nll", "PenalizedNLL", "penalized_nll",
@@ -63,6 +64,8 @@ GLAM_IWLS_EXACT = _K["GLAM_IWLS_EXACT"]
 GLAM_IWLS_KRON = _K["GLAM_IWLS_KRON"]
 GLAM_PENALTY_LASSO = _K["GLAM_PENALTY_LASSO"]
 GLAM_PENALTY_SCAD = _K["GLAM_PENALTY_SCAD"]
+GLAM_PENALTY_ENET = _K["GLAM_PENALTY_ENET"]
+GLAM_PENALTY_RIDGE = _K["GLAM_PENALTY_RIDGE"]
 
 
 class GlamDims(C.Structure):
@@ -78,7 +81,8 @@ class GlamOpts(C.Structure):
                 ("inner_floor", C.c_double), ("armijo_alpha0", C.c_double), ("armijo_b", C.c_double),
                 ("armijo_v", C.c_double), ("max_inner", C.c_int32), ("max_outer", C.c_int32),
                 ("max_linesearch", C.c_int32), ("check_every", C.c_int32), ("iwls", C.c_int32),
-                ("penalty", C.c_int32), ("steps", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("penalty", C.c_int32), ("steps", C.c_int32), ("reserved", C.c_int32 * 3),
+                ("enet_alpha", C.c_double)]
 
 
 class GlamBatchItem(C.Structure):

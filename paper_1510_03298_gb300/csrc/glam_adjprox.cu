@@ -63,7 +63,7 @@ adjprox_kernel(APShape sh, const __grid_constant__ CUtensorMap mapS, const __gri
   const int done = ctl->done;
   // the loop state of this iteration; the last CTA changes it only after every CTA has arrived
   const int l = ctl->l;
-  const double delta = ctl->delta, lam = ctl->lambda;
+  const double delta = ctl->delta, lam = ctl->lambda, pl1 = ctl->pen_l1, pl2 = ctl->pen_l2;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ uint64_t mbar[kAPBufs];
   __shared__ int timed_out;
@@ -161,8 +161,9 @@ adjprox_kernel(APShape sh, const __grid_constant__ CUtensorMap mapS, const __gri
     const double g = gm + q * inv_n;            // gradient of the quadratic model
     const double y = xm + omega * (xm - xpm);   // extrapolation, Sec. 3.2
     const double z = y - delta * g;
-    const double az = fabs(z) - delta * lam * pm;  // soft threshold, Sec. 6.3
-    const double xn = az > 0.0 ? copysign(az, z) : 0.0;
+    const double gam = delta * lam * pm;
+    const double az = fabs(z) - gam * pl1;  // soft threshold, Sec. 6.3, then the ridge shrinkage
+    const double xn = (az > 0.0 ? copysign(az, z) : 0.0) / (1.0 + 2.0 * gam * pl2);
     out[mo] = xn;
     dnext[mo] = (float)(xn + omega_next * (xn - xm) - am);
     crit = fabs(xn - y);

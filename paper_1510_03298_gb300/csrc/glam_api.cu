@@ -711,7 +711,7 @@ int glam_prox_step(glam_plan* pl, const void* const X[3], const glam_quad* q, co
 namespace {
 
 __global__ void ctl_init_kernel(InnerCtl* ctl, const DevScalars* sc, double lambda, double stop_rel,
-                                int max_iter) {
+                                int max_iter, double l1, double l2) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double delta = 1.0 / sc->Lhat;  // step 3 of Alg. 1: delta = 1 / L_hat (nu = 1)
   ctl->l = 1;
@@ -725,6 +725,8 @@ __global__ void ctl_init_kernel(InnerCtl* ctl, const DevScalars* sc, double lamb
   ctl->lambda = lambda;
   ctl->stop_abs = stop_rel * sc->lmax * delta;
   ctl->crit = 0.0;
+  ctl->pen_l1 = l1;
+  ctl->pen_l2 = l2;
 }
 
 __global__ void objective_kernel(DevScalars* sc, double lambda) {
@@ -745,6 +747,7 @@ struct Fit {
   cudaGraphExec_t graph = nullptr;
   int64_t graph_kernels = 0;
   bool kron = false;  // inner loop on the tensor-product form H(<M_j>, .) (Sec. 6.2)
+  double l1 = 1.0, l2 = 0.0;  // penalty J = sum_m w_m (l1 |theta_m| + l2 theta_m^2) (Sec. 6.3)
   ~Fit() {
     if (graph) cudaGraphExecDestroy(graph);
   }
@@ -761,7 +764,7 @@ int fp64_pass(Fit<T>& f, double lambda, double& r, double& F, int& nnz, bool& no
                               f.rho_prod, pl->sc, pl->red, f.s));
   CKS(op.G(pl->wd.U, pl->gk));
   CK(launch_scale<double>(pl->p, pl->gk, pl->gk, -1.0 / (double)pl->n, f.s));
-  CK(launch_kkt<double>(pl->p, pl->gk, pl->th, pl->pen, lambda, pl->sc, pl->red, f.s));
+  CK(launch_kkt<double>(pl->p, pl->gk, pl->th, pl->pen, lambda, pl->sc, pl->red, f.s, f.l1, f.l2));
   objective_kernel<<<1, 32, 0, f.s>>>(pl->sc, lambda);
   CK(cudaGetLastError());
   count_launches(1);
@@ -869,7 +872,7 @@ int run_inner(Fit<T>& f, double lambda, double stop_rel, int max_iter, double** 
   CK(cudaMemcpyAsync(pl->x1, pl->th, sizeof(double) * pl->p, cudaMemcpyDeviceToDevice, f.s));
   CK(cudaMemsetAsync(work_of<T>(pl).dn, 0, sizeof(T) * pl->p, f.s));  // y(1) - theta_k = 0
   CK(cudaMemsetAsync(&pl->sc->timeout, 0, sizeof(int), f.s));
-  ctl_init_kernel<<<1, 32, 0, f.s>>>(pl->ctl, pl->sc, lambda, stop_rel, max_iter);
+  ctl_init_kernel<<<1, 32, 0, f.s>>>(pl->ctl, pl->sc, lambda, stop_rel, max_iter, f.l1, f.l2);
   CK(cudaGetLastError());
   count_launches(1);
   if (f.graph == nullptr) CKS(capture_chunk<T>(f));
@@ -937,7 +940,7 @@ int solve_lambda(Fit<T>& f, double lambda, LamOut& lo) {
       CK(launch_armijo_stream<double, T>(pl->family, pl->n, pl->wd.eta, w.eta_bar, f.Y64, f.W64,
                                          f.o.armijo_alpha0, f.o.armijo_b, j0, pl->sc, pl->red, f.s));
       CK(launch_armijo_penalty<double>(pl->p, pl->th, xt, pl->pen, f.o.armijo_alpha0, f.o.armijo_b,
-                                       j0, pl->sc, pl->red, f.s));
+                                       j0, pl->sc, pl->red, f.s, f.l1, f.l2));
       CK(launch_armijo_select(lambda, f.o.armijo_v, f.o.armijo_alpha0, f.o.armijo_b, j0, pl->sc, f.s));
       CK(cudaMemcpyAsync(pl->h_sc, pl->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, f.s));
       CK(cudaStreamSynchronize(f.s));
@@ -1037,6 +1040,13 @@ int fit_impl(glam_plan* pl, const void* const X[3], const T* Y, const T* W, cons
   }
   CK(cudaMemcpyAsync(pl->pen, pen, sizeof(double) * pl->p, cudaMemcpyDeviceToDevice, f.s));
   const bool scad = o.penalty == GLAM_PENALTY_SCAD;
+  if (o.penalty == GLAM_PENALTY_ENET) {
+    f.l1 = 1.0;
+    f.l2 = o.enet_alpha;
+  } else if (o.penalty == GLAM_PENALTY_RIDGE) {
+    f.l1 = 0.0;
+    f.l2 = 1.0;
+  }
   if (scad) {
     if (pl->pen_base == nullptr) CKS(dalloc(pl, &pl->pen_base, pl->p));
     CK(cudaMemcpyAsync(pl->pen_base, pen, sizeof(double) * pl->p, cudaMemcpyDeviceToDevice, f.s));
@@ -1172,7 +1182,8 @@ int glam_fit_path(glam_plan* pl, const void* const X[3], const void* Y, const vo
       !(o.inner_forcing > 0) || !(o.inner_floor > 0) || !(o.armijo_b > 0 && o.armijo_b < 1) ||
       !(o.armijo_v > 0 && o.armijo_v < 1) || !(o.armijo_alpha0 > 0) ||
       !(o.iwls == GLAM_IWLS_EXACT || o.iwls == GLAM_IWLS_KRON) ||
-      !(o.penalty == GLAM_PENALTY_LASSO || o.penalty == GLAM_PENALTY_SCAD) || o.steps < 1)
+      !(o.penalty >= GLAM_PENALTY_LASSO && o.penalty <= GLAM_PENALTY_RIDGE) || o.steps < 1 ||
+      !(o.enet_alpha >= 0.0 && std::isfinite(o.enet_alpha)))
     return fail(pl, GLAM_EINVAL, "glam_fit_path: bad options");
   if (lambda[0] >= 0)
     for (int k = 0; k < nlambda; ++k)

@@ -450,16 +450,18 @@ prox_kernel(int64_t p, int ksplit, const Tq* __restrict__ Qpart, const TP* __res
     pw0 = pen_w[m0];
     if (dnext != nullptr) an0 = anchor[m0];
   }
-  TP omega, delta, lam, omega_next = TP(0);
+  TP omega, delta, lam, omega_next = TP(0), pl1 = TP(1), pl2 = TP(0);
   if (ctl != nullptr) {
     const int done = ctl->done;
     const int l = ctl->l;
-    const double cdelta = ctl->delta, clambda = ctl->lambda;
+    const double cdelta = ctl->delta, clambda = ctl->lambda, cl1 = ctl->pen_l1, cl2 = ctl->pen_l2;
     if (done) return;
     omega = TP(l - 1) / TP(l + 2);
     omega_next = TP(l) / TP(l + 3);
     delta = TP(cdelta);
     lam = TP(clambda);
+    pl1 = TP(cl1);
+    pl2 = TP(cl2);
   } else {
     omega = omega_h;
     delta = delta_h > TP(0) ? delta_h : TP(1.0 / *Lhat);
@@ -479,9 +481,10 @@ prox_kernel(int64_t p, int ksplit, const Tq* __restrict__ Qpart, const TP* __res
     const TP g = lin_scale * lm + q * inv_n;    // gradient of the quadratic model
     const TP y = xm + omega * (xm - xpm);       // extrapolation, Sec. 3.2
     const TP z = y - delta * g;
-    const TP thr = delta * lam * pwm;
-    const TP az = fabs(z) - thr;                // soft threshold, Sec. 6.3
-    const TP xn = az > TP(0) ? copysign(az, z) : TP(0);
+    const TP gam = delta * lam * pwm;
+    const TP az = fabs(z) - gam * pl1;          // soft threshold, Sec. 6.3
+    // then the ridge shrinkage of the elastic-net / ridge prox (Sec. 6.3)
+    const TP xn = (az > TP(0) ? copysign(az, z) : TP(0)) / (TP(1) + TP(2) * gam * pl2);
     out[m] = xn;
     if (dnext != nullptr) dnext[m] = Tq(xn + omega_next * (xn - xm) - anm);
     crit = fmax(crit, (double)fabs(xn - y));
@@ -606,7 +609,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 armijo_penalty_kernel(int64_t p, const T* __restrict__ th, const T* __restrict__ tt,
                       const T* __restrict__ pw, double alpha0, double bfac, int j0, DevScalars* sc,
-                      RedScratch red) {
+                      RedScratch red, double l1, double l2) {
   constexpr int NV = kTrials + 2;
   double acc[NV];
 #pragma unroll
@@ -625,10 +628,14 @@ armijo_penalty_kernel(int64_t p, const T* __restrict__ th, const T* __restrict__
     const double t0 = (double)th[m], t1 = (double)tt[m], w = (double)pw[m];
     const double d = t1 - t0;
     const double a0 = fabs(t0);
-    acc[0] += w * a0;
-    acc[1] += w * (fabs(t1) - a0);
+    // J = sum w (l1 |t| + l2 t^2); the changes use t^2 - t0^2 = s (2 t0 + s), s = t - t0
+    acc[0] += w * (l1 * a0 + l2 * t0 * t0);
+    acc[1] += w * (l1 * (fabs(t1) - a0) + l2 * d * (2.0 * t0 + d));
 #pragma unroll
-    for (int j = 0; j < kTrials; ++j) acc[2 + j] += w * (fabs(t0 + alpha[j] * d) - a0);
+    for (int j = 0; j < kTrials; ++j) {
+      const double sj = alpha[j] * d;
+      acc[2 + j] += w * (l1 * (fabs(t0 + sj) - a0) + l2 * sj * (2.0 * t0 + sj));
+    }
   }
   block_sum<NV>(acc);
   if (threadIdx.x == 0)
@@ -690,21 +697,22 @@ __global__ void armijo_update_kernel(int64_t p, T* __restrict__ th, const T* __r
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 kkt_kernel(int64_t p, const double* __restrict__ g, const T* __restrict__ th,
-           const T* __restrict__ pw, double lambda, DevScalars* sc, RedScratch red) {
+           const T* __restrict__ pw, double lambda, DevScalars* sc, RedScratch red, double l1,
+           double l2) {
   double rmax = 0.0;
   double acc[2] = {0.0, 0.0};  // J(theta), nnz
   for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < p;
        m += (int64_t)gridDim.x * blockDim.x) {
     const double t = (double)th[m], thr = lambda * (double)pw[m], gm = g[m];
     double r;
-    if (t != 0.0) {
-      r = fabs(gm + copysign(thr, t));
+    if (t != 0.0) {  // distance of -g to lambda dJ: J = sum w (l1 |t| + l2 t^2)
+      r = fabs(gm + thr * (copysign(l1, t) + 2.0 * l2 * t));
       acc[1] += 1.0;
     } else {
-      r = fmax(0.0, fabs(gm) - thr);
+      r = fmax(0.0, fabs(gm) - thr * l1);
     }
     rmax = fmax(rmax, r);
-    acc[0] += (double)pw[m] * fabs(t);
+    acc[0] += (double)pw[m] * (l1 * fabs(t) + l2 * t * t);
   }
   block_sum<2>(acc);
   const double bm = block_max(rmax);
@@ -902,9 +910,9 @@ cudaError_t launch_armijo_stream(int family, int64_t n, const TE* eta, const T* 
 template <typename T>
 cudaError_t launch_armijo_penalty(int64_t p, const T* theta, const T* theta_t, const T* pen_w,
                                   double alpha0, double b, int j0, DevScalars* sc, RedScratch red,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, double l1, double l2) {
   armijo_penalty_kernel<T><<<red_blocks(p, 1), kThreads, 0, s>>>(p, theta, theta_t, pen_w, alpha0,
-                                                                 b, j0, sc, red);
+                                                                 b, j0, sc, red, l1, l2);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -926,18 +934,18 @@ cudaError_t launch_armijo_update(int64_t p, T* theta, const T* theta_t, const De
 
 template <typename T>
 cudaError_t launch_kkt(int64_t p, const double* g, const T* theta, const T* pen_w, double lambda,
-                       DevScalars* sc, RedScratch red, cudaStream_t s) {
-  kkt_kernel<T><<<red_blocks(p, 1), kThreads, 0, s>>>(p, g, theta, pen_w, lambda, sc, red);
+                       DevScalars* sc, RedScratch red, cudaStream_t s, double l1, double l2) {
+  kkt_kernel<T><<<red_blocks(p, 1), kThreads, 0, s>>>(p, g, theta, pen_w, lambda, sc, red, l1, l2);
   count_launches(1);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_penalty(int64_t p, const T* theta, const T* pen_w, DevScalars* sc,
-                           RedScratch red, cudaStream_t s) {
+                           RedScratch red, cudaStream_t s, double l1, double l2) {
   // J(theta) only: reuse the Armijo penalty kernel with theta~ = theta.
   armijo_penalty_kernel<T><<<red_blocks(p, 1), kThreads, 0, s>>>(p, theta, theta, pen_w, 1.0, 0.5,
-                                                                 0, sc, red);
+                                                                 0, sc, red, l1, l2);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -979,13 +987,13 @@ cudaError_t launch_gram(int nj, int pj, const double* XT, double* gram, cudaStre
   template cudaError_t launch_sum_splits<T>(int64_t, int, const T*, T*, cudaStream_t);            \
   template cudaError_t launch_armijo_penalty<T>(int64_t, const T*, const T*, const T*, double,    \
                                                 double, int, DevScalars*, RedScratch,             \
-                                                cudaStream_t);                                    \
+                                                cudaStream_t, double, double);                    \
   template cudaError_t launch_armijo_update<T>(int64_t, T*, const T*, const DevScalars*,          \
                                                cudaStream_t);                                     \
   template cudaError_t launch_kkt<T>(int64_t, const double*, const T*, const T*, double,          \
-                                     DevScalars*, RedScratch, cudaStream_t);                      \
+                                     DevScalars*, RedScratch, cudaStream_t, double, double);      \
   template cudaError_t launch_penalty<T>(int64_t, const T*, const T*, DevScalars*, RedScratch,    \
-                                         cudaStream_t);                                           \
+                                         cudaStream_t, double, double);                           \
   template cudaError_t launch_lambda_max<T>(int64_t, const double*, const T*, DevScalars*,        \
                                             RedScratch, cudaStream_t);
 

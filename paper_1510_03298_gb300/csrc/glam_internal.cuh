@@ -38,6 +38,7 @@ struct InnerCtl {
   double lambda;               // penalty parameter
   double stop_abs;             // stop when max_m |x+_m - y_m| <= stop_abs
   double crit;                 // last criterion value
+  double pen_l1, pen_l2;       // penalty J = sum_m w_m (pen_l1 |theta_m| + pen_l2 theta_m^2)
 };
 
 // Scalars produced by reductions and consumed by later kernels (all device-resident).
@@ -173,10 +174,11 @@ cudaError_t launch_armijo_stream(int family, int64_t n, const TE* eta, const T* 
                                  const TE* A, double alpha0, double b, int j0, DevScalars* sc,
                                  RedScratch red, cudaStream_t s);
 
+// penalty J = sum_m w_m (l1 |theta_m| + l2 theta_m^2) in the three kernels below
 template <typename T>
 cudaError_t launch_armijo_penalty(int64_t p, const T* theta, const T* theta_t, const T* pen_w,
                                   double alpha0, double b, int j0, DevScalars* sc, RedScratch red,
-                                  cudaStream_t s);
+                                  cudaStream_t s, double l1 = 1.0, double l2 = 0.0);
 
 cudaError_t launch_armijo_select(double lambda, double v, double alpha0, double b, int j0,
                                  DevScalars* sc, cudaStream_t s);
@@ -187,11 +189,12 @@ cudaError_t launch_armijo_update(int64_t p, T* theta, const T* theta_t, const De
 
 template <typename T>
 cudaError_t launch_kkt(int64_t p, const double* g, const T* theta, const T* pen_w, double lambda,
-                       DevScalars* sc, RedScratch red, cudaStream_t s);
+                       DevScalars* sc, RedScratch red, cudaStream_t s, double l1 = 1.0,
+                       double l2 = 0.0);
 
 template <typename T>
 cudaError_t launch_penalty(int64_t p, const T* theta, const T* pen_w, DevScalars* sc,
-                           RedScratch red, cudaStream_t s);
+                           RedScratch red, cudaStream_t s, double l1 = 1.0, double l2 = 0.0);
 
 template <typename T>
 cudaError_t launch_lambda_max(int64_t p, const double* g0, const T* pen_w, DevScalars* sc,

@@ -252,3 +252,48 @@ def test_scad_path_matches_oracle(prec, fam):
         np.testing.assert_allclose(th, thetas[k], atol=(1e-7 if prec == "fp64" else 1e-4) * scale)
         dk = O.GlamData(d.family, d.Xs, d.Y, d.a, weights[k])
         assert O.kkt_residual(dk, th, lams[k], lmax) <= (1e-7 if prec == "fp64" else 1e-4), k
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("fam", [gen.GAUSSIAN, gen.POISSON])
+@pytest.mark.parametrize("pen", ["enet", "ridge"])
+def test_enet_and_ridge_paths_match_oracle(prec, fam, pen):
+    """The elastic net J = sum w (|theta| + alpha theta^2) and the ridge penalty J = sum w theta^2
+    (Sec. 6.3 prox forms) against the oracle: the KKT conditions of every returned solution (the
+    distance of -grad f to lambda dJ, the definition of the solution), and for the Gaussian family
+    the oracle's own path (objectives and solutions; both problems are strictly convex).  (The
+    FP64 oracle's Armijo test compares objective values and, for Poisson ridge fits near
+    lambda_max, stops at KKT ~1e-8; there the KKT conditions alone decide.)"""
+    torch, g = gpu_or_skip()
+    n, p = (13, 11, 9), (5, 4, 4)
+    pr = gen.random_problem(91, n, p, fam, mask_frac=0.1, basis="normal", pen_w="rand")
+    l1, l2, code = (1.0, 0.6, g.GLAM_PENALTY_ENET) if pen == "enet" else (0.0, 1.0, g.GLAM_PENALTY_RIDGE)
+    d0 = O.GlamData.from_c(pr.family, pr.XT, pr.Y, pr.W, pr.pen_w)
+    d = O.GlamData(d0.family, d0.Xs, d0.Y, d0.a, d0.pen_w, l1, l2)
+    lmax = O.lambda_max(d)
+    lams = O.lambda_sequence(lmax, 4, 1e-2)
+    if fam == gen.GAUSSIAN:
+        _, thetas, stats, _ = O.fit_path(d, nlambda=4, ratio=1e-2, tol=1e-10)
+        assert all(st.converged for st in stats)
+    dt = dtype_of(prec)
+    plan = g.Plan(n, p, fam, plan_prec(g, prec))
+    tol = 1e-9 if prec == "fp64" else 1e-6
+    res = g.glam_fit_path(plan, [dev(x, dt) for x in pr.XT], dev(pr.Y, dt), dev(pr.W, dt),
+                          dev(pr.pen_w, torch.float64), nlambda=4,
+                          opts=g.glam_opts_default(tol=tol, lambda_min_ratio=1e-2, penalty=code,
+                                                   enet_alpha=l2 if pen == "enet" else 0.0))
+    assert res.status == g.GLAM_OK, res.message
+    np.testing.assert_allclose(res.lambdas, lams, rtol=1e-10 if prec == "fp64" else 1e-6)
+    path = host(res.path)
+    for k in range(4):
+        th = O.paper_array(path[k])
+        r = O.kkt_residual(d, th, lams[k], lmax)
+        assert r <= (1e-9 if prec == "fp64" else 3e-6), (k, r)
+        assert res.stats[k]["kkt"] <= tol
+        if fam == gen.GAUSSIAN:
+            F, Fref = O.objective(d, th, lams[k]), O.objective(d, thetas[k], lams[k])
+            assert abs(F - Fref) <= (1e-10 if prec == "fp64" else 1e-6) * abs(Fref), (k, F, Fref)
+            scale = max(1.0, float(np.abs(thetas[k]).max()))
+            np.testing.assert_allclose(th, thetas[k], atol=(1e-7 if prec == "fp64" else 1e-4) * scale)
+    if pen == "ridge":  # no coefficient is set to zero below lambda_max
+        assert np.count_nonzero(path[-1]) == path[-1].size
