@@ -148,7 +148,10 @@ typedef struct {
   double time_ms;
   int32_t outer_iters;     /* outer GD iterations (inner solves) */
   int32_t inner_iters;     /* inner PG iterations, total */
-  int32_t fp64_passes;     /* FP64 gradient / KKT passes (outer_iters + 1 when converged) */
+  int32_t fp64_passes;     /* FP64 gradient passes (H and G in FP64 at an outer iterate); the KKT
+                              test at the start of a lambda reuses the gradient of the previous
+                              lambda's solution, so a converged lambda after the first takes
+                              outer_iters of them, the first lambda outer_iters + 1 */
   int32_t armijo_backtracks;
   int32_t nnz;
   int32_t status;          /* GLAM_OK or GLAM_ENOCONV / GLAM_ENONFINITE for this lambda */

@@ -748,6 +748,10 @@ struct Fit {
   int64_t graph_kernels = 0;
   bool kron = false;  // inner loop on the tensor-product form H(<M_j>, .) (Sec. 6.2)
   double l1 = 1.0, l2 = 0.0;  // penalty J = sum_m w_m (l1 |theta_m| + l2 theta_m^2) (Sec. 6.3)
+  // eta, U, V, the loss and g_k in the plan describe the current theta: set by a full FP64 pass,
+  // cleared whenever theta moves (a new lambda starts where the last one stopped, so its first
+  // pass needs only the lambda-dependent KKT residual and objective)
+  bool grad_fresh = false;
   ~Fit() {
     if (graph) cudaGraphExecDestroy(graph);
   }
@@ -759,11 +763,13 @@ int fp64_pass(Fit<T>& f, double lambda, double& r, double& F, int& nnz, bool& no
   glam_plan* pl = f.pl;
   Ops<double> op(pl, f.s, f.X64);
   Work<T>& w = work_of<T>(pl);
-  CKS(op.H(pl->th, pl->wd.eta));
-  CK(launch_family<double, T>(pl->family, pl->n, pl->wd.eta, f.Y64, f.W64, w.V, nullptr, pl->wd.U,
-                              f.rho_prod, pl->sc, pl->red, f.s));
-  CKS(op.G(pl->wd.U, pl->gk));
-  CK(launch_scale<double>(pl->p, pl->gk, pl->gk, -1.0 / (double)pl->n, f.s));
+  if (!f.grad_fresh) {
+    CKS(op.H(pl->th, pl->wd.eta));
+    CK(launch_family<double, T>(pl->family, pl->n, pl->wd.eta, f.Y64, f.W64, w.V, nullptr, pl->wd.U,
+                                f.rho_prod, pl->sc, pl->red, f.s));
+    CKS(op.G(pl->wd.U, pl->gk));
+    CK(launch_scale<double>(pl->p, pl->gk, pl->gk, -1.0 / (double)pl->n, f.s));
+  }
   CK(launch_kkt<double>(pl->p, pl->gk, pl->th, pl->pen, lambda, pl->sc, pl->red, f.s, f.l1, f.l2));
   objective_kernel<<<1, 32, 0, f.s>>>(pl->sc, lambda);
   CK(cudaGetLastError());
@@ -774,6 +780,7 @@ int fp64_pass(Fit<T>& f, double lambda, double& r, double& F, int& nnz, bool& no
   F = pl->h_sc->F;
   nnz = pl->h_sc->nnz;
   nonfinite = pl->h_sc->nonfinite != 0 || !std::isfinite(F) || !std::isfinite(r);
+  f.grad_fresh = true;
   return GLAM_OK;
 }
 
@@ -911,8 +918,9 @@ int solve_lambda(Fit<T>& f, double lambda, LamOut& lo) {
     double r = 0.0, F = 0.0;
     int nnz = 0;
     bool nonfinite = false;
+    const bool full = !f.grad_fresh;
     CKS(fp64_pass<T>(f, lambda, r, F, nnz, nonfinite));
-    lo.passes += 1;
+    if (full) lo.passes += 1;
     lo.kkt = r;
     lo.F = F;
     lo.nnz = nnz;
@@ -949,6 +957,7 @@ int solve_lambda(Fit<T>& f, double lambda, LamOut& lo) {
     if (accepted < 0) return GLAM_OK;  // no descent left: report the current residual
     lo.backtracks += accepted;
     CK(launch_armijo_update<double>(pl->p, pl->th, xt, pl->sc, f.s));
+    f.grad_fresh = false;
   }
 }
 
