@@ -172,6 +172,19 @@ def run_reference(args):
 # our arm
 # ------------------------------------------------------------------------------------------
 
+def job_totals(dist, t_rank, iters, device):
+    """Whole-job figures of independent replicas: the slowest rank's time and the iterations of
+    every rank (dist None: this process alone)."""
+    if dist is None:
+        return t_rank, float(iters)
+    import torch
+    tt = torch.tensor([t_rank, float(iters)], dtype=torch.float64, device=device)
+    tmax = tt.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+    return tmax[0].item(), tt[1].item()
+
+
 def run_ours(args):
     import torch
 
@@ -231,15 +244,7 @@ def run_ours(args):
     iters = sum(sum(s["inner_iters"] for s in r.stats) for r in results)
     ok = all(r.status == g.GLAM_OK for r in results)
     kkt_max = max(max(s["kkt"] for s in r.stats) for r in results)
-    t_rank = ms / 1e3
-    if dist is not None:
-        tt = torch.tensor([t_rank, float(iters)], dtype=torch.float64, device=dev)
-        tmax = tt.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        t_job, iters_job = tmax[0].item(), tt[1].item()
-    else:
-        t_job, iters_job = t_rank, float(iters)
+    t_job, iters_job = job_totals(dist, ms / 1e3, iters, dev)
     value = iters_job / t_job
 
     extra = {}
