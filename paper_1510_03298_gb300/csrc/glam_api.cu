@@ -800,14 +800,20 @@ int capture_chunk(Fit<T>& f) {
       // X^T W X d = H(<M_j>, d) on p-sized arrays (Sec. 6.2, Eq. kronweight), then the prox step
       Work<T>& w = op.w;
       const int* skip = &pl->ctl->done;
-      cudaError_t e = launch_gemm<T, T>(k_mode3_fwd(pl), w.Mk[2], w.dn, w.kTa, f.s, nullptr, nullptr,
-                                        nullptr, 0.0, skip);
-      if (e == cudaSuccess)
-        e = launch_gemm<T, T>(k_mode1_fwd(pl), w.kTa, w.Mk[0], w.kTb, f.s, nullptr, nullptr, nullptr,
+      cudaError_t e = cudaSuccess;
+      if (kron_product_supported<T>((int)pl->p1, (int)pl->p2, (int)pl->p3)) {
+        e = launch_kron_product<T>((int)pl->p1, (int)pl->p2, (int)pl->p3, w.Mk[0], w.Mk[1], w.Mk[2],
+                                   w.dn, w.kQ, skip, f.s);
+      } else {
+        e = launch_gemm<T, T>(k_mode3_fwd(pl), w.Mk[2], w.dn, w.kTa, f.s, nullptr, nullptr, nullptr,
                               0.0, skip);
-      if (e == cudaSuccess)
-        e = launch_gemm<T, T>(k_mode2_fwd(pl), w.Mk[1], w.kTb, w.kQ, f.s, nullptr, nullptr, nullptr,
-                              0.0, skip);
+        if (e == cudaSuccess)
+          e = launch_gemm<T, T>(k_mode1_fwd(pl), w.kTa, w.Mk[0], w.kTb, f.s, nullptr, nullptr, nullptr,
+                                0.0, skip);
+        if (e == cudaSuccess)
+          e = launch_gemm<T, T>(k_mode2_fwd(pl), w.Mk[1], w.kTb, w.kQ, f.s, nullptr, nullptr, nullptr,
+                                0.0, skip);
+      }
       if (e == cudaSuccess)
         e = launch_prox<T, double>(pl->p, 1, w.kQ, pl->gk, 1.0, x, xp, pl->pen, xp, 1.0 / (double)pl->n,
                                    pl->ctl, 0.0, 0.0, 0.0, nullptr, f.s, w.dn, pl->th);
@@ -1001,6 +1007,8 @@ int kron_setup(Fit<T>& f, const T* W, double& rho_kron, double& wmax) {
     return fail(pl, GLAM_EINVAL, "iwls = GLAM_IWLS_KRON needs W = w1 (x) w2 (x) w3 with W(0,0,0) > 0");
   wmax = w_max;
   rho_kron = 1.0;
+  if (kron_product_supported<T>((int)pl->p1, (int)pl->p2, (int)pl->p3))
+    CK(kron_product_prepare<T>((int)pl->p1, (int)pl->p2, (int)pl->p3));
   int64_t off = 0;
   for (int j = 0; j < 3; ++j) {
     const double* Xd = (const double*)f.X64[j];

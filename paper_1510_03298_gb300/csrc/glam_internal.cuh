@@ -151,6 +151,16 @@ cudaError_t launch_kron_factors(int64_t n1, int64_t n2, int64_t n3, const T* W, 
                                 double* w3, unsigned long long* check, cudaStream_t s);
 cudaError_t launch_weighted_gram(int nj, int pj, const double* XT, const double* w, double* M,
                                  cudaStream_t s);
+// Q = H(<M_j>, d) on p-sized arrays in one launch (one CTA per slab j3, d staged in shared memory);
+// supported when d and the M_j fit in shared memory; kron_product_prepare sets the kernel's
+// shared-memory limit (call it outside any stream capture, before the first launch).
+template <typename T>
+int kron_product_supported(int p1, int p2, int p3);
+template <typename T>
+cudaError_t kron_product_prepare(int p1, int p2, int p3);
+template <typename T>
+cudaError_t launch_kron_product(int p1, int p2, int p3, const T* M1, const T* M2, const T* M3,
+                                const T* d, T* Q, const int* skip, cudaStream_t s);
 
 // ------------------------------------------------------------------------------------
 // Elementwise / reduction kernels.

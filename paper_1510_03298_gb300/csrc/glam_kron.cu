@@ -1,7 +1,8 @@
 // Tensor-product weights (Sec. 6.2, Eq. kronweight): when the weight array is a tensor product
 // W = w_1 (x) w_2 (x) w_3, X^T W X theta = H(<X_j^T W_j X_j>, theta), so the inner PG loop needs
 // only the p_j x p_j matrices M_j = X_j^T diag(w_j) X_j and p-sized arrays.  These kernels find
-// the factors of W (and check that W is one), and form the M_j in FP64.
+// the factors of W (and check that W is one), form the M_j in FP64, and apply H(<M_j>, d) to the
+// correction of every inner iteration in one launch.
 #include <algorithm>
 
 #include "glam_internal.cuh"
@@ -57,7 +58,106 @@ __global__ void weighted_gram_kernel(int nj, int pj, const double* __restrict__ 
   M[e] = s;
 }
 
+// Q = H(<M_j>, d) for p-sized arrays (d, Q: (p3, p2, p1) C-order; M_j symmetric p_j x p_j),
+// one CTA per output slab j3: the CTA copies all of d into shared memory by asynchronous copies
+// (every copy in flight at once: one memory round trip), forms A = sum_k3 M_3(j3, k3) d(k3),
+// then B = M_2 A and Q(j3) = B M_1^T.  skip: the inner loop's stop flag (the kernel returns when
+// it is set, as every kernel of a captured chunk does).
+template <typename T>
+__global__ void __launch_bounds__(256)
+kron_product_kernel(int p1, int p2, int p3, const T* __restrict__ M1, const T* __restrict__ M2,
+                    const T* __restrict__ M3, const T* __restrict__ d, T* __restrict__ Q,
+                    const int* __restrict__ skip) {
+  if (skip != nullptr && *skip) return;
+  extern __shared__ float4 kron_smem[];
+  const int P21 = p1 * p2, P = p3 * P21, tid = threadIdx.x, j3 = blockIdx.x;
+  T* ds = reinterpret_cast<T*>(kron_smem);  // [p3][P21]
+  T* As = ds + ((P + 3) / 4) * 4;            // [P21]
+  T* Bs = As + P21;                          // [P21]
+  T* m1 = Bs + P21;                          // [p1][p1]
+  T* m2 = m1 + p1 * p1;                      // [p2][p2]
+  T* m3 = m2 + p2 * p2;                      // [p3]  row j3 of M_3
+  constexpr int kVec = 16 / sizeof(T);
+  const bool vec = (P % kVec == 0) && ((reinterpret_cast<uintptr_t>(d) & 15) == 0);
+  if (vec) {
+    for (int i = tid; i < P / kVec; i += 256)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                       static_cast<uint32_t>(__cvta_generic_to_shared(ds + i * kVec))),
+                   "l"(d + i * kVec)
+                   : "memory");
+  } else {
+    for (int i = tid; i < P; i += 256)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(
+                       static_cast<uint32_t>(__cvta_generic_to_shared(ds + i))),
+                   "l"(d + i), "n"(sizeof(T))
+                   : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  for (int i = tid; i < p1 * p1; i += 256) m1[i] = M1[i];
+  for (int i = tid; i < p2 * p2; i += 256) m2[i] = M2[i];
+  for (int i = tid; i < p3; i += 256) m3[i] = M3[(int64_t)j3 * p3 + i];
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+  for (int m = tid; m < P21; m += 256) {
+    T a = T(0);
+    for (int k3 = 0; k3 < p3; ++k3) a = fma(m3[k3], ds[k3 * P21 + m], a);
+    As[m] = a;
+  }
+  __syncthreads();
+  for (int e = tid; e < P21; e += 256) {
+    const int j2 = e / p1, k1 = e - j2 * p1;
+    T b = T(0);
+    for (int k2 = 0; k2 < p2; ++k2) b = fma(m2[j2 * p2 + k2], As[k2 * p1 + k1], b);
+    Bs[e] = b;
+  }
+  __syncthreads();
+  for (int e = tid; e < P21; e += 256) {
+    const int j2 = e / p1, j1 = e - j2 * p1;
+    T q = T(0);
+    for (int k1 = 0; k1 < p1; ++k1) q = fma(Bs[j2 * p1 + k1], m1[j1 * p1 + k1], q);
+    Q[(int64_t)j3 * P21 + e] = q;
+  }
+}
+
+template <typename T>
+size_t kron_product_smem(int p1, int p2, int p3) {
+  const int64_t P21 = (int64_t)p1 * p2, P = P21 * p3;
+  return sizeof(T) * (size_t)((P + 3) / 4 * 4 + 2 * P21 + (int64_t)p1 * p1 + (int64_t)p2 * p2 + p3);
+}
+
 }  // namespace
+
+template <typename T>
+int kron_product_supported(int p1, int p2, int p3) {
+  return kron_product_smem<T>(p1, p2, p3) <= 200 * 1024 ? 1 : 0;
+}
+
+template <typename T>
+cudaError_t kron_product_prepare(int p1, int p2, int p3) {
+  if (!kron_product_supported<T>(p1, p2, p3)) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(kron_product_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kron_product_smem<T>(p1, p2, p3));
+}
+
+template <typename T>
+cudaError_t launch_kron_product(int p1, int p2, int p3, const T* M1, const T* M2, const T* M3,
+                                const T* d, T* Q, const int* skip, cudaStream_t s) {
+  if (!kron_product_supported<T>(p1, p2, p3)) return cudaErrorInvalidValue;
+  const size_t smem = kron_product_smem<T>(p1, p2, p3);
+  kron_product_kernel<T><<<p3, 256, smem, s>>>(p1, p2, p3, M1, M2, M3, d, Q, skip);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template int kron_product_supported<float>(int, int, int);
+template cudaError_t kron_product_prepare<float>(int, int, int);
+template cudaError_t kron_product_prepare<double>(int, int, int);
+template int kron_product_supported<double>(int, int, int);
+template cudaError_t launch_kron_product<float>(int, int, int, const float*, const float*, const float*,
+                                                const float*, float*, const int*, cudaStream_t);
+template cudaError_t launch_kron_product<double>(int, int, int, const double*, const double*,
+                                                 const double*, const double*, double*, const int*,
+                                                 cudaStream_t);
 
 template <typename T>
 cudaError_t launch_kron_factors(int64_t n1, int64_t n2, int64_t n3, const T* W, double* w1, double* w2,
