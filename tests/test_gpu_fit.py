@@ -1,7 +1,7 @@
 """Parity of the GPU lambda path (glam_fit_path) with the oracle.
 
 The target of every lambda is the minimiser of Eq. (five) (the lasso KKT conditions), which the
-oracle reaches by running Algorithm 1 in FP64 to KKT 1e-10.  Parity is judged on the solution's
+oracle reaches by running Algorithm 1 in FP64 to KKT 1e-10.  Parity is assessed on the solution's
 objective, its linear predictor, the KKT residual evaluated by the oracle, and the active set
 (exactly, except degenerate coordinates: zero in the oracle with |g_m| within 1e-6 lambda_max of
 the threshold, or |theta_m| <= 1e-9 max|theta|).  The iteration trajectory is not compared.
