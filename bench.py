@@ -138,9 +138,52 @@ def cpu_baseline(budget_s=12.0):
     per = max(t, 1e-3)
     k = int(max(2, min(200, budget_s / per)))
     n_it, t = _oracle_iters(O, d, lmax, w, z, Lhat, k)
-    return {"value": n_it / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{n_it} inner PG iterations (FP64 numpy, paper's mode order) of the "
-                      f"128x128x600 Gaussian model at lambda = 0.1 lambda_max; {t:.1f} s"}
+    out = {"value": n_it / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"{n_it} inner PG iterations (FP64 numpy, paper's mode order) of the "
+                     f"128x128x600 Gaussian model at lambda = 0.1 lambda_max; {t:.1f} s"}
+    out["single_core"] = _oracle_single_core(20)
+    out["paths"] = _oracle_paths()
+    return out
+
+
+def _oracle_single_core(iters):
+    """The same oracle iterations on one host core: a child process with every BLAS / OpenMP pool
+    limited to one thread (the pools are sized when numpy loads, so it cannot be done in-process)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1", VECLIB_MAXIMUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-rate", str(iters)],
+                       capture_output=True, text=True, env=env, timeout=600)
+    try:
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception:
+        return {"error": (r.stderr or r.stdout)[-300:]}
+    d.update({"cores": 1, "sample": f"{d['iters']} inner PG iterations of the same model, one thread"})
+    return d
+
+
+def _oracle_paths():
+    """Whole lambda paths of the oracle on the host cores: the 20x20x20 Gaussian workload (10
+    lambdas to KKT 1e-6, complete) and, as a bounded sample of the 96x96x365 Poisson workload, its
+    first lambda below lambda_max (one GD-PG solve to KKT 1e-6, at most 3 outer iterations)."""
+    import gen
+    import oracle as O
+    out = {}
+    pr = gen.make_workload(0)
+    d = O.GlamData.from_c(pr.family, pr.XT, pr.Y, pr.W, pr.pen_w)
+    t0 = time.perf_counter()
+    lams, thetas, stats, lmax = O.fit_path(d, nlambda=pr.nlambda, ratio=pr.lambda_min_ratio, tol=1e-6)
+    out["gauss_20x20x20_10_lambda_path_s"] = time.perf_counter() - t0
+    pr = gen.make_workload(2)
+    d = O.GlamData.from_c(pr.family, pr.XT, pr.Y, pr.W, pr.pen_w)
+    lmax = O.lambda_max(d)
+    lam = float(O.lambda_sequence(lmax, pr.nlambda, pr.lambda_min_ratio)[1])
+    t0 = time.perf_counter()
+    _, st = O.gdpg(d, lam, np.zeros(d.pshape), lmax, tol=1e-6, max_outer=3)
+    out["poisson_96x96x365_second_lambda_s"] = time.perf_counter() - t0
+    out["poisson_96x96x365_second_lambda_note"] = ("one GD-PG solve (at most 3 outer iterations) at "
+                                                  "the path's second lambda from zero; KKT %.2e" % st.kkt)
+    out["cores"] = os.cpu_count()
+    return out
 
 
 def run_reference(args):
@@ -252,6 +295,8 @@ def run_ours(args):
     if rank == 0:
         extra = measure_details(g, torch, pr, plan, X, Y, W, pen, opts, dev, flush, results[-1])
         extra["e2e"] = measure_e2e(g, torch, pr, plan, opts, dev, args.steps)
+        if not args.no_config3:
+            extra["poisson_96x96x365_paths"] = measure_config3(g, torch, flush)
         if args.batched > 0:
             extra["batched"] = measure_batched(g, torch, args.batched, args.batched_baseline)
         if world == 1 and not args.no_cpu:
@@ -260,12 +305,18 @@ def run_ours(args):
         dist.barrier()
     if rank == 0:
         st = results[-1].stats
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        # time per 50-lambda path to KKT 1e-6 leads (the inner-iteration rate rewards more iterations);
+        # the FP64 GPU path, the comparison point of the metric, sits beside it
+        fp64 = extra.get("fp64_gpu_path", {})
+        lead = {"s_per_path_to_kkt_1e-6": ms / args.steps / 1e3,
+                "fp64_gpu_s_per_path_to_kkt_1e-6": fp64.get("ms_per_path", float("nan")) / 1e3,
+                "speedup_vs_fp64_gpu_path": fp64.get("ms_per_path", float("nan")) / (ms / args.steps)}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "headline": lead, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "grid": [128, 128, 600], "basis": [20, 20, 60],
                            "nlambda": pr.nlambda,
-                           "precision": "fp32-accurate mode products (inner-loop product as 3xTF32 on tensor cores), fp64 refinement",
+                           "precision": "fp32-accurate mode products (inner-loop product as 3xTF32 on the tcgen05 tensor cores), fp64 refinement",
                            "l2": "256 MB buffer written between steps",
                            "parallelism": f"replicas x{world}"},
                 "gpu_launches": int(launches),
@@ -282,8 +333,9 @@ def run_ours(args):
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of each fused slab kernel on this
-# workload, from an ncu capture (cold cache) of the current kernels
-NCU_TRAFFIC_BYTES = {"3xtf32": 39665408 + 768, "tf32": 39651072 + 0}
+# workload, from an ncu capture (cold cache) of the current kernels (None: not captured since the
+# kernel last changed)
+NCU_TRAFFIC_BYTES = {"3xtf32": None, "tf32": None, "bf16": None}
 
 
 def measure_details(g, torch, pr, plan, X, Y, W, pen, opts, dev, flush, last):
@@ -337,7 +389,7 @@ def measure_details(g, torch, pr, plan, X, Y, W, pen, opts, dev, flush, last):
     by = 4 * n + 4 * n3 * p2 * p1 + 4 * (p + n3 * p3) + 4 * (n1 * p1 + n2 * p2)
     t_f = ms[0] / 1e3
     tf32_peak = peaks["bf16_tflops"] * 1.1 / 2.25  # dense TF32 = measured BF16 x nominal ratio
-    out["roofline"] = {"bound": "hbm", "kernel": "fused_slab_tc_kernel<3,2,3> (3xTF32 mma.sync, G(V(.)H) per slab)",
+    out["roofline"] = {"bound": "hbm", "kernel": "fused_slab_umma_kernel<3,float> (3xTF32 tcgen05, TMEM accumulators, G(V(.)H) per slab)",
                        "achieved": by / t_f / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                        "frac": by / t_f / 1e9 / peaks["hbm_gbs"], "traffic": NCU_TRAFFIC_BYTES["3xtf32"],
                        "bytes_per_launch": by, "ms_per_launch": ms[0], "peak_src": src,
@@ -349,25 +401,124 @@ def measure_details(g, torch, pr, plan, X, Y, W, pen, opts, dev, flush, last):
     # ms[2] is the mode-3 adjoint, fused with the prox step where the path does so (ms[3] = 0)
     out["inner_iteration_ms"] = {"fused_slab": ms[0], "mode3": ms[1], "mode3_adjoint": ms[2],
                                  "prox": ms[3], "sum": per_iter}
-    # the FP64 GPU path on a bounded sample of the same path (its first 4 lambdas)
-    plan64 = g.Plan(pr.n, pr.p, pr.family, g.GLAM_FP64)
-    X64 = [x.double() for x in X]
-    lams = last.lambdas[:4]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    r64 = g.glam_fit_path(plan64, X64, Y.double(), W.double(), pen, lambdas=lams, opts=opts)
-    t64 = time.perf_counter() - t0
-    it64 = sum(s["inner_iters"] for s in r64.stats)
-    it32 = sum(s["inner_iters"] for s in last.stats[:4])
-    t32 = sum(s["time_ms"] for s in last.stats[:4]) / 1e3
-    out["fp64_gpu_path"] = {"iters_per_s": it64 / t64, "sample": "first 4 lambdas of the path",
-                            "time_s": t64, "fp32_time_s_same_lambdas": t32,
-                            "path_speedup_fp32_over_fp64": t64 / max(t32, 1e-9),
-                            "status": r64.status, "max_kkt": max(s["kkt"] for s in r64.stats),
-                            "fp32_iters_same_lambdas": it32, "fp64_iters": it64}
-    plan64.close()
+    # the metric's comparison point: the whole 50-lambda path to KKT 1e-6 with a GLAM_FP64 plan
+    out["fp64_gpu_path"] = measure_path_precision(g, torch, pr, X, Y, W, pen, opts, flush, last, g.GLAM_FP64)
+    out["h_transform_fp64"] = measure_h(g, torch, pr, X, theta, flush, peaks, src, fp64=True)
     out["kron_path"] = measure_kron(g, torch, pr, X, Y, W, pen, opts, flush, last)
     out["tf32_path"] = measure_tf32(g, torch, pr, X, Y, W, pen, opts, flush, last, theta, by, peaks, src)
+    out["bf16_path"] = measure_path_precision(g, torch, pr, X, Y, W, pen, opts, flush, last, g.GLAM_BF16,
+                                              kernel_bytes=by - 2 * n, peaks=peaks, src=src, theta=theta)
+    return out
+
+
+def measure_h(g, torch, pr, X, theta, flush, peaks, src, fp64=False):
+    """H-transform (glam_predict) throughput of an FP64 plan: a stream of 8 calls writing 8 distinct
+    eta arrays (more than L2), L2 flushed first; algorithmic bytes 8 (n + p + sum n_j p_j)."""
+    n1, n2, n3 = pr.n
+    n = n1 * n2 * n3
+    p = int(np.prod(pr.p))
+    plan = g.Plan(pr.n, pr.p, pr.family, g.GLAM_FP64)
+    Xd = [x.double() for x in X]
+    th = theta.double()
+    K = 8
+    etas = [torch.empty((n3, n2, n1), dtype=torch.float64, device=th.device) for _ in range(K)]
+    times = []
+    for r in range(8):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda._sleep(400_000)
+        a.record()
+        for k in range(K):
+            g.glam_predict(plan, Xd, th, etas[k])
+        b.record()
+        torch.cuda.synchronize()
+        if r >= 2:
+            times.append(a.elapsed_time(b) / K)
+    t = statistics.median(times) / 1e3
+    by = 8 * (n + p + sum(a * b for a, b in zip(pr.n, pr.p)))
+    plan.close()
+    return {"GB/s": by / t / 1e9, "ms": t * 1e3, "bytes": by, "frac_hbm": by / t / 1e9 / peaks["hbm_gbs"],
+            "peak_src": src, "kernels": "FP64 SIMT mode products (gemm_kernel<double>)"}
+
+
+def measure_path_precision(g, torch, pr, X, Y, W, pen, opts, flush, last, precision, kernel_bytes=None,
+                           peaks=None, src=None, theta=None):
+    """The same 50-lambda path to KKT 1e-6 with another plan precision (GLAM_FP64: the metric's
+    comparison point; GLAM_BF16: BF16 inner products with the FP64 polish of every outer
+    iteration), timed like a bench step after one warm-up path, against the FP32 path."""
+    fp64 = precision == g.GLAM_FP64
+    plan = g.Plan(pr.n, pr.p, pr.family, precision)
+    cast = (lambda t: t.double()) if fp64 else (lambda t: t)
+    Xp, Yp, Wp = [cast(x) for x in X], cast(Y), cast(W)
+    g.glam_fit_path(plan, Xp, Yp, Wp, pen, lambdas=last.lambdas[:3], opts=opts)  # warm-up (graph capture)
+    flush.fill_(1.0)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    res = g.glam_fit_path(plan, Xp, Yp, Wp, pen, nlambda=pr.nlambda, opts=opts)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    iters = sum(s["inner_iters"] for s in res.stats)
+    ms32 = sum(s["time_ms"] for s in last.stats)
+    F32 = [s["objective"] for s in last.stats]
+    Fp = [s["objective"] for s in res.stats]
+    out = {"ms_per_path": ms, "iters_per_s": iters / (ms / 1e3), "inner_iters": iters,
+           "outer_iters": sum(s["outer_iters"] for s in res.stats),
+           "fp64_passes": sum(s["fp64_passes"] for s in res.stats),
+           "converged": res.status == g.GLAM_OK, "max_kkt": max(s["kkt"] for s in res.stats),
+           "fp32_ms_per_path": ms32, "max_rel_objective_diff_vs_fp32": max(abs(x - y) / abs(y) for x, y in zip(Fp, F32))}
+    if fp64:
+        out["path_speedup_fp32_over_fp64"] = ms / ms32
+    else:
+        out["speedup_vs_fp32_path"] = ms32 / ms
+    if kernel_bytes is not None and theta is not None:
+        q = g.glam_quad_build(plan, X, theta, Y, W)
+        k = g.glam_time_inner_kernels(plan, X, q, reps=100)
+        t_f = k[0] / 1e3
+        out["inner_iteration_ms"] = {"fused_slab": k[0], "mode3_adjoint": k[2], "prox": k[3], "sum": sum(k)}
+        out["roofline"] = {"bound": "hbm", "kernel": "fused_slab_umma_kernel<16,bf16> (tcgen05 kind::f16, V in BF16)",
+                           "achieved": kernel_bytes / t_f / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                           "frac": kernel_bytes / t_f / 1e9 / peaks["hbm_gbs"], "traffic": NCU_TRAFFIC_BYTES["bf16"],
+                           "bytes_per_launch": kernel_bytes, "ms_per_launch": k[0], "peak_src": src}
+    plan.close()
+    return out
+
+
+def measure_config3(g, torch, flush):
+    """The 96x96x365 Poisson workload (log-rate in [-2, 4], 10% of cells masked, p = (30, 30, 40)),
+    its 30-lambda path to KKT 1e-6 with each plan precision, timed after a warm-up path."""
+    import gen
+    pr = gen.make_workload(2)
+    f = lambda a, dt: torch.tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    pen = f(pr.pen_w, torch.float64)
+    opts = g.glam_opts_default(tol=1e-6, lambda_min_ratio=pr.lambda_min_ratio)
+    out = {"workload": "poisson-96x96x365 p=(30,30,40) 10% masked, 30-lambda path, ratio 1e-3, KKT 1e-6"}
+    ref = None
+    for name, prec in (("fp64", g.GLAM_FP64), ("fp32", g.GLAM_FP32), ("tf32", g.GLAM_TF32), ("bf16", g.GLAM_BF16)):
+        dt = torch.float64 if prec == g.GLAM_FP64 else torch.float32
+        X = [f(x, dt) for x in pr.XT]
+        Y, W = f(pr.Y, dt), f(pr.W, dt)
+        plan = g.Plan(pr.n, pr.p, pr.family, prec)
+        r = g.glam_fit_path(plan, X, Y, W, pen, nlambda=pr.nlambda, opts=opts)  # warm-up
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        r = g.glam_fit_path(plan, X, Y, W, pen, nlambda=pr.nlambda, opts=opts)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        Fs = [s["objective"] for s in r.stats]
+        if ref is None:
+            ref = Fs
+        out[name] = {"ms_per_path": ms, "inner_iters": sum(s["inner_iters"] for s in r.stats),
+                     "outer_iters": sum(s["outer_iters"] for s in r.stats),
+                     "converged": r.status == g.GLAM_OK, "max_kkt": max(s["kkt"] for s in r.stats),
+                     "max_rel_objective_diff_vs_fp64": max(abs(x - y) / abs(y) for x, y in zip(Fs, ref))}
+        plan.close()
+    for name in ("fp32", "tf32", "bf16"):
+        out[name]["speedup_vs_fp64_path"] = out["fp64"]["ms_per_path"] / out[name]["ms_per_path"]
     return out
 
 
@@ -402,7 +553,7 @@ def measure_tf32(g, torch, pr, X, Y, W, pen, opts, flush, last, theta, by, peaks
            "outer_iters": sum(s["outer_iters"] for s in res.stats),
            "inner_iteration_ms": {"fused_slab_tc": k[0], "mode3_adjoint": k[2], "prox": k[3],
                                   "sum": sum(k)},
-           "roofline": {"bound": "hbm", "kernel": "fused_slab_tc_kernel<3,4,1> (TF32 mma.sync)",
+           "roofline": {"bound": "hbm", "kernel": "fused_slab_umma_kernel<1,float> (TF32 tcgen05)",
                         "achieved": by / t_f / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                         "frac": by / t_f / 1e9 / peaks["hbm_gbs"], "traffic": NCU_TRAFFIC_BYTES["tf32"],
                         "bytes_per_launch": by, "ms_per_launch": k[0], "peak_src": src}}
@@ -556,6 +707,14 @@ def run_predict(reps):
     return 0
 
 
+def run_oracle_rate(iters):
+    """Helper of the single-core CPU baseline (run in a child process with one BLAS thread)."""
+    O, d, lmax, w, z, Lhat = _oracle_setup()
+    n_it, t = _oracle_iters(O, d, lmax, w, z, Lhat, iters)
+    print(json.dumps({"value": n_it / t, "unit": UNIT, "iters": n_it, "seconds": t}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -573,7 +732,11 @@ def main():
                     help="plan precision of the --kernels diagnostic")
     ap.add_argument("--predict", type=int, default=0, metavar="REPS",
                     help="diagnostic: run glam_predict REPS times for a profiler")
+    ap.add_argument("--oracle-rate", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--no-config3", action="store_true", help="skip the 96x96x365 Poisson paths")
     args = ap.parse_args()
+    if args.oracle_rate > 0:
+        return run_oracle_rate(args.oracle_rate)
     if args.predict > 0:
         return run_predict(args.predict)
     if args.kernels > 0:

@@ -130,6 +130,11 @@ typedef struct {
   int32_t reserved[3];
   double enet_alpha;       /* GLAM_PENALTY_ENET: J = sum_m w_m (|theta_m| + enet_alpha theta_m^2),
                               the elastic net of Sec. 6.3 (default 0, >= 0) */
+  double wait_limit_s;     /* limit, in seconds, of every bounded device-side wait of the inner
+                              loop's kernels (a copy or an MMA that should complete); a wait that
+                              runs out makes glam_fit_path return GLAM_ETIMEOUT, and the plan stays
+                              usable (default 2, in [0, 3600]; 0 gives up at once unless the awaited
+                              data is already there, which tests the error path) */
 } glam_opts;
 
 #define GLAM_IWLS_EXACT 0
@@ -161,13 +166,24 @@ typedef struct {
 int glam_opts_default(glam_opts* opts);
 
 /* Create a plan for one problem shape.  dims: HOST pointer (copied).  family: one of the four
- * GLAM_* families above.  precision: GLAM_FP64, GLAM_FP32 or GLAM_TF32 (GLAM_BF16 returns
- * GLAM_EINVAL).  A GLAM_TF32 plan is a GLAM_FP32 plan whose bottleneck product
- * G(V (.) H(y)) (Sec. 6.2, Eq. twentysixnew: the inner-loop product of glam_prox_step and
- * glam_fit_path) runs on the tensor cores with TF32 operands (10-bit mantissa, round to
- * nearest) and FP32 accumulation, for shapes with n1 % 32 == 0, n2 % 8 == 0, p1, p2 <= 32 and
- * 4 n1 n2 < 2^20 bytes; other shapes, and every other product (glam_predict, glam_gradient,
- * glam_loss, glam_quad_build, the FP64 passes of glam_fit_path), use the GLAM_FP32 kernels.
+ * GLAM_* families above.  precision: GLAM_FP64, GLAM_FP32, GLAM_TF32 or GLAM_BF16; it names the
+ * arithmetic of the bottleneck product G(V (.) H(y)) (Sec. 6.2, Eq. twentysixnew: the inner-loop
+ * product of glam_prox_step and glam_fit_path), which runs on the tensor cores for the
+ * single-precision plans:
+ *   GLAM_FP32  3xTF32: every operand split into two TF32 parts, three products each, FP32
+ *              accumulation (about FP32 accuracy);
+ *   GLAM_TF32  TF32 operands (10-bit mantissa, rounded to nearest), FP32 accumulation;
+ *   GLAM_BF16  BF16 operands (8-bit mantissa, rounded to nearest), FP32 accumulation; the fit
+ *              path also keeps the IRLS weights in BF16, halving the bytes the inner loop streams.
+ * The 5th-generation tensor-core kernel serves shapes with n1 <= 128, n1 % 4 == 0 (% 8 for
+ * BF16), n2 % 32 == 0, n2 <= 128 (GLAM_FP32) or 256, p1, p2 <= 32; outside that domain a
+ * warp-level tensor-core kernel serves shapes with n1 % 32 == 0, n2 % 8 == 0, n2 <= 256,
+ * p1, p2 <= 32 and 4 n1 n2 < 2^20 bytes (3xTF32 for GLAM_FP32, TF32 for GLAM_TF32 and GLAM_BF16
+ * plans), and FP32 SIMT kernels every other shape.  Every other product (glam_predict,
+ * glam_gradient, glam_loss, glam_quad_build, the FP64 passes of glam_fit_path) uses the FP32
+ * kernels in every single-precision plan: each outer iteration of glam_fit_path recomputes the
+ * gradient and the KKT residual in FP64, so the product precision changes iteration counts,
+ * not the accuracy of the accepted solutions.
  * stream: a cudaStream_t (NULL = legacy default stream) on the
  * current device.  *out receives the plan.  Allocates the workspace on the current device. */
 int glam_plan_create(const glam_dims* dims, int family, int precision, void* stream, glam_plan** out);
@@ -291,13 +307,17 @@ int glam_fit_path_batched(int nitems, glam_plan* const* plans, glam_batch_item* 
  * cudaFree or allocating library routine and needs no plan: its reduction scratch (1024 FP64
  * block partials and a completion counter, 8448 bytes) is a fixed __device__ array inside
  * libglam, which every GPU that loads the library holds until the process exits.
- *   family: GLAM_GAUSSIAN_IDENTITY or GLAM_POISSON_LOG; precision: GLAM_FP64 (double arrays)
- *   or GLAM_FP32 (float arrays); n: cells, 1 <= n <= 2^40 (larger n returns GLAM_EINVAL);
+ *   family: any of the four families; precision: GLAM_FP64 (double arrays) or GLAM_FP32 (float
+ *   arrays); n: cells, 1 <= n <= 2^40 (the cell limit of a plan; larger n returns GLAM_EINVAL);
  *   eta, Y, W: n elements (DEVICE); out: one DEVICE double (written); stream: cudaStream_t.
- * Asynchronous on `stream`; FP64 accumulation with a fixed summation order (same bits on every
- * call).  The first call on a device looks up the scratch address (cudaGetSymbolAddress), so
- * make that first call before any stream capture.  All calls share the one scratch array:
- * calls whose kernels overlap on the GPU race on it and must be serialized (one stream).
+ * Each cell's term is computed exactly as glam_loss computes it, including the clamp of eta
+ * before the exponential (at 80 in FP32, 700 in FP64), so that a large eta gives a finite term
+ * and a masked cell (a_i = 0) contributes zero; a NaN or infinite input gives a NaN result.
+ * Every term is added in FP64, with a fixed summation order (same bits on every call).
+ * Asynchronous on `stream`.  The first call on a device looks up the scratch address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.  All calls share
+ * the one scratch array: calls whose kernels overlap on the GPU race on it and must be
+ * serialized (one stream).
  * Errors: GLAM_EINVAL (message from glam_last_error(NULL)), GLAM_ECUDA. */
 int glam_loss_eta_noalloc(int family, int precision, int64_t n, const void* eta, const void* Y,
                           const void* W, double* out, void* stream);

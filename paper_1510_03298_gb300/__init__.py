@@ -82,7 +82,7 @@ class GlamOpts(C.Structure):
                 ("armijo_v", C.c_double), ("max_inner", C.c_int32), ("max_outer", C.c_int32),
                 ("max_linesearch", C.c_int32), ("check_every", C.c_int32), ("iwls", C.c_int32),
                 ("penalty", C.c_int32), ("steps", C.c_int32), ("reserved", C.c_int32 * 3),
-                ("enet_alpha", C.c_double)]
+                ("enet_alpha", C.c_double), ("wait_limit_s", C.c_double)]
 
 
 class GlamBatchItem(C.Structure):

@@ -3,6 +3,7 @@
 //
 // Mode order (the Kronecker algebra of App. A leaves it free): H contracts mode 3, then mode 1,
 // then mode 2; G runs the reverse.  Mode 2 is the fused mode of the bottleneck kernel.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -20,6 +21,7 @@ using namespace glam;
 namespace {
 
 thread_local std::string g_thread_err;
+constexpr uint64_t kDefaultWaitNs = 2000000000ull;  // bounded device waits: 2 s unless a fit says otherwise
 
 template <typename T>
 struct Work {
@@ -55,6 +57,11 @@ struct glam_plan {
   // plans: 3xTF32, about FP32 accuracy), 0 when the shape is outside its domain or the plan is FP64
   int tc_split = 0;
   float* tc_cst = nullptr;  // the tensor-core kernel's constant block (X_1, X_2 in its layouts)
+  // form of the tcgen05 kernel of the inner-loop product (1 TF32, 3 3xTF32, 16 BF16), 0 when the
+  // shape is outside its domain (the warp-level tensor-core kernel above, or SIMT, serves then)
+  int um_form = 0;
+  void* um_cst = nullptr;          // its constant block
+  __nv_bfloat16* Vb = nullptr;     // BF16 plans: the IRLS weights of the fit path in BF16 (n)
   std::string err;
   Work<float> wf;
   Work<double> wd;
@@ -231,6 +238,18 @@ struct Ops {
   int XtWX(const TB* x, const TB* xp, const TB* sub, const T* V, const InnerCtl* ctl,
            double omega, const int* skip) {
     if constexpr (sizeof(T) == 4 && sizeof(TB) == 4) {
+      if (pl->um_form && sub == nullptr && ctl == nullptr && fused_tc_pointers_ok((const float*)pl->um_cst, w.yx, V)) {
+        // tcgen05 kernel: it forms T_a = X_3 y from the extrapolated point itself
+        CK(launch_extrap<T>(pl->p, x, xp, omega, w.yx, s));
+        CK(launch_fused_umma_const((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2,
+                                   (int)pl->p3, pl->um_form, X[0], X[1], pl->um_cst, s));
+        CK(launch_fused_umma((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2, (int)pl->p3,
+                             pl->um_form, false, pl->um_cst, w.yx, X[0], X[2], V, w.Sb, s, skip,
+                             &pl->sc->timeout, kDefaultWaitNs));
+        CK(launch_gemm<T, T>(d_mode3_adj(pl, pl->ksplit), X[2], w.Sb, w.Qpart, s, nullptr, nullptr,
+                             nullptr, 0.0, skip));
+        return GLAM_OK;
+      }
       if (pl->tc_split && sub == nullptr && ctl == nullptr && fused_tc_pointers_ok(pl->tc_cst, w.yx, V)) {
         // tensor-core kernel: it forms T_a = X_3 y from the extrapolated point itself
         CK(launch_extrap<T>(pl->p, x, xp, omega, w.yx, s));
@@ -367,6 +386,7 @@ int glam_opts_default(glam_opts* o) {
   o->iwls = GLAM_IWLS_EXACT;
   o->penalty = GLAM_PENALTY_LASSO;
   o->steps = 1;
+  o->wait_limit_s = 2.0;
   return GLAM_OK;
 }
 
@@ -384,8 +404,8 @@ int glam_plan_create(const glam_dims* dims, int family, int precision, void* str
   if (family != GLAM_GAUSSIAN_IDENTITY && family != GLAM_POISSON_LOG && family != GLAM_BINOMIAL_LOGIT &&
       family != GLAM_GAMMA_LOG)
     return fail(nullptr, GLAM_EINVAL, "unknown family");
-  if (precision != GLAM_FP64 && precision != GLAM_FP32 && precision != GLAM_TF32)
-    return fail(nullptr, GLAM_EINVAL, "precision: only GLAM_FP64, GLAM_FP32 and GLAM_TF32 are available");
+  if (precision != GLAM_FP64 && precision != GLAM_FP32 && precision != GLAM_TF32 && precision != GLAM_BF16)
+    return fail(nullptr, GLAM_EINVAL, "precision: GLAM_FP64, GLAM_FP32, GLAM_TF32 or GLAM_BF16");
   const int64_t n = dims->n[0] * dims->n[1] * dims->n[2];
   const int64_t p = dims->p[0] * dims->p[1] * dims->p[2];
   if (n > (int64_t)1 << 40 || dims->n[2] * dims->p[1] > 65535LL * 64 || dims->n[2] > 65535)
@@ -429,10 +449,22 @@ int glam_plan_create(const glam_dims* dims, int family, int precision, void* str
       pl->err = std::string("tensor-core kernel set-up (cudaFuncSetAttribute): ") + cudaGetErrorString(e);
       return bail(GLAM_ECUDA);
     }
-    const int split = precision == GLAM_TF32 ? 1 : 3;
-    if (fused_tc_supported((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2, (int)pl->p3,
-                           split))
-      pl->tc_split = split;
+    const cudaError_t e2 = fused_umma_prepare();
+    if (e2 != cudaSuccess) {
+      pl->err = std::string("tcgen05 kernel set-up (cudaFuncSetAttribute): ") + cudaGetErrorString(e2);
+      return bail(GLAM_ECUDA);
+    }
+    // the tcgen05 kernel where the shape allows; otherwise the warp-level tensor-core kernel (TF32
+    // operands for TF32 and BF16 plans, 3xTF32 for FP32 plans) or the FP32 SIMT kernel
+    const int form = precision == GLAM_TF32 ? 1 : (precision == GLAM_BF16 ? 16 : 3);
+    if (fused_umma_supported((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2, (int)pl->p3, form)) {
+      pl->um_form = form;
+    } else {
+      const int split = precision == GLAM_FP32 ? 3 : 1;
+      if (fused_tc_supported((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2, (int)pl->p3,
+                             split))
+        pl->tc_split = split;
+    }
   }
   int st;
   if (precision == GLAM_FP64) {
@@ -457,6 +489,14 @@ int glam_plan_create(const glam_dims* dims, int family, int precision, void* str
     }
   }
 
+  if (pl->um_form) {
+    const int64_t nb = fused_umma_const_bytes((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2,
+                                              (int)pl->p3, pl->um_form);
+    unsigned char* c = nullptr;
+    if ((st = dalloc(pl, &c, (size_t)nb)) != GLAM_OK) return bail(st);
+    pl->um_cst = c;
+    if (pl->um_form == 16 && (st = dalloc(pl, &pl->Vb, (size_t)n)) != GLAM_OK) return bail(st);
+  }
   if ((st = dalloc(pl, &pl->ctl, 1)) != GLAM_OK) return bail(st);
   if ((st = dalloc(pl, &pl->sc, 1)) != GLAM_OK) return bail(st);
   if ((st = dalloc(pl, &pl->red.partial, (size_t)kMaxRedBlocks * kRedSlots)) != GLAM_OK) return bail(st);
@@ -752,6 +792,7 @@ struct Fit {
   // cleared whenever theta moves (a new lambda starts where the last one stopped, so its first
   // pass needs only the lambda-dependent KKT residual and objective)
   bool grad_fresh = false;
+  uint64_t wait_ns = kDefaultWaitNs;  // limit of every bounded device wait of the inner loop
   ~Fit() {
     if (graph) cudaGraphExecDestroy(graph);
   }
@@ -765,8 +806,12 @@ int fp64_pass(Fit<T>& f, double lambda, double& r, double& F, int& nnz, bool& no
   Work<T>& w = work_of<T>(pl);
   if (!f.grad_fresh) {
     CKS(op.H(pl->th, pl->wd.eta));
-    CK(launch_family<double, T>(pl->family, pl->n, pl->wd.eta, f.Y64, f.W64, w.V, nullptr, pl->wd.U,
-                                f.rho_prod, pl->sc, pl->red, f.s));
+    if (pl->Vb != nullptr)  // BF16 plans: the inner product streams the weights in BF16
+      CK(launch_family<double, __nv_bfloat16>(pl->family, pl->n, pl->wd.eta, f.Y64, f.W64, pl->Vb, nullptr,
+                                              pl->wd.U, f.rho_prod, pl->sc, pl->red, f.s));
+    else
+      CK(launch_family<double, T>(pl->family, pl->n, pl->wd.eta, f.Y64, f.W64, w.V, nullptr, pl->wd.U,
+                                  f.rho_prod, pl->sc, pl->red, f.s));
     CKS(op.G(pl->wd.U, pl->gk));
     CK(launch_scale<double>(pl->p, pl->gk, pl->gk, -1.0 / (double)pl->n, f.s));
   }
@@ -820,23 +865,29 @@ int capture_chunk(Fit<T>& f) {
       if (e != cudaSuccess) st = fail(pl, GLAM_ECUDA, std::string("inner iteration launch: ") + cudaGetErrorString(e));
       continue;
     }
-    bool use_tc = false, use_ap = false;
+    bool use_tc = false, use_ap = false, use_um = false;
+    const void* Vin = pl->Vb != nullptr ? (const void*)pl->Vb : (const void*)op.w.V;
     if constexpr (sizeof(T) == 4) {
-      use_tc = pl->tc_split && fused_tc_pointers_ok(pl->tc_cst, op.w.dn, op.w.V);
+      use_um = pl->um_form && fused_tc_pointers_ok((const float*)pl->um_cst, op.w.dn, (const float*)Vin);
+      use_tc = !use_um && pl->tc_split && fused_tc_pointers_ok(pl->tc_cst, op.w.dn, op.w.V);
       use_ap = adjprox_supported((int)pl->n3, (int)pl->p3, (int)(pl->p2 * pl->p1),
                                  (const float*)op.X[2], (const float*)op.w.Sb) != 0;
     }
-    const bool fused = pl->fused[sizeof(T) == 8 ? 1 : 0] || use_tc;
+    const bool fused = pl->fused[sizeof(T) == 8 ? 1 : 0] || use_tc || use_um;
     if (fused) {
       // the fused kernel forms T_a = X_3 d from the correction itself, then the adjoint
       cudaError_t e = cudaSuccess;
       if constexpr (sizeof(T) == 4) {
-        if (use_tc)
+        if (use_um)
+          e = launch_fused_umma((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2, (int)pl->p3,
+                                pl->um_form, pl->Vb != nullptr, pl->um_cst, op.w.dn, op.X[0], op.X[2], Vin,
+                                op.w.Sb, f.s, &pl->ctl->done, &pl->sc->timeout, f.wait_ns);
+        else if (use_tc)
           e = launch_fused_slab_tc((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2,
                                    (int)pl->p3, pl->tc_cst, op.w.dn, op.w.V, op.w.Sb, f.s,
                                    &pl->ctl->done, &pl->sc->timeout, op.X[2], pl->tc_split);
       }
-      if (!use_tc)
+      if (!use_tc && !use_um)
         e = launch_fused_slab<T>((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2,
                                  op.X[0], op.X[1], op.w.dn, op.w.V, op.w.Sb, f.s, &pl->ctl->done,
                                  &pl->sc->timeout, op.X[2], (int)pl->p3);
@@ -896,8 +947,10 @@ int run_inner(Fit<T>& f, double lambda, double stop_rel, int max_iter, double** 
     CK(cudaGraphLaunch(f.graph, f.s));
     count_launches(f.graph_kernels);
     CK(cudaMemcpyAsync(pl->h_ctl, pl->ctl, sizeof(InnerCtl), cudaMemcpyDeviceToHost, f.s));
+    CK(cudaMemcpyAsync(&pl->h_sc->timeout, &pl->sc->timeout, sizeof(int), cudaMemcpyDeviceToHost, f.s));
     CK(cudaStreamSynchronize(f.s));
     done = pl->h_ctl->done != 0;
+    if (pl->h_sc->timeout) return fail(pl, GLAM_ETIMEOUT, "a bounded device-side wait ran out");
   }
   if (!done) return fail(pl, GLAM_ETIMEOUT, "inner loop did not stop within its iteration cap");
   CK(cudaMemcpyAsync(pl->h_sc, pl->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, f.s));
@@ -1037,6 +1090,10 @@ int fit_impl(glam_plan* pl, const void* const X[3], const T* Y, const T* W, cons
   CK(cudaEventRecord(pl->ev_in, pl->stream));
   CK(cudaStreamWaitEvent(f.s, pl->ev_in, 0));
   for (int j = 0; j < 3; ++j) f.Xw[j] = X[j];
+  f.wait_ns = (uint64_t)(o.wait_limit_s * 1e9);
+  if (sizeof(T) == 4 && pl->um_form)  // the tcgen05 kernel's constant block, once per fit
+    CK(launch_fused_umma_const((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2, (int)pl->p3,
+                               pl->um_form, (const float*)X[0], (const float*)X[1], pl->um_cst, f.s));
   if (sizeof(T) == 4 && pl->tc_split)  // the tensor-core kernel's constant block, once per fit
     CK(launch_fused_tc_const((int)pl->n1, (int)pl->n2, (int)pl->p1, (int)pl->p2, (const float*)X[0],
                              (const float*)X[1], pl->tc_cst, pl->tc_split, f.s));
@@ -1200,7 +1257,8 @@ int glam_fit_path(glam_plan* pl, const void* const X[3], const void* Y, const vo
       !(o.armijo_v > 0 && o.armijo_v < 1) || !(o.armijo_alpha0 > 0) ||
       !(o.iwls == GLAM_IWLS_EXACT || o.iwls == GLAM_IWLS_KRON) ||
       !(o.penalty >= GLAM_PENALTY_LASSO && o.penalty <= GLAM_PENALTY_RIDGE) || o.steps < 1 ||
-      !(o.enet_alpha >= 0.0 && std::isfinite(o.enet_alpha)))
+      !(o.enet_alpha >= 0.0 && std::isfinite(o.enet_alpha)) ||
+      !(o.wait_limit_s >= 0.0 && o.wait_limit_s <= 3600.0))
     return fail(pl, GLAM_EINVAL, "glam_fit_path: bad options");
   if (lambda[0] >= 0)
     for (int k = 0; k < nlambda; ++k)
@@ -1225,6 +1283,9 @@ int time_inner_impl(glam_plan* pl, const void* const X[3], const glam_quad* q, i
   CK(cudaEventCreate(&b));
   const int slot = sizeof(T) == 8 ? 1 : 0;
   if constexpr (sizeof(T) == 4) {
+    if (pl->um_form)
+      CK(launch_fused_umma_const((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2, (int)pl->p3,
+                                 pl->um_form, op.X[0], op.X[1], pl->um_cst, pl->stream));
     if (pl->tc_split)
       CK(launch_fused_tc_const((int)pl->n1, (int)pl->n2, (int)pl->p1, (int)pl->p2, op.X[0], op.X[1],
                                pl->tc_cst, pl->tc_split, pl->stream));
@@ -1247,9 +1308,14 @@ int time_inner_impl(glam_plan* pl, const void* const X[3], const glam_quad* q, i
   }
   auto timed = [&](int which) -> int {
     ms[which] = 0.0;
-    bool use_tc = false;
-    if constexpr (sizeof(T) == 4) use_tc = pl->tc_split && fused_tc_pointers_ok(pl->tc_cst, op.w.dn, V);
-    const bool fused = pl->fused[slot] || use_tc;
+    bool use_tc = false, use_um = false;
+    // the weights as the fit reads them: BF16 plans stream their own BF16 copy
+    const void* Vin = pl->Vb != nullptr ? (const void*)pl->Vb : (const void*)V;
+    if constexpr (sizeof(T) == 4) {
+      use_um = pl->um_form && fused_tc_pointers_ok((const float*)pl->um_cst, op.w.dn, (const float*)Vin);
+      use_tc = !use_um && pl->tc_split && fused_tc_pointers_ok(pl->tc_cst, op.w.dn, V);
+    }
+    const bool fused = pl->fused[slot] || use_tc || use_um;
     if (which == 0 && !fused) return GLAM_OK;
     if (which == 3 && fused && use_ap) return GLAM_OK;  // part of ms[2]
     for (int r = -2; r < reps; ++r) {
@@ -1257,6 +1323,12 @@ int time_inner_impl(glam_plan* pl, const void* const X[3], const glam_quad* q, i
       switch (which) {
         case 0:
           if constexpr (sizeof(T) == 4) {
+            if (use_um) {
+              CK(launch_fused_umma((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2, (int)pl->p3,
+                                   pl->um_form, pl->Vb != nullptr, pl->um_cst, op.w.dn, op.X[0], op.X[2], Vin,
+                                   op.w.Sb, pl->stream, nullptr, &pl->sc->timeout, kDefaultWaitNs));
+              break;
+            }
             if (use_tc) {
               CK(launch_fused_slab_tc((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1,
                                       (int)pl->p2, (int)pl->p3, pl->tc_cst, op.w.dn, V,

@@ -13,9 +13,13 @@
 // Reductions: per-thread partials in the working precision over a few elements, FP64 across
 // threads and blocks, and a deterministic final sum in block order by the last block to finish
 // (no floating-point atomics, so every run gives the same bits).
+#include <cuda_bf16.h>
+
 #include <atomic>
 #include <cfloat>
+#include <type_traits>
 
+#include "glam_family.cuh"
 #include "glam_internal.cuh"
 
 namespace glam {
@@ -83,103 +87,6 @@ __device__ bool last_block(unsigned int* counter) {
   return is_last;
 }
 
-template <typename T>
-__device__ __forceinline__ T poisson_clamp();
-template <>
-__device__ __forceinline__ float poisson_clamp<float>() {
-  return 80.0f;  // exp(80) ~ 5.5e34 < FLT_MAX
-}
-template <>
-__device__ __forceinline__ double poisson_clamp<double>() {
-  return 700.0;
-}
-
-template <typename T>
-__device__ __forceinline__ T t_exp(T x);
-template <>
-__device__ __forceinline__ float t_exp<float>(float x) {
-  return expf(x);
-}
-template <>
-__device__ __forceinline__ double t_exp<double>(double x) {
-  return exp(x);
-}
-template <typename T>
-__device__ __forceinline__ T t_expm1(T x);
-template <>
-__device__ __forceinline__ float t_expm1<float>(float x) {
-  return expm1f(x);
-}
-template <>
-__device__ __forceinline__ double t_expm1<double>(double x) {
-  return expm1(x);
-}
-
-template <typename T>
-__device__ __forceinline__ T t_log1p(T x);
-template <>
-__device__ __forceinline__ float t_log1p<float>(float x) {
-  return log1pf(x);
-}
-template <>
-__device__ __forceinline__ double t_log1p<double>(double x) {
-  return log1p(x);
-}
-
-// The per-cell quantities of App. B at eta = e for response y and observation weight a:
-//   u  the score a theta'(e) (y - g^-1(e))                       (Eq. four)
-//   w  the IRLS weight a theta'(e) (g^-1)'(e)                     (Eq. weights, times a)
-//   l  the cell's term of n f, f = -(1/n) l(eta) + constants      (Eq. two)
-//   dy the derivative of l in y
-// Gaussian/identity, Poisson/log, binomial/logit (y a proportion of a trials) and Gamma/log
-// (dispersion 1; the link is not canonical: theta(e) = -exp(-e)).  bad is set where e had to be
-// clamped to keep the mean finite.
-template <typename T>
-struct CellTerms {
-  T u, w, l, dy;
-};
-template <typename T>
-__device__ __forceinline__ CellTerms<T> family_cell(int family, T e, T y, T a, int& bad) {
-  CellTerms<T> c;
-  if (family == GLAM_GAUSSIAN_IDENTITY) {
-    const T r = y - e;              // identity link: mu = eta
-    c.u = a * r;
-    c.w = a;                        // theta' = (g^-1)' = 1
-    c.l = T(0.5) * a * r * r;
-    c.dy = a * r;
-  } else if (family == GLAM_POISSON_LOG) {
-    T ec = e;
-    if (ec > poisson_clamp<T>()) {
-      ec = poisson_clamp<T>();
-      bad = 1;
-    }
-    const T mu = t_exp<T>(ec);      // log link: mu = exp(eta)
-    c.u = a * (y - mu);
-    c.w = a * mu;                   // (g^-1)' = exp(eta)
-    c.l = a * (mu - y * e);
-    c.dy = -a * e;
-  } else if (family == GLAM_BINOMIAL_LOGIT) {
-    const T ex = t_exp<T>(-fabs(e));  // in (0, 1]: no overflow on either side
-    const T mu = e >= T(0) ? T(1) / (T(1) + ex) : ex / (T(1) + ex);
-    c.u = a * (y - mu);
-    c.w = a * mu * (T(1) - mu);     // (g^-1)' = mu (1 - mu)
-    c.l = a * (fmax(e, T(0)) + t_log1p<T>(ex) - y * e);  // log(1 + e^eta) - y eta
-    c.dy = -a * e;
-  } else {                          // GLAM_GAMMA_LOG
-    T ec = e;
-    if (ec < -poisson_clamp<T>()) {
-      ec = -poisson_clamp<T>();
-      bad = 1;
-    }
-    const T ie = t_exp<T>(-ec);     // 1 / mu
-    c.u = a * (y * ie - T(1));      // theta'(eta) = exp(-eta)
-    c.w = a;                        // theta' (g^-1)' = exp(-eta) exp(eta)
-    c.l = a * (y * ie + e);
-    c.dy = a * ie;
-  }
-  return c;
-}
-
 int red_blocks(int64_t n, int per_thread) {
   const int64_t per_block = (int64_t)kThreads * per_thread;
   int64_t b = (n + per_block - 1) / per_block;
@@ -191,6 +98,17 @@ int red_blocks(int64_t n, int per_thread) {
 }
 
 // ---------------------------------------------------------------- family pass
+// The stored IRLS weight in the type the inner-loop product reads (BF16 rounds to nearest).
+template <typename TV, typename T>
+__device__ __forceinline__ TV to_weight(T w) {
+  if constexpr (std::is_same<TV, __nv_bfloat16>::value) {
+    if constexpr (sizeof(T) == 8) return __double2bfloat16(w);
+    else return __float2bfloat16_rn(w);
+  } else {
+    return TV(w);
+  }
+}
+
 template <typename T, typename TV>
 __global__ void __launch_bounds__(kThreads)
 family_kernel(int family, int64_t n, const T* __restrict__ eta, const T* __restrict__ Y,
@@ -209,7 +127,7 @@ family_kernel(int family, int64_t n, const T* __restrict__ eta, const T* __restr
       const CellTerms<T> c = family_cell<T>(family, e, y, a, bad);
       const T u = c.u, w = c.w, l = c.l;
       if (!(isfinite(e) && isfinite(y) && isfinite(a))) bad = 1;
-      if (V != nullptr) V[i] = TV(w);
+      if (V != nullptr) V[i] = to_weight<TV>(w);
       if (VZ != nullptr) VZ[i] = u + w * e;  // V (.) Z with Z = W^-1 u + eta (Eq. ten)
       if (U != nullptr) U[i] = u;
       lpart += l;
@@ -1010,6 +928,9 @@ template cudaError_t launch_family<double, double>(int, int64_t, const double*, 
 template cudaError_t launch_family<double, float>(int, int64_t, const double*, const double*,
                                                   const double*, float*, double*, double*, double,
                                                   DevScalars*, RedScratch, cudaStream_t);
+template cudaError_t launch_family<double, __nv_bfloat16>(int, int64_t, const double*, const double*,
+                                                          const double*, __nv_bfloat16*, double*, double*,
+                                                          double, DevScalars*, RedScratch, cudaStream_t);
 #define GLAM_PROX_INST(Tq, TP)                                                                  \
   template cudaError_t launch_prox<Tq, TP>(int64_t, int, const Tq*, const TP*, double, const TP*,  \
                                            const TP*, const TP*, TP*, double, InnerCtl*, double,  \

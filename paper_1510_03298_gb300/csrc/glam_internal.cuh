@@ -115,6 +115,24 @@ int fused_tc_supported(int n1, int n2, int n3, int p1, int p2, int p3, int split
 int fused_tc_pointers_ok(const float* Cst, const float* D, const float* V);
 cudaError_t fused_tc_prepare();
 
+// The same product on the 5th-generation tensor cores (tcgen05, accumulators in tensor memory):
+// form 1 TF32, 3 3xTF32 (about FP32 accuracy), 16 BF16 operands, FP32 accumulation throughout.  T_a
+// = X_3 D is formed in the kernel from the correction D (p3 x p2p1, FP32).  Cst is the constant
+// block (fused_umma_const_bytes bytes, written by launch_fused_umma_const from X_1^T and X_2^T
+// once per set of designs); V is FP32, or BF16 for form 16 with v_bf16.  Every wait of the
+// kernel gives up after wait_ns nanoseconds and sets *err.  fused_umma_supported tells whether
+// the shape is in the kernel's domain (n1 <= 128, n1 a multiple of 4 (8 for BF16), n2 a multiple
+// of 32 up to 128 (3xTF32) or 256, p1, p2 <= 32).
+cudaError_t fused_umma_prepare();
+int fused_umma_supported(int n1, int n2, int n3, int p1, int p2, int p3, int form);
+int64_t fused_umma_const_bytes(int n1, int n2, int n3, int p1, int p2, int p3, int form);
+cudaError_t launch_fused_umma_const(int n1, int n2, int n3, int p1, int p2, int p3, int form,
+                                    const float* X1T, const float* X2T, void* Cst, cudaStream_t st);
+cudaError_t launch_fused_umma(int n1, int n2, int n3, int p1, int p2, int p3, int form, bool v_bf16,
+                              const void* Cst, const float* D, const float* X1T, const float* X3T,
+                              const void* V, float* Sb, cudaStream_t st, const int* skip, int* err,
+                              uint64_t wait_ns);
+
 // The last two stages of H for FP32 (modes 1 and 2, Sec. 6.1, Eq. eighteen) in one kernel:
 // eta[i3] = X_2 (T_a[i3] X_1^T) per slab, T_a (n3 x p2p1) from the mode-3 product.
 int predict_tiles_supported(int p1, int p2);

@@ -21,6 +21,7 @@
 #include <mutex>
 #include <string>
 
+#include "glam_family.cuh"
 #include "glam_internal.cuh"
 
 namespace {
@@ -28,6 +29,8 @@ namespace {
 constexpr int kNoAllocThreads = 256;
 constexpr int kNoAllocPerThread = 8;           // elements per thread per tile
 constexpr int kNoAllocBlocks = 1024;           // maximum reduction grid (one partial per block)
+// Largest accepted n: the cell limit of glam_plan_create, chosen for the interface.  The scratch
+// does not depend on n (the grid is capped at kNoAllocBlocks blocks that stride over the cells).
 constexpr int64_t kNoAllocMaxCells = (int64_t)1 << 40;
 constexpr size_t kCounterOffset = (size_t)kNoAllocBlocks * sizeof(double);
 constexpr size_t kScratchBytes = kCounterOffset + 256;
@@ -55,20 +58,11 @@ cudaError_t scratch_address(void** out) {
   return cudaSuccess;
 }
 
-template <typename T>
-__device__ __forceinline__ T noalloc_exp(T x);
-template <>
-__device__ __forceinline__ float noalloc_exp<float>(float x) {
-  return expf(x);
-}
-template <>
-__device__ __forceinline__ double noalloc_exp<double>(double x) {
-  return exp(x);
-}
-
-// f(eta) = (1/n) sum_i a_i l_i (Sec. 2, Eq. two with the constants of glam.h): per-thread
-// partials over kNoAllocPerThread elements in T, FP64 across threads and blocks, final sum in
-// block order by the last block (the same bits on every run).
+// f(eta) = (1/n) sum_i a_i l_i (Sec. 2, Eq. two with the constants of glam.h), each cell's term
+// from the same per-cell code as glam_loss (family_cell: App. B, with its clamp of eta before the
+// exponential, so that a large eta gives the same finite term there and here, and a masked cell
+// contributes exactly zero); every term is added to an FP64 accumulator, FP64 across threads and
+// blocks, final sum in block order by the last block (the same bits on every run).
 template <typename T>
 __global__ void __launch_bounds__(kNoAllocThreads)
 loss_noalloc_kernel(int family, int64_t n, const T* __restrict__ eta, const T* __restrict__ Y,
@@ -80,20 +74,13 @@ loss_noalloc_kernel(int family, int64_t n, const T* __restrict__ eta, const T* _
   double acc = 0.0;
   const int64_t tile = (int64_t)gridDim.x * blockDim.x * kNoAllocPerThread;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kNoAllocPerThread; base < n; base += tile) {
-    T part = T(0);
 #pragma unroll
     for (int k = 0; k < kNoAllocPerThread; ++k) {
       const int64_t i = base + (int64_t)k * blockDim.x + threadIdx.x;
       if (i >= n) break;
-      const T e = eta[i], y = Y[i], a = A[i];
-      if (family == GLAM_GAUSSIAN_IDENTITY) {
-        const T r = y - e;
-        part += T(0.5) * a * r * r;
-      } else {
-        part += a * (noalloc_exp<T>(e) - y * e);
-      }
+      int clamped = 0;
+      acc += (double)glam::family_cell<T>(family, eta[i], Y[i], A[i], clamped).l;
     }
-    acc += (double)part;
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) warp_part[threadIdx.x >> 5] = acc;
@@ -118,14 +105,15 @@ loss_noalloc_kernel(int family, int64_t n, const T* __restrict__ eta, const T* _
 
 int glam_loss_eta_noalloc(int family, int precision, int64_t n, const void* eta, const void* Y,
                           const void* W, double* out, void* stream) {
-  if (family != GLAM_GAUSSIAN_IDENTITY && family != GLAM_POISSON_LOG)
+  if (family != GLAM_GAUSSIAN_IDENTITY && family != GLAM_POISSON_LOG && family != GLAM_BINOMIAL_LOGIT &&
+      family != GLAM_GAMMA_LOG)
     return glam::thread_fail(GLAM_EINVAL, "glam_loss_eta_noalloc: unknown family");
   if (precision != GLAM_FP64 && precision != GLAM_FP32)
     return glam::thread_fail(GLAM_EINVAL, "glam_loss_eta_noalloc: precision must be GLAM_FP64 or GLAM_FP32");
   if (n < 1 || n > kNoAllocMaxCells)
     return glam::thread_fail(GLAM_EINVAL,
-                             "glam_loss_eta_noalloc: n must be in [1, 2^40] (the fixed scratch is "
-                             "sized for that many cells)");
+                             "glam_loss_eta_noalloc: n must be in [1, 2^40] (a limit of the interface, "
+                             "the same as a plan's; the scratch does not depend on n)");
   if (!eta || !Y || !W || !out) return glam::thread_fail(GLAM_EINVAL, "glam_loss_eta_noalloc: NULL array");
   void* scratch = nullptr;
   cudaError_t e = scratch_address(&scratch);

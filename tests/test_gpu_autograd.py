@@ -17,7 +17,7 @@ import pytest
 
 import gen
 import oracle as O
-from gpu_helpers import dev, gpu_or_skip, host, rel_err
+from gpu_helpers import BAR, assert_within, cell_scales, chain_G, chain_H, dev, gpu_or_skip, host
 
 pytestmark = pytest.mark.gpu
 
@@ -60,11 +60,14 @@ class _Setup:
         return O.objective(d, O.paper_array(theta_c), self.lam)
 
     def grads(self, theta_c):
+        """The oracle's dF/dTheta and dF/dY and their absolute-value chains (the bounds of
+        gpu_helpers: |G|(su)/n + lambda w for Theta, the magnitude of df/dy for Y)."""
         th = O.paper_array(theta_c)
         gT = O.c_array(O.penalized_gradient(self.data, th, self.lam))
         eta = O.H(self.data.Xs, th)
         gY = O.c_array(O.loss_grad_y(self.fam, eta, self.data.Y, self.data.a))
-        return gT, gY
+        cT, cY = _vjp_chains(self.data, th, eta, self.lam)
+        return gT, gY, cT, cY
 
     def coord_fd(self, theta_c, eta_c, m):
         """Central difference of F along coordinate m = (m3, m2, m1), evaluated on the cells the
@@ -82,6 +85,22 @@ class _Setup:
         return (df + dp) / (2 * H_FD)
 
 
+def _vjp_chains(data, th, eta, lam):
+    """Element-wise scales of dF/dTheta and dF/dY (C layout): the chain of the gradient of f,
+    |G|(su)/n, plus lambda w for the penalty term; |df/dy| evaluated on the chain of eta."""
+    ea = chain_H(data.Xs, th)
+    su, _, _ = cell_scales(data.family, eta, ea, data.Y, data.a)
+    cT = chain_G(data.Xs, su) / data.n + lam * np.abs(data.pen_w)
+    aa = np.abs(data.a)
+    if data.family == O.GAUSSIAN:
+        cY = aa * (np.abs(data.Y) + ea)
+    elif data.family == O.GAMMA:
+        cY = aa * np.exp(-eta) * (1.0 + ea)
+    else:
+        cY = aa * ea
+    return O.c_array(cT), O.c_array(cY / data.n)
+
+
 @pytest.fixture(scope="module")
 def setup():
     torch, g = gpu_or_skip()
@@ -97,10 +116,11 @@ def test_autograd_matches_oracle_and_finite_differences(setup):
         theta = _f32(rng.normal(0.0, 0.1, (s.p[2], s.p[1], s.p[0])))
         F, gT, gY = s.gpu(theta)
         F_o = s.F(theta)
-        gT_o, gY_o = s.grads(theta)
+        gT_o, gY_o, cT, cY = s.grads(theta)
         worst["F"] = max(worst["F"], abs(F - F_o) / abs(F_o))
-        worst["gT"] = max(worst["gT"], rel_err(gT, gT_o))
-        worst["gY"] = max(worst["gY"], rel_err(gY, gY_o))
+        # element-wise, relative to each entry's chain: the ratio must stay <= TOL32
+        worst["gT"] = max(worst["gT"], TOL32 * assert_within(gT, gT_o, cT, TOL32, what="dF/dTheta"))
+        worst["gY"] = max(worst["gY"], TOL32 * assert_within(gY, gY_o, cY, TOL32, what="dF/dY"))
         smooth = np.abs(theta) >= 2 * H_FD
         # random directions in Theta (zero on the coordinates near a kink)
         eta_c = O.predict_c(s.XT, theta)
@@ -196,9 +216,12 @@ def test_penalized_nll_ragged_against_oracle(prec, fam):
     thp = O.paper_array(th)
     tol = 1e-11 if prec == "fp64" else TOL32
     assert abs(F.item() - O.objective(data, thp, lam)) <= tol * abs(O.objective(data, thp, lam))
-    assert rel_err(host(gT), 2.5 * O.c_array(O.penalized_gradient(data, thp, lam))) <= tol
     eta = O.H(data.Xs, thp)
-    assert rel_err(host(gY), 2.5 * O.c_array(O.loss_grad_y(fam, eta, data.Y, data.a))) <= tol
+    cT, cY = _vjp_chains(data, thp, eta, lam)
+    assert_within(host(gT), 2.5 * O.c_array(O.penalized_gradient(data, thp, lam)), 2.5 * cT, BAR[prec],
+                  what="dF/dTheta")
+    assert_within(host(gY), 2.5 * O.c_array(O.loss_grad_y(fam, eta, data.Y, data.a)), 2.5 * cY, BAR[prec],
+                  what="dF/dY")
 
 
 def test_penalized_nll_rejects_bad_calls():

@@ -6,7 +6,8 @@ import pytest
 
 import gen
 import oracle as O
-from gpu_helpers import TOL, dev, dtype_of, gpu_or_skip, host, plan_prec, rel_err
+from gpu_helpers import (BAR, assert_within, cell_scales, chain_G, chain_H, dev, dtype_of, gpu_or_skip,
+                         host, plan_prec)
 
 pytestmark = pytest.mark.gpu
 
@@ -28,8 +29,11 @@ def test_edge_shapes_predict_gradient_loss(prec, fam, n, p):
     torch.cuda.synchronize()
     d = O.GlamData.from_c(pr.family, pr.XT, pr.Y, pr.W, pr.pen_w)
     th = O.paper_array(theta)
-    assert rel_err(host(eta), O.predict_c(pr.XT, theta)) <= TOL[prec]
-    assert rel_err(host(grad), O.c_array(O.gradient(d, th))) <= 10 * TOL[prec]
+    eta_abs = chain_H(d.Xs, th)
+    assert_within(host(eta), O.predict_c(pr.XT, theta), O.c_array(eta_abs), BAR[prec], what="eta")
+    su, _, _ = cell_scales(fam, O.H(d.Xs, th), eta_abs, d.Y, d.a)
+    assert_within(host(grad), O.c_array(O.gradient(d, th)), O.c_array(chain_G(d.Xs, su)) / d.n, BAR[prec],
+                  what="grad")
     fref = O.loss(fam, O.H(d.Xs, th), d.Y, d.a)
     assert abs(loss.item() - fref) <= (1e-12 if prec == "fp64" else 1e-6) * max(1.0, abs(fref))
 

@@ -13,7 +13,8 @@ import pytest
 
 import gen
 import oracle as O
-from gpu_helpers import dev, dtype_of, gpu_or_skip, host, plan_prec, rel_err
+from gpu_helpers import (BAR, assert_within, cell_scales, chain_G, chain_H, dev, dtype_of, f32_rounded,
+                         gpu_or_skip, host, plan_prec, rel_err)
 
 pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -297,3 +298,171 @@ def test_enet_and_ridge_paths_match_oracle(prec, fam, pen):
             np.testing.assert_allclose(th, thetas[k], atol=(1e-7 if prec == "fp64" else 1e-4) * scale)
     if pen == "ridge":  # no coefficient is set to zero below lambda_max
         assert np.count_nonzero(path[-1]) == path[-1].size
+
+
+# ------------------------------------------------------------------------------------------
+# FP32 plans on the shapes whose inner-loop product runs on the tensor cores (n1 <= 128 or a
+# multiple of 32, n2 a multiple of 16, p1, p2 <= 32): the configuration the benchmark times.
+# ------------------------------------------------------------------------------------------
+
+def _cast32(pr):
+    """The problem as an FP32 plan sees it: designs and data rounded to binary32 (the oracle then
+    measures the solver, not the rounding of its inputs)."""
+    pr.XT = [f32_rounded(x) for x in pr.XT]
+    pr.Y, pr.W = f32_rounded(pr.Y), f32_rounded(pr.W)
+    return pr
+
+
+@pytest.mark.parametrize("fam", [gen.GAUSSIAN, gen.POISSON])
+@pytest.mark.parametrize("n,p", [((64, 32, 7), (9, 17, 4)), ((64, 24, 7), (9, 17, 4)), ((96, 48, 5), (30, 25, 3))])
+def test_fp32_tensor_core_shape_path_matches_oracle(n, p, fam):
+    """Masked lambda paths with GLAM_FP32 plans on tensor-core shapes: every returned solution
+    against the oracle's path (objective, solution, active set) and the oracle's KKT residual."""
+    torch, g = gpu_or_skip()
+    pr = _cast32(gen.random_problem(61, n, p, fam, mask_frac=0.15, basis="normal", pen_w="rand"))
+    d = O.GlamData.from_c(pr.family, pr.XT, pr.Y, pr.W, pr.pen_w)
+    lams, thetas, stats, lmax = O.fit_path(d, nlambda=6, ratio=1e-2, tol=1e-10)
+    dt = torch.float32
+    plan = g.Plan(n, p, fam, g.GLAM_FP32)
+    res = g.glam_fit_path(plan, [dev(x, dt) for x in pr.XT], dev(pr.Y, dt), dev(pr.W, dt),
+                          dev(pr.pen_w, torch.float64), lambdas=list(lams), opts=g.glam_opts_default(tol=1e-6))
+    assert res.status == g.GLAM_OK, res.message
+    path = host(res.path)
+    for k in range(len(lams)):
+        th = O.paper_array(path[k])
+        r = O.kkt_residual(d, th, lams[k], lmax)
+        assert r <= 1.001e-6, (k, r)
+        F, Fref = O.objective(d, th, lams[k]), O.objective(d, thetas[k], lams[k])
+        assert abs(F - Fref) <= 1e-6 * abs(Fref), (k, F, Fref)
+        np.testing.assert_allclose(th, thetas[k], atol=1e-4 * max(1, np.abs(thetas[k]).max()))
+        same, ndeg = _active_sets_agree(d, th, thetas[k], lams[k], lmax, r + stats[k].kkt)
+        assert same, (k, ndeg)
+
+
+def _slack_degenerate(d, th, lam, lmax, r_tot):
+    """Coordinates whose zero/nonzero status two points within KKT r_tot of the solution may
+    legitimately disagree on, judged from the oracle gradient alone (for problems too large for
+    the explicit design): inactive ones whose subgradient slack is below 10 r_tot lambda_max and
+    active ones smaller than 1e-3 of the largest coefficient."""
+    gr = O.gradient(d, th)
+    act = th != 0
+    small = np.abs(th) <= 1e-3 * max(np.abs(th).max(), 1e-300)
+    return (~act & (np.abs(np.abs(gr) - lam * d.pen_w) <= 10.0 * r_tot * lmax)) | (act & small)
+
+
+def test_fp32_and_fp64_plans_on_128x128x160_meet_the_oracle_kkt():
+    """A 128 x 128 x 160 Gaussian problem (p = (20, 20, 12)): the FP32 plan (tensor-core inner
+    product) and the FP64 plan (FP64 SIMT products) each reach the oracle's KKT conditions at every
+    lambda; their objectives agree, and so do their active sets outside degenerate coordinates."""
+    torch, g = gpu_or_skip()
+    n, p = (128, 128, 160), (20, 20, 12)
+    pr = _cast32(gen.random_problem(62, n, p, gen.GAUSSIAN, mask_frac=0.1, basis="normal"))
+    d = O.GlamData.from_c(pr.family, pr.XT, pr.Y, pr.W, pr.pen_w)
+    lmax = O.lambda_max(d)
+    lams = list(O.lambda_sequence(lmax, 6, 1e-2))
+    out = {}
+    for prec, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+        plan = g.Plan(n, p, gen.GAUSSIAN, plan_prec(g, prec))
+        res = g.glam_fit_path(plan, [dev(x, dt) for x in pr.XT], dev(pr.Y, dt), dev(pr.W, dt),
+                              dev(pr.pen_w, torch.float64), lambdas=lams, opts=g.glam_opts_default(tol=1e-7))
+        assert res.status == g.GLAM_OK, (prec, res.message)
+        out[prec] = host(res.path)
+        plan.close()
+    for k in range(len(lams)):
+        th32, th64 = O.paper_array(out["fp32"][k]), O.paper_array(out["fp64"][k])
+        r32 = O.kkt_residual(d, th32, lams[k], lmax)
+        r64 = O.kkt_residual(d, th64, lams[k], lmax)
+        assert r32 <= 1.001e-7 and r64 <= 1.001e-7, (k, r32, r64)
+        F32, F64 = O.objective(d, th32, lams[k]), O.objective(d, th64, lams[k])
+        assert abs(F32 - F64) <= 1e-9 * abs(F64), (k, F32, F64)
+        deg = _slack_degenerate(d, th64, lams[k], lmax, r32 + r64)
+        assert np.array_equal((th32 != 0)[~deg], (th64 != 0)[~deg]), (k, int(deg.sum()))
+
+
+def test_full_workload_fp32_path_meets_the_oracle_kkt():
+    """The benchmark's workload, 128 x 128 x 600 Gaussian with cubic B-spline bases p = (20, 20,
+    60), 50 lambdas to KKT 1e-6 with a GLAM_FP32 plan: the oracle's KKT residual of the returned
+    solution at the first, middle and last lambda, and the objective decreasing along the path."""
+    torch, g = gpu_or_skip()
+    pr = _cast32(gen.make_workload(1))
+    d = O.GlamData.from_c(pr.family, pr.XT, pr.Y, pr.W, pr.pen_w)
+    dt = torch.float32
+    plan = g.Plan(pr.n, pr.p, pr.family, g.GLAM_FP32)
+    res = g.glam_fit_path(plan, [dev(x, dt) for x in pr.XT], dev(pr.Y, dt), dev(pr.W, dt),
+                          dev(pr.pen_w, torch.float64), nlambda=pr.nlambda,
+                          opts=g.glam_opts_default(tol=1e-6, lambda_min_ratio=1e-3))
+    assert res.status == g.GLAM_OK, res.message
+    lmax = O.lambda_max(d)
+    assert abs(res.lambdas[0] - lmax) <= 1e-10 * lmax
+    for k in (0, pr.nlambda // 2 - 1, pr.nlambda - 1):
+        th = O.paper_array(host(res.path[k]))
+        r = O.kkt_residual(d, th, res.lambdas[k], lmax)
+        assert r <= 1.001e-6, (k, r)
+        assert abs(O.objective(d, th, res.lambdas[k]) - res.stats[k]["objective"]) <= 1e-9 * abs(res.stats[k]["objective"])
+    objs = [s["objective"] for s in res.stats]
+    assert all(b < a for a, b in zip(objs, objs[1:]))
+
+
+def test_masked_poisson_workload_path_meets_the_oracle_kkt():
+    """The 96 x 96 x 365 Poisson workload (log-rate in [-2, 4], 10% of cells masked by W = 0,
+    p = (30, 30, 40)), its 30-lambda path to KKT 1e-6 with a GLAM_FP32 plan: the oracle's KKT
+    residual at the first, middle and last lambda."""
+    torch, g = gpu_or_skip()
+    pr = _cast32(gen.make_workload(2))
+    d = O.GlamData.from_c(pr.family, pr.XT, pr.Y, pr.W, pr.pen_w)
+    dt = torch.float32
+    plan = g.Plan(pr.n, pr.p, pr.family, g.GLAM_FP32)
+    res = g.glam_fit_path(plan, [dev(x, dt) for x in pr.XT], dev(pr.Y, dt), dev(pr.W, dt),
+                          dev(pr.pen_w, torch.float64), nlambda=pr.nlambda,
+                          opts=g.glam_opts_default(tol=1e-6, lambda_min_ratio=1e-3))
+    assert res.status == g.GLAM_OK, res.message
+    lmax = O.lambda_max(d)
+    for k in (0, pr.nlambda // 2 - 1, pr.nlambda - 1):
+        th = O.paper_array(host(res.path[k]))
+        r = O.kkt_residual(d, th, res.lambdas[k], lmax)
+        assert r <= 1.001e-6, (k, r)
+        F = O.objective(d, th, res.lambdas[k])
+        assert abs(F - res.stats[k]["objective"]) <= 1e-9 * abs(F)
+
+
+# ------------------------------------------------------------------------------------------
+# d = 2 (n3 = p3 = 1, X[2] = None: the trivial third mode of Sec. 6.4's d = 2, 3)
+# ------------------------------------------------------------------------------------------
+
+def _two_d(seed, n2d, p2d, fam, mask=0.1):
+    pr = gen.random_problem(seed, n2d + (1,), p2d + (1,), fam, mask_frac=mask, basis="normal", pen_w="rand")
+    pr.XT[2] = np.ones((1, 1))
+    return pr
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("fam", [gen.GAUSSIAN, gen.POISSON])
+def test_two_dimensional_gradient_and_path_match_oracle(prec, fam):
+    torch, g = gpu_or_skip()
+    n2d, p2d = (45, 31), (7, 9)
+    pr = _two_d(63, n2d, p2d, fam)
+    if prec == "fp32":
+        pr = _cast32(pr)
+    d = O.GlamData.from_c(pr.family, pr.XT, pr.Y, pr.W, pr.pen_w)
+    dt = dtype_of(prec)
+    plan = g.Plan(n2d, p2d, fam, plan_prec(g, prec))
+    X = [dev(pr.XT[0], dt), dev(pr.XT[1], dt), None]
+    theta = 0.3 * np.random.default_rng(64).standard_normal((1, p2d[1], p2d[0]))
+    grad = host(g.glam_gradient(plan, X, dev(theta, dt), dev(pr.Y, dt), dev(pr.W, dt)))
+    th = O.paper_array(theta)
+    su, _, _ = cell_scales(fam, O.H(d.Xs, th), chain_H(d.Xs, th), d.Y, d.a)
+    assert_within(grad, O.c_array(O.gradient(d, th)), O.c_array(chain_G(d.Xs, su)) / d.n, BAR[prec],
+                  what="grad (d = 2)")
+    lams, thetas, stats, lmax = O.fit_path(d, nlambda=5, ratio=1e-2, tol=1e-10)
+    tol = 1e-9 if prec == "fp64" else 1e-6
+    res = g.glam_fit_path(plan, X, dev(pr.Y, dt), dev(pr.W, dt), dev(pr.pen_w, torch.float64),
+                          lambdas=list(lams), opts=g.glam_opts_default(tol=tol))
+    assert res.status == g.GLAM_OK, res.message
+    for k in range(len(lams)):
+        thk = O.paper_array(host(res.path[k]))
+        r = O.kkt_residual(d, thk, lams[k], lmax)
+        assert r <= 1.001 * tol, (k, r)
+        F, Fref = O.objective(d, thk, lams[k]), O.objective(d, thetas[k], lams[k])
+        assert abs(F - Fref) <= (1e-10 if prec == "fp64" else 1e-6) * abs(Fref)
+        same, ndeg = _active_sets_agree(d, thk, thetas[k], lams[k], lmax, r + stats[k].kkt)
+        assert same, (k, ndeg)
