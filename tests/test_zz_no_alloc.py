@@ -103,9 +103,9 @@ def test_noalloc_poisson_large_eta_is_clamped_like_glam_loss(prec):
     terms = ah * (np.exp(np.minimum(eh, c)) - yh * eh)
     ref = float(np.sum(terms)) / n
     out = torch.full((), float("nan"), dtype=torch.float64, device="cuda")
-    st = fn(gen.POISSON, g.GLAM_FP64 if prec == "fp64" else g.GLAM_FP32, n, dev(eh, dt).data_ptr(),
-            dev(yh, dt).data_ptr(), dev(ah, dt).data_ptr(), out.data_ptr(),
-            torch.cuda.current_stream().cuda_stream)
+    ed, yd, ad = dev(eh, dt), dev(yh, dt), dev(ah, dt)  # held until the call has run
+    st = fn(gen.POISSON, g.GLAM_FP64 if prec == "fp64" else g.GLAM_FP32, n, ed.data_ptr(), yd.data_ptr(),
+            ad.data_ptr(), out.data_ptr(), torch.cuda.current_stream().cuda_stream)
     assert st == g.GLAM_OK
     v = out.item()
     assert np.isfinite(v)
