@@ -58,6 +58,9 @@ adjprox_kernel(APShape sh, const __grid_constant__ CUtensorMap mapS, const __gri
                const double* __restrict__ gk, const double* __restrict__ x, const double* xp,
                const double* __restrict__ pen, double* out, float* __restrict__ dnext,
                const double* __restrict__ anchor, double inv_n, InnerCtl* ctl, int* err) {
+  // with a programmatic dependent launch this kernel may start before the preceding one ends:
+  // nothing is read or written before it has
+  griddep_wait();
   // written by the preceding kernels: the same value in every thread; tested once the first
   // copies are under way, so its load overlaps their issue
   const int done = ctl->done;
@@ -242,7 +245,7 @@ int adjprox_supported(int n3, int p3, int P21, const float* X3T, const float* Sb
 cudaError_t launch_adjprox(int n3, int p3, int P21, const float* X3T, const float* Sb, const double* gk,
                            const double* x, const double* xp, const double* pen, double* out,
                            float* dnext, const double* anchor, double inv_n, InnerCtl* ctl, int* err,
-                           cudaStream_t s) {
+                           cudaStream_t s, bool pdl) {
   APShape sh;
   size_t smem;
   if (!adjprox_supported(n3, p3, P21, X3T, Sb) || !ap_configure(n3, p3, P21, sh, smem))
@@ -267,18 +270,19 @@ cudaError_t launch_adjprox(int n3, int p3, int P21, const float* X3T, const floa
                      (uint32_t)sh.TJ))
     return cudaErrorInvalidValue;
   const int blocks = sh.nx * ((p3 + sh.TJ - 1) / sh.TJ);
+  cudaError_t e = cudaSuccess;
   switch (sh.TJ) {
-#define GLAM_AP(tj)                                                                                \
-  case tj:                                                                                         \
-    adjprox_kernel<tj><<<blocks, kAPThreads, smem, s>>>(sh, mapS, mapX, gk, x, xp, pen, out, dnext, \
-                                                        anchor, inv_n, ctl, err);                  \
+#define GLAM_AP(tj)                                                                                  \
+  case tj:                                                                                           \
+    e = launch_pdl(adjprox_kernel<tj>, dim3(blocks), dim3(kAPThreads), smem, s, pdl, sh, mapS, mapX, gk, \
+                   x, xp, pen, out, dnext, anchor, inv_n, ctl, err);                                 \
     break;
     GLAM_AP(1) GLAM_AP(2) GLAM_AP(3) GLAM_AP(4) GLAM_AP(5) GLAM_AP(6) GLAM_AP(7) GLAM_AP(8)
 #undef GLAM_AP
     default: return cudaErrorInvalidValue;
   }
   count_launches(1);
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace glam

@@ -877,11 +877,15 @@ int capture_chunk(Fit<T>& f) {
     if (fused) {
       // the fused kernel forms T_a = X_3 d from the correction itself, then the adjoint
       cudaError_t e = cudaSuccess;
+      // the tensor-core kernel and the adjoint + prox kernel alternate: each launch may overlap the
+      // end of the one before it (programmatic dependent launch), which writes nothing the overlapped
+      // part of the next reads (V, X_1, X_3 and the constant block stay fixed inside this loop)
+      const bool pdl = use_um && use_ap;
       if constexpr (sizeof(T) == 4) {
         if (use_um)
           e = launch_fused_umma((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2, (int)pl->p3,
                                 pl->um_form, pl->Vb != nullptr, pl->um_cst, op.w.dn, op.X[0], op.X[2], Vin,
-                                op.w.Sb, f.s, &pl->ctl->done, &pl->sc->timeout, f.wait_ns);
+                                op.w.Sb, f.s, &pl->ctl->done, &pl->sc->timeout, f.wait_ns, pdl && it > 0);
         else if (use_tc)
           e = launch_fused_slab_tc((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2,
                                    (int)pl->p3, pl->tc_cst, op.w.dn, op.w.V, op.w.Sb, f.s,
@@ -895,7 +899,7 @@ int capture_chunk(Fit<T>& f) {
         if (e == cudaSuccess && use_ap)  // mode-3 adjoint and prox step in one kernel
           e = launch_adjprox((int)pl->n3, (int)pl->p3, (int)(pl->p2 * pl->p1), op.X[2], op.w.Sb, pl->gk,
                              x, xp, pl->pen, xp, op.w.dn, pl->th, 1.0 / (double)pl->n, pl->ctl,
-                             &pl->sc->timeout, f.s);
+                             &pl->sc->timeout, f.s, pdl);
       }
       if (e == cudaSuccess && !use_ap)
         e = launch_gemm<T, T>(d_mode3_adj(pl, pl->ksplit), op.X[2], op.w.Sb, op.w.Qpart, f.s, nullptr,

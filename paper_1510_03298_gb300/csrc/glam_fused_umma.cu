@@ -12,7 +12,8 @@
 //   MMA2 (tcgen05) P (c x j2) = r^T X_2                              A = r from TMEM, B X_2^T (j2
 //                  rows) in shared memory
 //   MMA3 (tcgen05) S_b^T (j1 x j2) = X_1^T P                         P goes through shared memory
-//                  (the one transposition of the chain: it contracts the lane index c), M = 64
+//                  (the one transposition of the chain: it contracts the lane index c), M = 128
+//                  so that row j1 of S_b^T sits in TMEM lane j1
 // and S_b (p2 x p1) is written to global memory for the mode-3 adjoint.  Only eta's 128 x n2 tile
 // is ever formed, and only in TMEM.
 //
@@ -22,21 +23,23 @@
 // accumulation).  V is read as FP32, or as BF16 (TV) by the BF16 fit path.
 //
 // Issue.  A tcgen05.mma of the small N used here costs its issuing thread about 100 cycles
-// whatever N is (measured on this GPU), while several threads issuing at once overlap; so the MMAs
-// are issued by three threads and the operand splits of the 3xTF32 form share instructions where
-// an operand is common: the hi and lo parts of the constant operand sit side by side along N
-// (hi hi' and hi lo' in one instruction of twice the N), leaving hi' lo as the third.
+// whatever N is (measured on this GPU), while threads of different warps issuing at once overlap;
+// so the MMAs are issued by three threads of three warps that do nothing else, and the operand
+// splits of the 3xTF32 form share instructions where an operand is common: the hi and lo parts of
+// the constant operand sit side by side along N (hi hi' and hi lo' in one instruction of twice the
+// N), leaving hi' lo as the third.
 //
-// Warp roles (320 threads).  Warps 0-7 compute in two warpgroups; warp w reaches TMEM lanes
+// Warp roles (384 threads).  Warps 0-7 compute in two warpgroups; warp w reaches TMEM lanes
 // 32 (w mod 4) .. + 31 (rows c = 32 (w mod 4) + lane).  Warpgroup g owns the i2 columns
-// [g n2/2, (g+1) n2/2): its leader (warp 4g + 3, lane 0) issues MMA1 for those columns and, chunk
-// by chunk as r is formed, MMA2 over those columns into the warpgroup's own partial P (summed when
-// P is read); issuing both keeps every reuse of the group's TMEM columns in issue order on one
-// thread.  Warp 8 issues MMA3 and owns the TMEM allocation; warp 9 streams V by TMA through a ring
-// of 16-row chunks.  The roles meet at mbarriers; every wait is bounded (a kernel parameter,
-// default 2 s) and a wait that runs out sets an error flag, after which every role leaves its
-// loop, the copies and MMAs already issued are waited for (bounded by at least 2 s), the TMEM is
-// freed and the CTA exits.
+// [g n2/2, (g+1) n2/2) and its issuer warp 10 + g (lane 0) issues MMA1 for those columns and,
+// chunk by chunk as the warpgroup signals that r is in TMEM, MMA2 over those columns into the
+// group's own partial P (summed when P is read); one thread issuing both keeps every reuse of the
+// group's TMEM columns in issue order.  Warp 8 issues MMA3, writes S_b out and owns the TMEM
+// allocation; warp 9 streams V by TMA through a ring of 16-row chunks.  The roles meet only at
+// mbarriers; every wait is bounded (a kernel parameter, default 2 s) and a wait that runs out sets
+// an error flag, after which every role leaves its loop, the copies and MMAs already issued are
+// waited for (bounded by at least 2 s), the TMEM is freed and the CTA exits.
+
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -52,13 +55,14 @@ namespace {
 
 using namespace tma;
 
-constexpr int kUmThreads = 320;
-constexpr int kUmCompute = 256;     // warps 0-7
-constexpr int kUmMmaWarp = 8;
-constexpr int kUmTmaWarp = 9;
+constexpr int kUmThreads = 384;
+constexpr int kUmMmaWarp = 8;       // MMA3, S_b out, TMEM owner
+constexpr int kUmTmaWarp = 9;       // V producer
+constexpr int kUmIssWarp = 10;      // MMA1 / MMA2 issuers of warpgroups 0 and 1: warps 10, 11
 constexpr int kUmRows = 16;         // rows i2 of a V chunk (one 16-column TMEM load per thread)
 constexpr uint32_t kUmTmemCols = 512;
 constexpr int kUmMaxSlots = 24;
+constexpr int kUmMaxHalf = 8;       // chunks of a warpgroup per slab, at most (n2 <= 256)
 constexpr uint64_t kDrainNs = 2000000000ull;
 
 enum : int { kFormTF32 = 1, kForm3x = 3, kFormBF16 = 16 };
@@ -68,7 +72,8 @@ struct UmShape {
   int n1, n2, n3, p1, p2, p3;
   int K1;      // K of MMA1 (j2, padded): multiple of 8 (TF32) or 16 (BF16)
   int N2;      // N of MMA2 per part (j2, padded to 16)
-  int N3;      // N of MMA3 per part (j2, padded to 8)
+  int N3;      // N of MMA3 per part (j2, padded to 8 in the split form, else 16)
+  int P1P;     // rows j1 of a slab's T_a in shared memory (p1 padded to 4 with zero rows)
   int KA1;     // K atoms of MMA3 (i1): 32 (TF32) or 64 (BF16) elements each
   int KA2;     // K atoms of MMA2 (i2)
   int nchunk;  // V chunks of kUmRows rows i2 per slab (each warpgroup takes half)
@@ -77,6 +82,7 @@ struct UmShape {
   int R;       // rows of d per staging round
   int parts;   // 2 for the 3xTF32 form (hi, lo), else 1
   int64_t o_cst, o_xt1, o_x2t, o_x2, cst_bytes;  // constant block: [XT1 parts][X2T parts][X2]
+                                                 // (copied in two pieces: X2T and X2 first)
   int64_t xt1_part, x2t_part, x2_atom;           // X2: KA2 atoms of [hi rows N2][lo rows N2]
   int64_t o_stage, stage_bytes;  // d staging: the last bytes of the V ring and the P tile
   int64_t o_ptile, ptile_atom;   // P tile: KA1 atoms of [hi rows N3][lo rows N3]
@@ -92,10 +98,11 @@ __host__ __device__ inline int64_t up(int64_t v, int64_t a) { return (v + a - 1)
 __host__ __device__ inline int um_esz(int form) { return form == kFormBF16 ? 2 : 4; }
 
 // ---------------------------------------------------------------- device helpers
+// x rounded to TF32 (10 mantissa bits), to nearest with ties away from zero, on the bit pattern:
+// half a TF32 unit (bit 12) is added to the magnitude and the 13 low bits cleared; a carry moves
+// into the exponent as rounding requires (finite inputs; integer operations at full rate)
 __device__ __forceinline__ uint32_t rna_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
+  return (__float_as_uint(x) + 0x1000u) & 0xffffe000u;
 }
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x = lo (low half), .y = hi
@@ -128,12 +135,15 @@ __device__ __forceinline__ bool named_sync_and(int id, int n, bool ok) {
 }
 
 // Bounded wait with a caller-given limit (0: give up at once unless the phase has completed).
+// Between checks of the clock the thread sleeps in the barrier's wait (up to kSleepNs), so that
+// waiting roles take no issue slots or shared-memory bandwidth from the working ones.
+constexpr uint32_t kSleepNs = 1000;
 __device__ __forceinline__ bool wait_for(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   if (limit_ns == 0) return false;
   const uint64_t t0 = globaltimer_ns();
   while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait_sleep(bar, parity, kSleepNs)) return true;
     if (globaltimer_ns() - t0 > limit_ns) return false;
   }
 }
@@ -153,9 +163,10 @@ __device__ __forceinline__ void warp_arrive(uint64_t* bar) {
 // The mbarriers of the kernel, in static shared memory.
 struct UmBars {
   uint64_t full[kUmMaxSlots], empty[kUmMaxSlots];
-  uint64_t cst, stage, stage_free;
+  uint64_t cst, cst1, stage, stage_free;  // cst: X2T and X2 tiles; cst1: XT1 tiles
   uint64_t tb_ready, pt_ready, sb_ready;
-  uint64_t eta_ready[2], p_ready[2];  // per warpgroup
+  uint64_t eta_ready[2], p_ready[2];      // per warpgroup
+  uint64_t r_ready[2][kUmMaxHalf];        // per warpgroup and chunk of a slab: r is in TMEM
 };
 
 // One tcgen05.mma whose A operand sits in TMEM (TS) or shared memory (SS), by form.
@@ -168,6 +179,35 @@ template <int FORM>
 __device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
   if (FORM == kFormBF16) umma::mma_f16_ss(d, a, b, id, acc);
   else umma::mma_tf32_ss(d, a, b, id, acc);
+}
+
+// The FMA core of MMA0 for one thread (row c): acc[4 v + u] += sum_j1 X_1(c, j1) T(j1, 4 v + u)
+// over NV groups of four columns; the rows j1 go four at a time (rows past p1 are zero in T), the
+// four X_1 values through L1 and the 4 NV loads of T issued together.  A rolled loop: the kernel's
+// roles run different code at once, so its hot loops are kept small for the instruction cache.
+template <int NV>
+__device__ __forceinline__ void mma0_fma(const float* __restrict__ tk, int K1, int p1, const float* __restrict__ x1c,
+                                         int n1, bool rowok, float (&acc)[16]) {
+#pragma unroll 1
+  for (int j0 = 0; j0 < p1; j0 += 4) {
+    float x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) x[u] = (rowok && j0 + u < p1) ? __ldg(x1c + (int64_t)(j0 + u) * n1) : 0.f;
+    float4 t[4][NV];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) t[u][v] = reinterpret_cast<const float4*>(tk + (j0 + u) * K1)[v];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        acc[4 * v + 0] = fmaf(x[u], t[u][v].x, acc[4 * v + 0]);
+        acc[4 * v + 1] = fmaf(x[u], t[u][v].y, acc[4 * v + 1]);
+        acc[4 * v + 2] = fmaf(x[u], t[u][v].z, acc[4 * v + 2]);
+        acc[4 * v + 3] = fmaf(x[u], t[u][v].w, acc[4 * v + 3]);
+      }
+  }
 }
 
 template <int FORM, typename TV>
@@ -190,12 +230,14 @@ fused_slab_umma_kernel(UmShape sh, const unsigned char* __restrict__ Cst, const 
   const int kcta = (n3 - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
   unsigned char* const base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const uint32_t sbase = smem_u32(base);
-  float* const TaS = reinterpret_cast<float*>(base + sh.o_tas);   // [kmax][p1][K1]: T_a(k, j2, j1) at [k][j1][j2]
+  float* const TaS = reinterpret_cast<float*>(base + sh.o_tas);   // [kmax][P1P][K1]: T_a(k, j2, j1) at [k][j1][j2]
   float* const X3r = reinterpret_cast<float*>(base + sh.o_x3r);   // [p3][KQ]
   int* const rowlist = reinterpret_cast<int*>(base + sh.o_rows);  // rows j3 with a nonzero X_3 entry
   float* const stage = reinterpret_cast<float*>(base + sh.o_stage);
   const int KQ = (sh.kmax + 3) / 4 * 4;
+  const int P1P = sh.P1P;
   const uint64_t drain_ns = wait_ns > kDrainNs ? wait_ns : kDrainNs;
+  const int half = sh.nchunk / 2;  // chunks of a warpgroup per slab
 
   // ---------------------------------------------------------------- set-up
   if (tid == 0) {
@@ -206,6 +248,7 @@ fused_slab_umma_kernel(UmShape sh, const unsigned char* __restrict__ Cst, const 
       mbar_init(&bars.empty[s], 4);  // the four warps of the warpgroup that consumes the chunk
     }
     mbar_init(&bars.cst, 1);
+    mbar_init(&bars.cst1, 1);
     mbar_init(&bars.stage, 1);
     mbar_init(&bars.stage_free, 1);
     mbar_init(&bars.tb_ready, 8);
@@ -214,6 +257,7 @@ fused_slab_umma_kernel(UmShape sh, const unsigned char* __restrict__ Cst, const 
     for (int g = 0; g < 2; ++g) {
       mbar_init(&bars.eta_ready[g], 1);
       mbar_init(&bars.p_ready[g], 1);
+      for (int i = 0; i < kUmMaxHalf; ++i) mbar_init(&bars.r_ready[g][i], 4);
     }
     fence_mbar_init();
   }
@@ -265,10 +309,11 @@ fused_slab_umma_kernel(UmShape sh, const unsigned char* __restrict__ Cst, const 
     }
     __syncwarp();
   } else {
-    // ---------------------------------------------------------------- prologue (warps 0-8)
-    const int nth = kUmCompute + 32, ptid = tid;  // 288 threads
-    int rounds_issued = 0;                        // thread 0's count of staging copies
-    auto issue_round = [&](int rd) {              // thread 0: R rows of d (16-byte multiple)
+    // ---------------------------------------------------------------- prologue (every warp but 9)
+    const int nth = kUmThreads - 32;                     // 352 threads
+    const int ptid = warp < kUmTmaWarp ? tid : tid - 32;
+    int rounds_issued = 0;                               // thread 0's count of staging copies
+    auto issue_round = [&](int rd) {                     // thread 0: R rows of d (16-byte multiple)
       const int j0 = rd * sh.R, rows = (j0 + sh.R < p3) ? sh.R : p3 - j0;
       const uint32_t bulk = (uint32_t)(((int64_t)rows * P21) / 4 * 16);
       fence_proxy_async();
@@ -276,24 +321,25 @@ fused_slab_umma_kernel(UmShape sh, const unsigned char* __restrict__ Cst, const 
       if (bulk > 0) bulk_g2s(stage, D + (int64_t)j0 * P21, bulk, &bars.stage);
       ++rounds_issued;
     };
-    if (tid == 0) {
-      mbar_expect_tx(&bars.cst, (uint32_t)sh.cst_bytes);
-      bulk_g2s(base + sh.o_cst, Cst, (uint32_t)sh.cst_bytes, &bars.cst);
-      issue_round(0);
+    if (tid == 0) {  // the operands of MMA1 and MMA2 first, X_1's tiles (MMA3 needs them last) next
+      const uint32_t b23 = (uint32_t)(sh.cst_bytes - sh.o_x2t);
+      mbar_expect_tx(&bars.cst, b23);
+      bulk_g2s(base + sh.o_cst + sh.o_x2t, Cst + sh.o_x2t, b23, &bars.cst);
+      mbar_expect_tx(&bars.cst1, (uint32_t)sh.o_x2t);
+      bulk_g2s(base + sh.o_cst, Cst, (uint32_t)sh.o_x2t, &bars.cst1);
     }
-    // the compute warps' rows of X_1 (FP32), zero past p1 and past n1, loaded behind the copies
-    const int q = warp & 3, wg = warp >> 2;
-    const int c = 32 * q + lane;  // TMEM lane = row i1
-    const bool rowok = c < n1;
-    float x1[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) x1[j] = (warp < 8 && rowok && j < p1) ? X1T[(int64_t)j * n1 + c] : 0.f;
     // X_3 entries of this CTA's slabs, [j3][k]
     for (int idx = ptid; idx < p3 * KQ; idx += nth) {
       const int j3 = idx / KQ, kk = idx - j3 * KQ;
       X3r[idx] = kk < kcta ? X3T[(int64_t)j3 * n3 + blockIdx.x + (int64_t)kk * gridDim.x] : 0.f;
     }
-    for (int idx = ptid; idx < sh.kmax * p1 * K1; idx += nth) TaS[idx] = 0.f;
+    // d and S_b belong to the preceding kernels of the fit loop: with a programmatic dependent
+    // launch everything above may overlap them, nothing below
+    griddep_wait();
+    if (tid == 0) issue_round(0);
+    // T_a starts at zero, rows j1 >= p1 stay zero (MMA0 reads them in groups of four), and the
+    // slack after it is finite
+    for (int idx = ptid; idx < sh.kmax * P1P * K1 + 16; idx += nth) TaS[idx] = 0.f;
     named_sync(1, nth);
     // the rows j3 whose X_3 entries are not all zero for this CTA's slabs, in increasing order (a
     // zero row adds exactly nothing to the sums of the first H stage)
@@ -322,32 +368,42 @@ fused_slab_umma_kernel(UmShape sh, const unsigned char* __restrict__ Cst, const 
       }
       for (int i = (int)(bulk / 4) + ptid; i < rows * P21; i += nth) stage[i] = D[(int64_t)j0 * P21 + i];
       if (!wait_for(&bars.stage, (uint32_t)(rd & 1), wait_ns)) atomicOr(&timed_out, 1);
-      named_sync(1, nth);
-      if (*(volatile int*)&timed_out) break;
+      // one decision for all the threads (the flag may be raised by the producer at any time)
+      if (!named_sync_and(1, nth, !*(volatile int*)&timed_out)) break;
       int re = rl;
       const int nr = nrows_s;
       while (re < nr && rowlist[re] < j0 + rows) ++re;
-      // task = (one column n, 4 slabs k)
+      // task = (one column n, 4 slabs k); the rows are taken eight at a time with their loads
+      // issued together (past the last row the d value is zero, which adds exactly nothing)
       const int nkg = (kcta + 3) / 4;
       for (int task = ptid; task < P21 * nkg; task += nth) {
         const int nn = task % P21, k0 = 4 * (task / P21);
         const int j2 = nn / p1, j1 = nn - j2 * p1;
         float a[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) a[r] = (k0 + r < kcta) ? TaS[((k0 + r) * p1 + j1) * K1 + j2] : 0.f;
-#pragma unroll 4
-        for (int t = rl; t < re; ++t) {
-          const int j3 = rowlist[t];
-          const float dv = stage[(j3 - j0) * P21 + nn];
-          const float4 x4 = *reinterpret_cast<const float4*>(X3r + j3 * KQ + k0);
-          a[0] = fmaf(x4.x, dv, a[0]);
-          a[1] = fmaf(x4.y, dv, a[1]);
-          a[2] = fmaf(x4.z, dv, a[2]);
-          a[3] = fmaf(x4.w, dv, a[3]);
+        for (int r = 0; r < 4; ++r) a[r] = (k0 + r < kcta) ? TaS[((k0 + r) * P1P + j1) * K1 + j2] : 0.f;
+        for (int t0 = rl; t0 < re; t0 += 8) {
+          int jr[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) jr[u] = rowlist[t0 + u < re ? t0 + u : re - 1];
+          float dv[8];
+          float4 xv[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            dv[u] = t0 + u < re ? stage[(jr[u] - j0) * P21 + nn] : 0.f;
+            xv[u] = *reinterpret_cast<const float4*>(X3r + jr[u] * KQ + k0);
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            a[0] = fmaf(xv[u].x, dv[u], a[0]);
+            a[1] = fmaf(xv[u].y, dv[u], a[1]);
+            a[2] = fmaf(xv[u].z, dv[u], a[2]);
+            a[3] = fmaf(xv[u].w, dv[u], a[3]);
+          }
         }
 #pragma unroll
         for (int r = 0; r < 4; ++r)
-          if (k0 + r < kcta) TaS[((k0 + r) * p1 + j1) * K1 + j2] = a[r];
+          if (k0 + r < kcta) TaS[((k0 + r) * P1P + j1) * K1 + j2] = a[r];
       }
       rl = re;
     }
@@ -361,278 +417,326 @@ fused_slab_umma_kernel(UmShape sh, const unsigned char* __restrict__ Cst, const 
     const uint32_t x1b = sbase + (uint32_t)sh.o_xt1, x2tb = sbase + (uint32_t)sh.o_x2t,
                    x2b = sbase + (uint32_t)sh.o_x2, ptb = sbase + (uint32_t)sh.o_ptile;
     if (warp == kUmMmaWarp) {
-      // ---------------------------------------------------------------- MMA3 issue (warp 8)
-      if (lane == 0) {
-        bool ok = !*(volatile int*)&timed_out && wait_for(&bars.cst, 0u, wait_ns);
-        const uint32_t id3 = umma::idesc(64, (uint32_t)(PARTS * sh.N3), kType, kType, 0, 0);
-        const uint32_t id3h = umma::idesc(64, (uint32_t)sh.N3, kType, kType, 0, 0);
-        const uint64_t ad0 = umma::sdesc(x1b, 16, 1024, umma::kSwizzle128B);
-        const uint64_t ad1 = umma::sdesc(x1b + (uint32_t)sh.xt1_part, 16, 1024, umma::kSwizzle128B);
-        const uint64_t bd0 = umma::sdesc(ptb, 16, 1024, umma::kSwizzle128B);
-        const uint32_t da = (uint32_t)(4096 >> 4), db = (uint32_t)(sh.ptile_atom >> 4);  // atom steps
-        int committed = 0;
-        for (int k = 0; k < kcta && ok; ++k) {
-          const uint32_t par = (uint32_t)(k & 1);
+      // ---------------------------------------------------------------- MMA3 and S_b (warp 8)
+      // S_b^T = X_1^T P with M = 128: A reads 128 rows j1 from each 32-row K atom of XT1 (the rows
+      // past the atom belong to the next atoms or the tiles after them; their outputs, TMEM lanes
+      // 32 .. 127, are never read).  In the split form both instructions take B = [P_hi | P_lo]:
+      // X_1 hi with it gives hi hi' and hi lo', X_1 lo gives lo hi' (and lo lo', a smaller term).
+      const uint32_t id3 = umma::idesc(128, (uint32_t)(PARTS * sh.N3), kType, kType, 0, 0);
+      const uint64_t ad0 = umma::sdesc(x1b, 16, 1024, umma::kSwizzle128B);
+      const uint64_t ad1 = umma::sdesc(x1b + (uint32_t)sh.xt1_part, 16, 1024, umma::kSwizzle128B);
+      const uint64_t bd0 = umma::sdesc(ptb, 16, 1024, umma::kSwizzle128B);
+      const uint32_t da = (uint32_t)(4096 >> 4), db = (uint32_t)(sh.ptile_atom >> 4);  // atom steps
+      int committed = 0;
+      bool ok = true;
+      if (lane == 0) ok = !*(volatile int*)&timed_out && wait_for(&bars.cst1, 0u, wait_ns);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      for (int k = 0; k < kcta && ok; ++k) {
+        const uint32_t par = (uint32_t)(k & 1);
+        if (lane == 0) {
           ok = wait_for(&bars.pt_ready, par, wait_ns);
-          if (!ok) break;
-          umma::fence_after_sync();
-          // S_b^T = X_1^T P: A reads 64 rows j1 of the 32-row atoms (rows past p1 unused); in the
-          // split form the first instruction takes B = [P_hi | P_lo] (hi hi' and hi lo'), the second
-          // A = X_1 lo with B = P_hi
-          for (int ka = 0; ka < sh.KA1; ++ka)
+          if (ok) {
+            umma::fence_after_sync();
+            for (int ka = 0; ka < sh.KA1; ++ka)
 #pragma unroll
-            for (int s4 = 0; s4 < 4; ++s4) {
-              const uint64_t off = (uint64_t)(2 * s4);
-              mma_ss<FORM>(tb + sh.c_sb, ad0 + ka * da + off, bd0 + ka * db + off, id3, (ka | s4) != 0);
-              if (PARTS == 2) mma_ss<FORM>(tb + sh.c_sb, ad1 + ka * da + off, bd0 + ka * db + off, id3h, 1u);
+              for (int s4 = 0; s4 < 4; ++s4) {
+                const uint64_t off = (uint64_t)(2 * s4);
+                mma_ss<FORM>(tb + sh.c_sb, ad0 + ka * da + off, bd0 + ka * db + off, id3, (ka | s4) != 0);
+                if (PARTS == 2) mma_ss<FORM>(tb + sh.c_sb, ad1 + ka * da + off, bd0 + ka * db + off, id3, 1u);
+              }
+            umma::commit(&bars.sb_ready);
+            ++committed;
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        if (!ok) break;
+        ok = warp_wait(&bars.sb_ready, par, wait_ns);
+        if (!ok) break;
+        umma::fence_after_sync();
+        // row j1 of S_b^T in lane j1; S_b(s, j2, j1) is stored with j1 fastest
+        float* out = Sb + (int64_t)((int)blockIdx.x + k * (int)gridDim.x) * P21;
+        for (int g0 = 0; g0 < sh.N3 / 8; ++g0) {
+          uint32_t sv[8], sl[8];
+          umma::ld_x8(tb + sh.c_sb + 8u * g0, sv);
+          if (PARTS == 2) umma::ld_x8(tb + sh.c_sb + (uint32_t)sh.N3 + 8u * g0, sl);
+          umma::wait_ld();
+          umma::ld_done(sv);
+          if (PARTS == 2) umma::ld_done(sl);
+          if (lane < p1) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int j2 = 8 * g0 + u;
+              const float x = PARTS == 2 ? __uint_as_float(sv[u]) + __uint_as_float(sl[u]) : __uint_as_float(sv[u]);
+              if (j2 < p2) out[j2 * p1 + lane] = x;
             }
-          umma::commit(&bars.sb_ready);
-          ++committed;
+          }
+        }
+      }
+      if (!ok) atomicOr(&timed_out, 1);
+      // every MMA issued has completed before the TMEM is released (the last commit covers all)
+      if (lane == 0 && committed > 0) wait_for(&bars.sb_ready, (uint32_t)((committed - 1) & 1), drain_ns);
+      __syncwarp();
+    } else if (warp >= kUmIssWarp) {
+      // ---------------------------------------------------------------- MMA1 / MMA2 issue (warps 10, 11)
+      const int g = warp - kUmIssWarp;  // the warpgroup served
+      if (lane == 0) {
+        const int ncw = n2 / 2;         // i2 columns of the warpgroup
+        // MMA1: eta^T(:, g ncw .. + ncw) = T_b^T X_2^T
+        const uint32_t id1 = umma::idesc(128, (uint32_t)ncw, kType, kType, 0, 0);
+        const uint64_t b1h = umma::sdesc(x2tb + (uint32_t)(g * ncw * 128), 16, 1024, umma::kSwizzle128B);
+        const uint64_t b1l = umma::sdesc(x2tb + (uint32_t)sh.x2t_part + (uint32_t)(g * ncw * 128), 16, 1024,
+                                         umma::kSwizzle128B);
+        const uint32_t d1 = tb + sh.c_eta + (uint32_t)(g * ncw);
+        auto mma1 = [&]() {
+          for (int s = 0; s < K1 / (int)KS; ++s) {
+            const uint64_t off = (uint64_t)(2 * s);  // 32 bytes of K
+            mma_ts<FORM>(d1, tb + sh.c_tb + 8u * s, b1h + off, id1, s != 0);
+            if (PARTS == 2) {
+              mma_ts<FORM>(d1, tb + sh.c_tb + 8u * s, b1l + off, id1, 1u);
+              mma_ts<FORM>(d1, tb + sh.c_tblo + 8u * s, b1h + off, id1, 1u);
+            }
+          }
+        };
+        // MMA2 for one chunk (kUmRows columns i2 = one or two K steps): P_g (+)= r^T X_2
+        const uint32_t id2 = umma::idesc(128, (uint32_t)(PARTS * sh.N2), kType, kType, 0, 0);
+        const uint32_t id2h = umma::idesc(128, (uint32_t)sh.N2, kType, kType, 0, 0);
+        const uint64_t b2 = umma::sdesc(x2b, 16, 1024, umma::kSwizzle128B);
+        const uint32_t pcol = tb + sh.c_p + (uint32_t)g * sh.pw;
+        auto mma2 = [&](int ch, bool first) {
+          for (int u = 0; u < kUmRows / (int)KS; ++u) {
+            const int s = ch * (kUmRows / (int)KS) + u;  // global K step over i2
+            const uint64_t bd = b2 + (uint64_t)(((s >> 2) * sh.x2_atom + (s & 3) * 32) >> 4);
+            const uint32_t ar = FORM == kFormBF16 ? tb + sh.c_rb + 8u * s : tb + sh.c_eta + 8u * s;
+            mma_ts<FORM>(pcol, ar, bd, id2, (first && u == 0) ? 0u : 1u);
+            if (PARTS == 2) mma_ts<FORM>(pcol, tb + sh.c_rlo + 8u * s, bd, id2h, 1u);
+          }
+        };
+        int ne = 0, np = 0;  // commits on eta_ready[g] and p_ready[g]
+        bool ok = !*(volatile int*)&timed_out && wait_for(&bars.cst, 0u, wait_ns) &&
+                  wait_for(&bars.tb_ready, 0u, wait_ns);
+        if (ok) {
+          umma::fence_after_sync();
+          mma1();
+          umma::commit(&bars.eta_ready[g]);
+          ++ne;
+        }
+        for (int k = 0; k < kcta && ok; ++k) {
+          for (int i = 0; i < half && ok; ++i) {
+            ok = wait_for(&bars.r_ready[g][i], (uint32_t)(k & 1), wait_ns);
+            // P_g is overwritten by this slab's first MMA2: every compute warp has read the last
+            // slab's (pt_ready)
+            if (ok && i == 0 && k > 0) ok = wait_for(&bars.pt_ready, (uint32_t)((k - 1) & 1), wait_ns);
+            if (!ok) break;
+            umma::fence_after_sync();
+            mma2(g * half + i, i == 0);
+          }
+          if (!ok) break;
+          umma::commit(&bars.p_ready[g]);
+          ++np;
+          if (k + 1 < kcta) {
+            // MMA1 of the next slab once every compute warp has written its T_b^T
+            ok = wait_for(&bars.tb_ready, (uint32_t)((k + 1) & 1), wait_ns);
+            if (!ok) break;
+            umma::fence_after_sync();
+            mma1();
+            umma::commit(&bars.eta_ready[g]);
+            ++ne;
+          }
         }
         if (!ok) atomicOr(&timed_out, 1);
-        // every MMA issued has completed before the TMEM is released (the last commit covers all)
-        if (committed > 0) wait_for(&bars.sb_ready, (uint32_t)((committed - 1) & 1), drain_ns);
+        // this issuer's MMAs have completed before the TMEM is released
+        if (ne > 0) wait_for(&bars.eta_ready[g], (uint32_t)((ne - 1) & 1), drain_ns);
+        if (np > 0) wait_for(&bars.p_ready[g], (uint32_t)((np - 1) & 1), drain_ns);
       }
       __syncwarp();
     } else {
       // ---------------------------------------------------------------- compute warps 0-7
+      const int q = warp & 3, wg = warp >> 2;
+      const int c = 32 * q + lane;  // TMEM lane = row i1
+      const bool rowok = c < n1;
       const uint32_t lq = (uint32_t)(32 * q) << 16;
-      const int half = sh.nchunk / 2;                 // chunks of this warpgroup
-      const int ncw = n2 / 2;                         // i2 columns of this warpgroup
-      const bool leader_warp = q == 3;                // issues this warpgroup's MMA1 and MMA2
-      const bool issuer = leader_warp && lane == 0;
-      const uint32_t pcol = sh.c_p + (uint32_t)wg * sh.pw;  // this warpgroup's partial P
-      // MMA1 for this warpgroup's columns: eta^T(:, wg ncw .. + ncw) = T_b^T X_2^T
-      const uint32_t id1 = umma::idesc(128, (uint32_t)ncw, kType, kType, 0, 0);
-      const uint64_t b1h = umma::sdesc(x2tb + (uint32_t)(wg * ncw * 128), 16, 1024, umma::kSwizzle128B);
-      const uint64_t b1l = umma::sdesc(x2tb + (uint32_t)sh.x2t_part + (uint32_t)(wg * ncw * 128), 16, 1024,
-                                       umma::kSwizzle128B);
-      const uint32_t d1 = tb + sh.c_eta + (uint32_t)(wg * ncw);
-      auto mma1 = [&]() {
-        for (int s = 0; s < K1 / (int)KS; ++s) {
-          const uint64_t off = (uint64_t)(2 * s);  // 32 bytes of K
-          mma_ts<FORM>(d1, tb + sh.c_tb + 8u * s, b1h + off, id1, s != 0);
-          if (PARTS == 2) {
-            mma_ts<FORM>(d1, tb + sh.c_tb + 8u * s, b1l + off, id1, 1u);
-            mma_ts<FORM>(d1, tb + sh.c_tblo + 8u * s, b1h + off, id1, 1u);
-          }
-        }
-      };
-      // MMA2 for one chunk (kUmRows columns i2 = one or two K steps): P_g (+)= r^T X_2
-      const uint32_t id2 = umma::idesc(128, (uint32_t)(PARTS * sh.N2), kType, kType, 0, 0);
-      const uint32_t id2h = umma::idesc(128, (uint32_t)sh.N2, kType, kType, 0, 0);
-      const uint64_t b2 = umma::sdesc(x2b, 16, 1024, umma::kSwizzle128B);
-      auto mma2 = [&](int ch, bool first) {
-        for (int u = 0; u < kUmRows / (int)KS; ++u) {
-          const int s = ch * (kUmRows / (int)KS) + u;  // global K step over i2
-          const uint64_t bd = b2 + (uint64_t)(((s >> 2) * sh.x2_atom + (s & 3) * 32) >> 4);
-          const uint32_t ar = FORM == kFormBF16 ? tb + sh.c_rb + 8u * s : tb + sh.c_eta + 8u * s;
-          mma_ts<FORM>(tb + pcol, ar, bd, id2, (first && u == 0) ? 0u : 1u);
-          if (PARTS == 2) mma_ts<FORM>(tb + pcol, tb + sh.c_rlo + 8u * s, bd, id2h, 1u);
-        }
-      };
+      const int hw = K1 / 2;        // columns j2 of T_b^T this warpgroup forms
       bool ok = __all_sync(0xffffffffu, !*(volatile int*)&timed_out) != 0;
-      // MMA0 on the compute warps: T_b^T(c, j2) = sum_j1 X_1(c, j1) T_a(k, j2, j1), written as the
-      // A operand of MMA1 (warpgroup wg takes the 8- or 16-column groups wg, wg + 2, ...); each
-      // thread keeps one independent FMA chain per column of its group
+      // MMA0 on the compute warps: T_b^T(c, j2) = sum_j1 X_1(c, j1) T_a(k, j2, j1) for this
+      // warpgroup's columns j2 in [wg hw, wg hw + hw), written as the A operand of MMA1
+      const float* const x1c = X1T + (rowok ? c : 0);
       auto mma0 = [&](int kk) {
-        constexpr int GW = FORM == kFormBF16 ? 16 : 8;  // j2 per group (8 TMEM columns)
-        for (int g0 = wg; g0 < K1 / GW; g0 += 2) {
-          float acc[GW];
+        const float* tk = TaS + (int64_t)kk * P1P * K1 + wg * hw;
+        float acc[16];
 #pragma unroll
-          for (int u = 0; u < GW; ++u) acc[u] = 0.f;
+        for (int u = 0; u < 16; ++u) acc[u] = 0.f;
+        switch (hw >> 2) {
+          case 1: mma0_fma<1>(tk, K1, p1, x1c, n1, rowok, acc); break;
+          case 2: mma0_fma<2>(tk, K1, p1, x1c, n1, rowok, acc); break;
+          case 3: mma0_fma<3>(tk, K1, p1, x1c, n1, rowok, acc); break;
+          default: mma0_fma<4>(tk, K1, p1, x1c, n1, rowok, acc); break;
+        }
+        if (FORM == kFormBF16) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            if (j < p1) {
-              const float4* t4 = reinterpret_cast<const float4*>(TaS + ((int64_t)kk * p1 + j) * K1 + g0 * GW);
+          for (int q8 = 0; q8 < 2; ++q8)
+            if (8 * q8 < hw) {
+              uint32_t pk[4];
 #pragma unroll
-              for (int v = 0; v < GW / 4; ++v) {
-                const float4 t = t4[v];
-                acc[4 * v + 0] = fmaf(x1[j], t.x, acc[4 * v + 0]);
-                acc[4 * v + 1] = fmaf(x1[j], t.y, acc[4 * v + 1]);
-                acc[4 * v + 2] = fmaf(x1[j], t.z, acc[4 * v + 2]);
-                acc[4 * v + 3] = fmaf(x1[j], t.w, acc[4 * v + 3]);
+              for (int u = 0; u < 4; ++u) pk[u] = pack_bf16(acc[8 * q8 + 2 * u], acc[8 * q8 + 2 * u + 1]);
+              umma::st_x4(tb + lq + sh.c_tb + (uint32_t)((wg * hw + 8 * q8) / 2), pk);
+            }
+        } else {
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            if (4 * v < hw) {
+              uint32_t hi[4], lo[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                hi[u] = rna_tf32(acc[4 * v + u]);
+                lo[u] = rna_tf32(acc[4 * v + u] - __uint_as_float(hi[u]));
               }
+              umma::st_x4(tb + lq + sh.c_tb + (uint32_t)(wg * hw + 4 * v), hi);
+              if (PARTS == 2) umma::st_x4(tb + lq + sh.c_tblo + (uint32_t)(wg * hw + 4 * v), lo);
             }
-          }
-          uint32_t hi[8], lo[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            if (FORM == kFormBF16) {
-              hi[u] = pack_bf16(acc[2 * u], acc[(2 * u + 1) % GW]);
-            } else {
-              hi[u] = rna_tf32(acc[u]);
-              lo[u] = rna_tf32(acc[u] - __uint_as_float(hi[u]));
-            }
-          }
-          umma::st_x8(tb + lq + sh.c_tb + 8u * g0, hi);
-          if (PARTS == 2) umma::st_x8(tb + lq + sh.c_tblo + 8u * g0, lo);
         }
         umma::wait_st();
         umma::fence_before_sync();
         warp_arrive(&bars.tb_ready);
       };
-      // the leader issues MMA1 of slab kk once every warp has written T_b^T (tb_ready) and the
-      // constant tiles have landed; its commit tells the warpgroup that eta is in TMEM
-      auto issue_mma1 = [&](int kk) -> bool {
-        bool lok = true;
-        if (issuer) {
-          lok = wait_for(&bars.tb_ready, (uint32_t)(kk & 1), wait_ns) && (kk > 0 || wait_for(&bars.cst, 0u, wait_ns));
-          if (lok) {
-            umma::fence_after_sync();
-            mma1();
-            umma::commit(&bars.eta_ready[wg]);
-          }
-        }
-        __syncwarp();
-        return __all_sync(0xffffffffu, lok) != 0;
+      // the chunks whose r stores are in flight: their r_ready arrivals wait until the next chunks'
+      // loads have been issued, so the store latency overlaps them
+      auto r_done = [&](int i, int m) {
+        umma::wait_st();
+        umma::fence_before_sync();
+        warp_arrive(&bars.r_ready[wg][i]);
+        if (m == 2) warp_arrive(&bars.r_ready[wg][i + 1]);
       };
-      int committed = 0;  // this issuer's commits (eta_ready and p_ready alternate: 2 per slab)
-      if (ok) mma0(0);
-      if (ok && leader_warp) ok = issue_mma1(0);
-      if (issuer && ok) committed = 1;
-      // Every warp of a warpgroup passes that group's named barrier (2 + wg) exactly once per chunk
-      // until the group leaves its loop together: the barrier ANDs the warps' status, and it is the
-      // only place a warp leaves the loop.  Elsewhere a wait that runs out only clears `ok`, which
-      // skips the remaining work and reaches the next chunk barrier.
-      for (int k = 0; k < kcta; ++k) {
-        const uint32_t par = (uint32_t)(k & 1);
-        // ---- r = V (.) eta over this warpgroup's chunks; MMA2 of each chunk as soon as it is in TMEM
-        ok = ok && warp_wait(&bars.eta_ready[wg], par, wait_ns);
-        umma::fence_after_sync();
-        // P_g is overwritten by this slab's MMA2: every warp has read the last slab's (pt_ready)
-        if (leader_warp && k > 0) ok = ok && warp_wait(&bars.pt_ready, (uint32_t)((k - 1) & 1), wait_ns);
-        for (int i = 0; i < half; ++i) {
-          const int ch = wg * half + i;
-          const int g = k * sh.nchunk + ch, slot = g % sh.nslot;
-          const bool okc = ok && warp_wait(&bars.full[slot], (uint32_t)((g / sh.nslot) & 1), wait_ns);
-          if (okc) {
-            const TV* vs = reinterpret_cast<const TV*>(base + sh.o_ring + (int64_t)slot * sh.slot_bytes);
-            uint32_t e[16];
-            umma::ld_x16(tb + lq + sh.c_eta + (uint32_t)(kUmRows * ch), e);
-            float v[16];
+      // r = V (.) eta for one chunk: eta from e, V from the slot; r (split or packed) to TMEM
+      auto v_load = [&](int s, float (&v)[16]) {
+        const TV* vs = reinterpret_cast<const TV*>(base + sh.o_ring + (int64_t)s * sh.slot_bytes);
 #pragma unroll
-            for (int u = 0; u < 16; ++u) v[u] = rowok ? vload<TV>(vs + u * n1 + c) : 0.f;
-            umma::wait_ld();
-            if (FORM == kFormBF16) {
-              uint32_t pk[8];
+        for (int u = 0; u < 16; ++u) v[u] = rowok ? vload<TV>(vs + u * n1 + c) : 0.f;
+      };
+      auto r_chunk = [&](int ch, const float (&v)[16], uint32_t (&e)[16]) {
+        if (FORM == kFormBF16) {
+          uint32_t pk[8];
 #pragma unroll
-              for (int u = 0; u < 8; ++u)
-                pk[u] = pack_bf16(v[2 * u] * __uint_as_float(e[2 * u]), v[2 * u + 1] * __uint_as_float(e[2 * u + 1]));
-              umma::st_x8(tb + lq + sh.c_rb + (uint32_t)(8 * ch), pk);
-            } else {
-              uint32_t hi[16], lo[16];
+          for (int u = 0; u < 8; ++u)
+            pk[u] = pack_bf16(v[2 * u] * __uint_as_float(e[2 * u]), v[2 * u + 1] * __uint_as_float(e[2 * u + 1]));
+          umma::st_x8(tb + lq + sh.c_rb + (uint32_t)(8 * ch), pk);
+        } else {
+          uint32_t lo[16];
 #pragma unroll
-              for (int u = 0; u < 16; ++u) {
-                const float r = v[u] * __uint_as_float(e[u]);
-                hi[u] = rna_tf32(r);
-                lo[u] = rna_tf32(r - __uint_as_float(hi[u]));
-              }
-              umma::st_x16(tb + lq + sh.c_eta + (uint32_t)(kUmRows * ch), hi);
-              if (PARTS == 2) umma::st_x16(tb + lq + sh.c_rlo + (uint32_t)(kUmRows * ch), lo);
-            }
-            warp_arrive(&bars.empty[slot]);
-            umma::wait_st();
+          for (int u = 0; u < 16; ++u) {
+            const float r = v[u] * __uint_as_float(e[u]);
+            e[u] = rna_tf32(r);
+            lo[u] = rna_tf32(r - __uint_as_float(e[u]));
           }
-          umma::fence_before_sync();
-          // the chunk's r is in TMEM for all 128 rows
-          ok = named_sync_and(2 + wg, 128, okc);
-          if (!ok) break;
-          if (issuer) {
-            umma::fence_after_sync();
-            mma2(ch, i == 0);
-            if (i == half - 1) umma::commit(&bars.p_ready[wg]);
-          }
-          __syncwarp();
+          umma::st_x16(tb + lq + sh.c_eta + (uint32_t)(kUmRows * ch), e);
+          if (PARTS == 2) umma::st_x16(tb + lq + sh.c_rlo + (uint32_t)(kUmRows * ch), lo);
         }
-        if (!ok) break;  // the whole warpgroup (the barrier's AND)
-        if (issuer) ++committed;
+      };
+      if (ok) mma0(0);
+      for (int k = 0; k < kcta && ok; ++k) {
+        const uint32_t par = (uint32_t)(k & 1);
+        // ---- r = V (.) eta over this warpgroup's chunks, two at a time (both chunks' loads issued
+        // before one wait), each chunk signalled to the issuer when in TMEM
+        ok = warp_wait(&bars.eta_ready[wg], par, wait_ns);
+        if (!ok) break;
+        umma::fence_after_sync();
+        const int g0 = k * sh.nchunk + wg * half;  // ring position of the first chunk
+        int slot = g0 % sh.nslot;
+        uint32_t ph = (uint32_t)((g0 / sh.nslot) & 1);
+        int pend = -1, pm = 0;
+        for (int i = 0; i < half; i += 2) {
+          const int m = i + 1 < half ? 2 : 1;
+          const int ch = wg * half + i;
+          const int s0 = slot;
+          const uint32_t ph0 = ph;
+          if (++slot == sh.nslot) slot = 0, ph ^= 1u;
+          const int s1 = slot;
+          const uint32_t ph1 = ph;
+          if (m == 2 && ++slot == sh.nslot) slot = 0, ph ^= 1u;
+          ok = warp_wait(&bars.full[s0], ph0, wait_ns) && (m == 1 || warp_wait(&bars.full[s1], ph1, wait_ns));
+          if (!ok) break;
+          uint32_t e0[16], e1[16];
+          float v0[16], v1[16];
+          umma::ld_x16(tb + lq + sh.c_eta + (uint32_t)(kUmRows * ch), e0);
+          if (m == 2) umma::ld_x16(tb + lq + sh.c_eta + (uint32_t)(kUmRows * (ch + 1)), e1);
+          v_load(s0, v0);
+          if (m == 2) v_load(s1, v1);
+          if (pend >= 0) r_done(pend, pm);
+          umma::wait_ld();
+          umma::ld_done(e0);
+          umma::ld_done(e1);
+          warp_arrive(&bars.empty[s0]);  // the slots' data is in registers
+          if (m == 2) warp_arrive(&bars.empty[s1]);
+          r_chunk(ch, v0, e0);
+          if (m == 2) r_chunk(ch + 1, v1, e1);
+          pend = i;
+          pm = m;
+        }
+        if (!ok) break;
+        r_done(pend, pm);
         // ---- MMA0 of the next slab (T_b^T is free once both warpgroups' MMA1 of this slab ran)
         if (k + 1 < kcta) {
-          ok = ok && warp_wait(&bars.eta_ready[wg ^ 1], par, wait_ns);
-          if (ok) mma0(k + 1);
-          if (ok && leader_warp) {
-            ok = issue_mma1(k + 1);
-            if (ok && issuer) ++committed;
-          }
+          ok = warp_wait(&bars.eta_ready[wg ^ 1], par, wait_ns);
+          if (!ok) break;
+          umma::fence_after_sync();
+          mma0(k + 1);
         }
         // ---- P = P_0 + P_1 from TMEM into the B operand of MMA3 (K-major rows j2, K = c; warp q
         // writes K atom q of 32 rows c (TF32) or half of atom q / 2 (BF16); the split form stores
         // hi in rows j2 and lo in rows N3 + j2 of the atom).  The tile is free once MMA3 of the last
-        // slab ran (sb_ready), whose S_b warps 0 and 1 write out first.
-        ok = ok && warp_wait(&bars.p_ready[0], par, wait_ns) && warp_wait(&bars.p_ready[1], par, wait_ns);
-        if (k > 0) ok = ok && warp_wait(&bars.sb_ready, (uint32_t)((k - 1) & 1), wait_ns);
+        // slab ran (sb_ready).
+        ok = warp_wait(&bars.p_ready[0], par, wait_ns) && warp_wait(&bars.p_ready[1], par, wait_ns);
+        if (ok && k > 0) ok = warp_wait(&bars.sb_ready, (uint32_t)((k - 1) & 1), wait_ns);
+        if (!ok) break;
         umma::fence_after_sync();
-        auto write_sb = [&](int kk) {  // S_b^T (M = 64 layout: rows 0-15 in lanes 0-15 of warps 0, 1)
-          const int j1 = 16 * warp + lane;
-          float* out = Sb + (int64_t)((int)blockIdx.x + kk * (int)gridDim.x) * P21;
-          for (int g0 = 0; g0 < sh.N3 / 8; ++g0) {
-            uint32_t sv[8], sl[8];
-            umma::ld_x8(tb + lq + sh.c_sb + 8u * g0, sv);
-            if (PARTS == 2) umma::ld_x8(tb + lq + sh.c_sb + (uint32_t)sh.N3 + 8u * g0, sl);
-            umma::wait_ld();
-            if (lane < 16 && j1 < p1) {
-#pragma unroll
-              for (int u = 0; u < 8; ++u) {
-                const int j2 = 8 * g0 + u;
-                const float x = PARTS == 2 ? __uint_as_float(sv[u]) + __uint_as_float(sl[u]) : __uint_as_float(sv[u]);
-                if (j2 < p2) out[j2 * p1 + j1] = x;
-              }
-            }
+        for (int g4 = wg; g4 < sh.N3 / 4; g4 += 2) {
+          uint32_t a0[4], a1[4], b0[4], b1[4];
+          umma::ld_x4(tb + lq + sh.c_p + 4u * g4, a0);
+          umma::ld_x4(tb + lq + sh.c_p + sh.pw + 4u * g4, a1);
+          if (PARTS == 2) {
+            umma::ld_x4(tb + lq + sh.c_p + (uint32_t)sh.N2 + 4u * g4, b0);
+            umma::ld_x4(tb + lq + sh.c_p + sh.pw + (uint32_t)sh.N2 + 4u * g4, b1);
           }
-        };
-        if (ok) {
-          if (k > 0 && warp < 2) write_sb(k - 1);
-          for (int g0 = wg; g0 < sh.N3 / 8; g0 += 2) {
-            uint32_t a0[8], a1[8], b0[8], b1[8];
-            umma::ld_x8(tb + lq + sh.c_p + 8u * g0, a0);
-            umma::ld_x8(tb + lq + sh.c_p + sh.pw + 8u * g0, a1);
-            if (PARTS == 2) {
-              umma::ld_x8(tb + lq + sh.c_p + (uint32_t)sh.N2 + 8u * g0, b0);
-              umma::ld_x8(tb + lq + sh.c_p + sh.pw + (uint32_t)sh.N2 + 8u * g0, b1);
-            }
-            umma::wait_ld();
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const int j2 = 8 * g0 + u;
-              float x = __uint_as_float(a0[u]) + __uint_as_float(a1[u]);
-              if (PARTS == 2) x += __uint_as_float(b0[u]) + __uint_as_float(b1[u]);
-              if (FORM == kFormBF16) {
-                if ((c >> 6) >= sh.KA1) continue;  // rows past the last K atom: MMA3 does not read them
-                const uint32_t off =
-                    (uint32_t)((c >> 6) * sh.ptile_atom) + umma::sw128_k2((uint32_t)j2, (uint32_t)(c & 63));
-                *reinterpret_cast<__nv_bfloat16*>(base + sh.o_ptile + off) = __float2bfloat16_rn(x);
-              } else {
-                if (q >= sh.KA1) continue;
-                const uint32_t off = (uint32_t)(q * sh.ptile_atom);
-                const uint32_t h = rna_tf32(x);
-                *reinterpret_cast<uint32_t*>(base + sh.o_ptile + off + umma::sw128_k4((uint32_t)j2, (uint32_t)lane)) = h;
-                if (PARTS == 2)
-                  *reinterpret_cast<uint32_t*>(base + sh.o_ptile + off +
-                                               umma::sw128_k4((uint32_t)(sh.N3 + j2), (uint32_t)lane)) =
-                      rna_tf32(x - __uint_as_float(h));
-              }
-            }
+          umma::wait_ld();
+          umma::ld_done(a0);
+          umma::ld_done(a1);
+          if (PARTS == 2) {
+            umma::ld_done(b0);
+            umma::ld_done(b1);
           }
-          fence_proxy_async();
-          warp_arrive(&bars.pt_ready);
-          if (k == kcta - 1 && warp < 2) {
-            ok = warp_wait(&bars.sb_ready, par, wait_ns);
-            umma::fence_after_sync();
-            if (ok) write_sb(k);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j2 = 4 * g4 + u;
+            float x = __uint_as_float(a0[u]) + __uint_as_float(a1[u]);
+            if (PARTS == 2) x += __uint_as_float(b0[u]) + __uint_as_float(b1[u]);
+            if (FORM == kFormBF16) {
+              if ((c >> 6) >= sh.KA1) continue;  // rows past the last K atom: MMA3 does not read them
+              const uint32_t off =
+                  (uint32_t)((c >> 6) * sh.ptile_atom) + umma::sw128_k2((uint32_t)j2, (uint32_t)(c & 63));
+              *reinterpret_cast<__nv_bfloat16*>(base + sh.o_ptile + off) = __float2bfloat16_rn(x);
+            } else {
+              if (q >= sh.KA1) continue;
+              const uint32_t off = (uint32_t)(q * sh.ptile_atom);
+              const uint32_t h = rna_tf32(x);
+              *reinterpret_cast<uint32_t*>(base + sh.o_ptile + off + umma::sw128_k4((uint32_t)j2, (uint32_t)lane)) = h;
+              if (PARTS == 2)
+                *reinterpret_cast<uint32_t*>(base + sh.o_ptile + off +
+                                             umma::sw128_k4((uint32_t)(sh.N3 + j2), (uint32_t)lane)) =
+                    rna_tf32(x - __uint_as_float(h));
+            }
           }
         }
+        umma::fence_before_sync();
+        fence_proxy_async();
+        warp_arrive(&bars.pt_ready);
       }
       if (!ok) atomicOr(&timed_out, 1);
-      // this issuer's MMAs have completed before the TMEM is released: its last commit was on
-      // eta_ready (slab k + 1's MMA1) or p_ready (slab k's last chunk); each covers all earlier ones
-      if (issuer && committed > 0) {
-        wait_for(&bars.eta_ready[wg], (uint32_t)(((committed + 1) / 2 - 1) & 1), drain_ns);
-        if (committed >= 2) wait_for(&bars.p_ready[wg], (uint32_t)((committed / 2 - 1) & 1), drain_ns);
-      }
-      umma::fence_before_sync();
-      // the constant block's copy has landed before the CTA leaves (at once in a normal run)
-      if (tid == 0) wait_for(&bars.cst, 0u, drain_ns);
+      umma::wait_st();  // after a time-out, r stores may still be in flight
+    }
+    umma::fence_before_sync();
+    // the constant block's copies have landed before the CTA leaves (at once in a normal run)
+    if (tid == 0) {
+      wait_for(&bars.cst, 0u, drain_ns);
+      wait_for(&bars.cst1, 0u, drain_ns);
     }
   }
   __syncthreads();
@@ -713,7 +817,8 @@ bool um_configure(int n1, int n2, int n3, int p1, int p2, int p3, int grid, int 
   s.parts = parts;
   s.K1 = form == kFormBF16 ? (int)up(p2, 16) : (int)up(p2, 8);
   s.N2 = (int)up(p2, 16);
-  s.N3 = (int)up(p2, 8);
+  s.N3 = parts == 2 ? (int)up(p2, 8) : (int)up(p2, 16);  // MMA3 (M = 128) takes N = parts N3, a multiple of 16
+  s.P1P = (int)up(p1, 4);
   const int epr = 128 / esz;
   s.KA1 = (n1 + epr - 1) / epr;
   s.KA2 = (n2 + epr - 1) / epr;
@@ -732,8 +837,6 @@ bool um_configure(int n1, int n2, int n3, int p1, int p2, int p3, int grid, int 
   s.o_x2 = o;
   o += (int64_t)s.KA2 * s.x2_atom;
   s.cst_bytes = o - s.o_cst;
-  // MMA3 reads 64 rows of each 32-row XT1 atom: the last atom's reads run 4 KB past the XT1 parts,
-  // into the X2T tile (n2 >= 32 rows of 128 bytes)
   o = up(o, 1024);
   // the V ring, then the P tile; d is staged for the first H stage in the last bytes of the two
   // (so that the first V chunks, in the first slots, can be in flight while T_a is formed)
@@ -742,7 +845,7 @@ bool um_configure(int n1, int n2, int n3, int p1, int p2, int p3, int grid, int 
   s.ptile_atom = (int64_t)parts * s.N3 * 128;
   const int64_t ptile_bytes = up((int64_t)s.KA1 * s.ptile_atom, 1024);
   const int KQ = (s.kmax + 3) / 4 * 4;
-  const int64_t tas_bytes = up((int64_t)s.kmax * p1 * s.K1 * 4, 16);
+  const int64_t tas_bytes = up(((int64_t)s.kmax * s.P1P * s.K1 + 16) * 4, 16);  // + slack read by MMA0
   const int64_t tail = ptile_bytes + tas_bytes + up((int64_t)p3 * KQ * 4, 16) + up((int64_t)p3 * 4, 16);
   const int64_t room = (int64_t)g_um_budget - 1024 - o - tail;
   int slots = (int)(room / s.slot_bytes);
@@ -761,6 +864,9 @@ bool um_configure(int n1, int n2, int n3, int p1, int p2, int p3, int grid, int 
   s.o_rows = o;
   o += up((int64_t)p3 * 4, 16);
   s.total = up(o, 16);
+  // MMA3 reads 128 rows from each 32-row XT1 atom: the last atom's reads run 12 KB past the XT1
+  // parts, into the tiles after them, which must lie inside the allocation
+  if (s.total < parts * s.xt1_part + 12288) s.total = parts * s.xt1_part + 12288;
   // rows of d per staging round (16-byte aligned round starts when p2 p1 is not a multiple of 4)
   const int64_t P21 = (int64_t)p1 * p2;
   int64_t R = stage_cap / (P21 * 4);
@@ -873,7 +979,7 @@ cudaError_t launch_fused_umma_const(int n1, int n2, int n3, int p1, int p2, int 
 cudaError_t launch_fused_umma(int n1, int n2, int n3, int p1, int p2, int p3, int form, bool v_bf16,
                               const void* Cst, const float* D, const float* X1T, const float* X3T,
                               const void* V, float* Sb, cudaStream_t st, const int* skip, int* err,
-                              uint64_t wait_ns) {
+                              uint64_t wait_ns, bool pdl) {
   UmShape s;
   const int grid = um_grid(n3);
   if (!um_configure(n1, n2, n3, p1, p2, p3, grid, form, v_bf16, s)) return cudaErrorInvalidValue;
@@ -886,18 +992,21 @@ cudaError_t launch_fused_umma(int n1, int n2, int n3, int p1, int p2, int p3, in
   size_t smem = (size_t)s.total + 1024;
   if (smem < g_um_budget / 2 + 1024) smem = g_um_budget / 2 + 1024;
   const unsigned char* c = static_cast<const unsigned char*>(Cst);
+  const dim3 g(grid), b(kUmThreads);
+  cudaError_t e;
   if (form == kFormTF32)
-    fused_slab_umma_kernel<kFormTF32, float><<<grid, kUmThreads, smem, st>>>(s, c, D, X1T, X3T, tmapV, Sb, skip,
-                                                                            err, wait_ns);
+    e = launch_pdl(fused_slab_umma_kernel<kFormTF32, float>, g, b, smem, st, pdl, s, c, D, X1T, X3T, tmapV, Sb,
+                   skip, err, wait_ns);
   else if (form == kForm3x)
-    fused_slab_umma_kernel<kForm3x, float><<<grid, kUmThreads, smem, st>>>(s, c, D, X1T, X3T, tmapV, Sb, skip,
-                                                                          err, wait_ns);
+    e = launch_pdl(fused_slab_umma_kernel<kForm3x, float>, g, b, smem, st, pdl, s, c, D, X1T, X3T, tmapV, Sb,
+                   skip, err, wait_ns);
   else if (v_bf16)
-    fused_slab_umma_kernel<kFormBF16, __nv_bfloat16><<<grid, kUmThreads, smem, st>>>(s, c, D, X1T, X3T, tmapV, Sb,
-                                                                                    skip, err, wait_ns);
+    e = launch_pdl(fused_slab_umma_kernel<kFormBF16, __nv_bfloat16>, g, b, smem, st, pdl, s, c, D, X1T, X3T,
+                   tmapV, Sb, skip, err, wait_ns);
   else
-    fused_slab_umma_kernel<kFormBF16, float><<<grid, kUmThreads, smem, st>>>(s, c, D, X1T, X3T, tmapV, Sb, skip,
-                                                                            err, wait_ns);
+    e = launch_pdl(fused_slab_umma_kernel<kFormBF16, float>, g, b, smem, st, pdl, s, c, D, X1T, X3T, tmapV, Sb,
+                   skip, err, wait_ns);
+  if (e != cudaSuccess) return e;
   count_launches(1);
   return cudaGetLastError();
 }

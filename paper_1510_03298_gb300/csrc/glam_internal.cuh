@@ -15,6 +15,36 @@
 
 namespace glam {
 
+
+// Launches kernel k; with pdl the launch may begin while the preceding kernel of the stream is
+// still running (programmatic dependent launch): k then must execute griddep_wait() before it
+// reads anything that kernel writes or writes anything it reads.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl ? at : nullptr;
+  cfg.numAttrs = pdl ? 1u : 0u;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
+#ifdef __CUDACC__
+// Waits until the preceding kernel of the stream has completed and its writes are visible (at
+// once when this launch was not a programmatic dependent one), then lets the next kernel of the
+// stream begin launching.
+__device__ __forceinline__ void griddep_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+#endif
+
 constexpr int kThreads = 256;
 constexpr int kTrials = 8;          // Armijo trial step sizes evaluated per n-stream pass
 constexpr int kMaxRedBlocks = 1216; // 8 x 152 SMs: upper bound of blocks in a reduction grid
@@ -120,7 +150,10 @@ cudaError_t fused_tc_prepare();
 // = X_3 D is formed in the kernel from the correction D (p3 x p2p1, FP32).  Cst is the constant
 // block (fused_umma_const_bytes bytes, written by launch_fused_umma_const from X_1^T and X_2^T
 // once per set of designs); V is FP32, or BF16 for form 16 with v_bf16.  Every wait of the
-// kernel gives up after wait_ns nanoseconds and sets *err.  fused_umma_supported tells whether
+// kernel gives up after wait_ns nanoseconds and sets *err.  With pdl the launch may overlap the
+// preceding kernel of the stream: the kernel reads D (and writes Sb) only after that kernel has
+// completed, and reads V, X_1, X_3 and the constant block before, so the preceding kernel must not
+// write those.  fused_umma_supported tells whether
 // the shape is in the kernel's domain (n1 <= 128, n1 a multiple of 4 (8 for BF16), n2 a multiple
 // of 32 up to 128 (3xTF32) or 256, p1, p2 <= 32).
 cudaError_t fused_umma_prepare();
@@ -131,7 +164,7 @@ cudaError_t launch_fused_umma_const(int n1, int n2, int n3, int p1, int p2, int 
 cudaError_t launch_fused_umma(int n1, int n2, int n3, int p1, int p2, int p3, int form, bool v_bf16,
                               const void* Cst, const float* D, const float* X1T, const float* X3T,
                               const void* V, float* Sb, cudaStream_t st, const int* skip, int* err,
-                              uint64_t wait_ns);
+                              uint64_t wait_ns, bool pdl = false);
 
 // The last two stages of H for FP32 (modes 1 and 2, Sec. 6.1, Eq. eighteen) in one kernel:
 // eta[i3] = X_2 (T_a[i3] X_1^T) per slab, T_a (n3 x p2p1) from the mode-3 product.
@@ -152,14 +185,16 @@ int encode_map_2d(CUtensorMap* m, const float* base, uint64_t dim0, uint64_t dim
 // Last G stage (mode 3 of Eq. nineteen) and the inner PG step of Sec. 3.2 in one kernel, for the
 // FP32 products of the fit path: Q = X_3^T S_b (p3 x p2p1, every i3 summed in the CTA that owns
 // the entry), then the prox step of launch_prox with lin = g_k, lin_scale = 1 and the anchor
-// theta_k (x, xp, out, gk, pen, anchor FP64; dnext FP32).  adjprox_supported tells whether the
+// theta_k (x, xp, out, gk, pen, anchor FP64; dnext FP32).  With pdl the launch may overlap the
+// preceding kernel of the stream; the kernel touches no memory before that kernel has completed.
+// adjprox_supported tells whether the
 // shape and pointers allow its tensor copies.
 // ------------------------------------------------------------------------------------
 int adjprox_supported(int n3, int p3, int P21, const float* X3T, const float* Sb);
 cudaError_t launch_adjprox(int n3, int p3, int P21, const float* X3T, const float* Sb, const double* gk,
                            const double* x, const double* xp, const double* pen, double* out,
                            float* dnext, const double* anchor, double inv_n, InnerCtl* ctl, int* err,
-                           cudaStream_t s);
+                           cudaStream_t s, bool pdl = false);
 
 // Tensor-product weights (Sec. 6.2, Eq. kronweight): the factors w1 (n1), w2 (n2), w3 (n3) of W
 // read off its first row, column and tube, and check[0] = max |W - w1 w2 w3|, check[1] = max |W|
