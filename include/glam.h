@@ -114,7 +114,15 @@ typedef struct {
                               accepted, for the families whose IRLS weight is the observation weight
                               itself (Gaussian; Gamma with log link) with an observation-weight
                               array W that is a tensor product w1 (x) w2 (x) w3 with W(0,0,0) > 0
-                              (W = 1 included); otherwise glam_fit_path returns GLAM_EINVAL */
+                              (W = 1 included); otherwise glam_fit_path returns GLAM_EINVAL.
+                              GLAM_IWLS_KRON1 / GLAM_IWLS_KRON2 replace the weights V of every outer
+                              iteration by their geometric-mean tensor approximation (Sec. 6.2,
+                              computed as glam_kron_weights does: KRON1 as printed, normalised by the
+                              overall geometric mean; KRON2 with that mean restored) for any family
+                              and W; the inner loop then runs on H(<X_j^T diag(v_j) X_j>, .) with the
+                              exact Lipschitz constant of the approximation, while the gradient, the
+                              line search and the KKT test stay exact, so the solutions are those of
+                              GLAM_IWLS_EXACT (Sec. 5: any positive weights keep the fixed point) */
   int32_t penalty;         /* GLAM_PENALTY_LASSO (default): the weighted l1 penalty of Eq. (five);
                               GLAM_PENALTY_ENET / GLAM_PENALTY_RIDGE: the elastic net and ridge
                               penalties of Sec. 6.3 (below; the KKT residual is then the distance
@@ -135,10 +143,19 @@ typedef struct {
                               runs out makes glam_fit_path return GLAM_ETIMEOUT, and the plan stays
                               usable (default 2, in [0, 3600]; 0 gives up at once unless the awaited
                               data is already there, which tests the error path) */
+  double nu;               /* inner step size relative to the bound L_hat (the package's nu, Sec. 6.4;
+                              default 1, in [0, 1]): nu = 1 takes delta = 1/L_hat and never backtracks;
+                              nu in (0, 1) starts from delta = 1/(nu L_hat), nu = 0 from delta = 1, and
+                              when an inner solve diverges (its step max_m |x+_m - y_m| grows past 10
+                              times its first value, or turns non-finite) the solve restarts from
+                              theta_k with delta halved, but not below 1/L_hat, where it cannot
+                              diverge; the divergence test runs only while delta > 1/L_hat */
 } glam_opts;
 
 #define GLAM_IWLS_EXACT 0
 #define GLAM_IWLS_KRON 1
+#define GLAM_IWLS_KRON1 2  /* geometric-mean tensor approximation of V, as printed (Sec. 6.2) */
+#define GLAM_IWLS_KRON2 3  /* the same times the overall geometric mean of V */
 #define GLAM_PENALTY_LASSO 0
 #define GLAM_PENALTY_SCAD 1
 #define GLAM_PENALTY_ENET 2  /* J = sum w (|theta| + alpha theta^2); prox: soft threshold, then / (1 + 2 alpha gamma) */
@@ -160,6 +177,8 @@ typedef struct {
   int32_t armijo_backtracks;
   int32_t nnz;
   int32_t status;          /* GLAM_OK or GLAM_ENOCONV / GLAM_ENONFINITE for this lambda */
+  int32_t inner_restarts;  /* inner solves restarted with a halved step (opts.nu < 1) */
+  int32_t reserved0;
 } glam_stats;
 
 /* Fill *opts with the defaults listed in glam_opts.  Returns GLAM_EINVAL for NULL. */
@@ -249,6 +268,19 @@ int glam_prox_step(glam_plan* plan, const void* const X[3], const glam_quad* q, 
 int glam_fit_path(glam_plan* plan, const void* const X[3], const void* Y, const void* W,
                   const void* pen_w, int nlambda, double* lambda, const glam_opts* opts,
                   const double* Theta0, double* Theta_path, glam_stats* stats, int* nfit);
+
+/* Geometric-mean tensor approximation of a weight array (Sec. 6.2, "tensor approximation" of the
+ * weights; the iwls options "kron1" and "kron2" of Sec. 6.4): for V (n elements in the plan's
+ * layout, FP64, DEVICE) writes the factors v1 (n1), v2 (n2), v3 (n3) (FP64, DEVICE) with
+ *   v_j(i) = exp( mean over the cells of slice i of mode j of log V  -  mean over all cells of log V ),
+ * so that V_hat(i1, i2, i3) = v1(i1) v2(i2) v3(i3) (the product form of the paper, with the
+ * normalisation by the overall geometric mean V_bar); scaled != 0 multiplies v1 by V_bar, so that
+ * V_hat = V whenever V is a tensor product.  Reading of the paper: the means run over the cells
+ * with V > 0 (a masked cell, weight 0, has no logarithm and carries no weight), and a slice without
+ * such a cell gets the factor 1.  Sums in a fixed order (the same bits on every run).  Stream-
+ * ordered on the plan's stream; uses plan workspace.
+ * Errors: GLAM_EINVAL (NULL argument), GLAM_ENOMEM, GLAM_ECUDA. */
+int glam_kron_weights(glam_plan* plan, const double* V, int scaled, double* v1, double* v2, double* v3);
 
 /* Penalized negative log-likelihood F(Theta) = f(Theta) + lambda sum_m pen_w[m] |theta_m| (the
  * PMLE objective of Sec. 2, Eq. five, scaled by 1/n as stated above) and its vector-Jacobian

@@ -312,6 +312,39 @@ def lipschitz_tensor(Xs, ws, n) -> float:
     return math.prod(float(np.max(np.abs(np.linalg.eigvalsh(M)))) for M in tensor_weight_grams(Xs, ws)) / n
 
 
+def geometric_mean_weights(V, scaled=False):
+    """The tensor approximation of a non-tensor weight array of Sec. 6.2: V_hat = v_1 (x) ... (x) v_d
+    with v_j(i) = exp( (1/m_j) sum over the other indices of log V  -  log V_bar ), V_bar the
+    geometric mean of all of V, i.e. the paper's product of ratios V / V_bar over the slice taken to
+    the power 1/m_j.  V is in paper layout (n1 x ... x nd).  Reading (the paper's V is strictly
+    positive): the means run over the cells with V > 0 only, m_j being their number in the slice
+    (and n their total), and a slice without such a cell gets the factor 1.  scaled=True returns
+    V_bar v_1 in place of v_1 (the iwls option "kron2"; "kron1" is the approximation as printed),
+    so that the product reproduces any positive tensor-product V exactly."""
+    V = np.asarray(V, dtype=np.float64)
+    pos = V > 0
+    logV = np.where(pos, np.log(np.where(pos, V, 1.0)), 0.0)
+    log_bar = float(logV.sum() / pos.sum()) if pos.any() else 0.0
+    out = []
+    for j in range(V.ndim):
+        other = tuple(k for k in range(V.ndim) if k != j)
+        cnt = pos.sum(axis=other)
+        s = logV.sum(axis=other)
+        vj = np.where(cnt > 0, np.exp(np.where(cnt > 0, s / np.maximum(cnt, 1), 0.0) - log_bar), 1.0)
+        out.append(vj)
+    if scaled:
+        out[0] = out[0] * math.exp(log_bar)
+    return out
+
+
+def tensor_array(ws) -> np.ndarray:
+    """w_1 (x) ... (x) w_d as an n1 x ... x nd array (paper layout)."""
+    A = np.asarray(ws[0], dtype=np.float64)
+    for w in ws[1:]:
+        A = np.multiply.outer(A, np.asarray(w, dtype=np.float64))
+    return A
+
+
 # --------------------------------------------------------------------------------------
 # Problem container in paper layout
 # --------------------------------------------------------------------------------------
@@ -462,7 +495,9 @@ def gdpg(data: GlamData, lam, theta0, lmax, tol=1e-9, tol_inner=1e-12, max_outer
          max_inner=100000, alpha0=1.0, b=0.5, v=0.1, max_ls=60, weights="exact"):
     """Algorithm 1 (GD-PG) for one lambda.  weights='exact' uses the IRLS weights of App. B
     (times a, R2); weights='one' uses w_i = a_i (any positive weights keep the fixed point,
-    Sec. 5).  Returns (theta, FitStats)."""
+    Sec. 5); weights='kron1' / 'kron2' use the geometric-mean tensor approximation of the IRLS
+    weights (Sec. 6.2, `geometric_mean_weights`) with z = W^-1 u + eta for those weights (Eq. ten)
+    and the exact Lipschitz constant of tensor-product weights.  Returns (theta, FitStats)."""
     fam = data.family
     n = data.n
     rho_prod = math.prod(spectral_radius_gram(X) for X in data.Xs)
@@ -475,14 +510,21 @@ def gdpg(data: GlamData, lam, theta0, lmax, tol=1e-9, tol_inner=1e-12, max_outer
     for k in range(max_outer):
         # Step 2: U, V and Z at theta(k)
         u = score(fam, eta, data.Y, data.a)
+        Lhat = None
         if weights == "exact":
             w = irls_weight(fam, eta, data.a)
             z = working_response(fam, eta, data.Y, data.a)
+        elif weights in ("kron1", "kron2"):
+            vs = geometric_mean_weights(irls_weight(fam, eta, data.a), scaled=weights == "kron2")
+            w = tensor_array(vs)
+            z = u / w + eta
+            Lhat = lipschitz_tensor(data.Xs, vs, n)
         else:
             w = data.a.astype(np.float64)
             z = np.where(w > 0, u / np.where(w > 0, w, 1.0) + eta, eta)
-        # Step 3: delta = 1 / L_hat (Prop. 1)
-        Lhat = float(np.max(w)) / n * rho_prod
+        # Step 3: delta = 1 / L_hat (Prop. 1; the exact constant for tensor-product weights)
+        if Lhat is None:
+            Lhat = float(np.max(w)) / n * rho_prod
         if Lhat <= 0:
             break
         delta = 1.0 / Lhat

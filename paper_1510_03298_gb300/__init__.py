@@ -62,6 +62,8 @@ GLAM_TF32 = _K["GLAM_TF32"]
 GLAM_BF16 = _K["GLAM_BF16"]
 GLAM_IWLS_EXACT = _K["GLAM_IWLS_EXACT"]
 GLAM_IWLS_KRON = _K["GLAM_IWLS_KRON"]
+GLAM_IWLS_KRON1 = _K["GLAM_IWLS_KRON1"]
+GLAM_IWLS_KRON2 = _K["GLAM_IWLS_KRON2"]
 GLAM_PENALTY_LASSO = _K["GLAM_PENALTY_LASSO"]
 GLAM_PENALTY_SCAD = _K["GLAM_PENALTY_SCAD"]
 GLAM_PENALTY_ENET = _K["GLAM_PENALTY_ENET"]
@@ -82,7 +84,7 @@ class GlamOpts(C.Structure):
                 ("armijo_v", C.c_double), ("max_inner", C.c_int32), ("max_outer", C.c_int32),
                 ("max_linesearch", C.c_int32), ("check_every", C.c_int32), ("iwls", C.c_int32),
                 ("penalty", C.c_int32), ("steps", C.c_int32), ("reserved", C.c_int32 * 3),
-                ("enet_alpha", C.c_double), ("wait_limit_s", C.c_double)]
+                ("enet_alpha", C.c_double), ("wait_limit_s", C.c_double), ("nu", C.c_double)]
 
 
 class GlamBatchItem(C.Structure):
@@ -96,7 +98,7 @@ class GlamStats(C.Structure):
     _fields_ = [("lambda_", C.c_double), ("objective", C.c_double), ("kkt", C.c_double),
                 ("time_ms", C.c_double), ("outer_iters", C.c_int32), ("inner_iters", C.c_int32),
                 ("fp64_passes", C.c_int32), ("armijo_backtracks", C.c_int32), ("nnz", C.c_int32),
-                ("status", C.c_int32)]
+                ("status", C.c_int32), ("inner_restarts", C.c_int32), ("reserved0", C.c_int32)]
 
 
 def library_path() -> str:
@@ -136,6 +138,7 @@ def load_library():
         "glam_fit_path_batched": (C.c_int, [C.c_int, C.POINTER(_VP), C.POINTER(GlamBatchItem),
                                             C.POINTER(GlamOpts), C.c_int]),
         "glam_launch_count": (C.c_int64, []),
+        "glam_kron_weights": (C.c_int, [_VP, _VP, C.c_int, _VP, _VP, _VP]),
         "glam_time_inner_kernels": (C.c_int, [_VP, _X3, C.POINTER(GlamQuadC), C.c_int,
                                               C.POINTER(C.c_double)]),
     }
@@ -390,10 +393,7 @@ def glam_fit_path(plan: Plan, X, Y, W, pen_w, nlambda: int = 10, lambdas=None, o
     msg = msg.decode() if msg else ""
     if status not in (GLAM_OK, GLAM_ENOCONV):
         raise GlamError(status, msg)
-    stats = [dict(lam=s.lambda_, objective=s.objective, kkt=s.kkt, time_ms=s.time_ms,
-                  outer_iters=s.outer_iters, inner_iters=s.inner_iters, fp64_passes=s.fp64_passes,
-                  armijo_backtracks=s.armijo_backtracks, nnz=s.nnz, status=s.status) for s in st]
-    return FitResult(list(lam), path, stats, nfit.value, status, msg)
+    return FitResult(list(lam), path, _stats_list(st), nfit.value, status, msg)
 
 
 def _p64(t, shape, name):
@@ -402,6 +402,20 @@ def _p64(t, shape, name):
     if tuple(t.shape) != tuple(shape) or not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous with shape {tuple(shape)}")
     return t
+
+
+def glam_kron_weights(plan: Plan, V, scaled: bool = False):
+    """Geometric-mean tensor approximation of a weight array (Sec. 6.2): V is a float64 CUDA
+    tensor of the plan's cell shape; returns (v1, v2, v3), float64 CUDA tensors of n1, n2, n3
+    entries, with V_hat(i1, i2, i3) = v1(i1) v2(i2) v3(i3) (scaled: times the overall geometric
+    mean, the iwls option "kron2"; else as printed, "kron1")."""
+    plan._sync_stream()
+    _p64(V, plan.cells_shape(), "V")
+    n = plan.cells_shape()[::-1]
+    vs = [torch.empty(int(n[j]), dtype=torch.float64, device=V.device) for j in range(3)]
+    _check(load_library().glam_kron_weights(plan.handle, _ptr(V), 1 if scaled else 0, _ptr(vs[0]), _ptr(vs[1]),
+                                            _ptr(vs[2])), plan.handle)
+    return tuple(vs)
 
 
 def glam_launch_count() -> int:
@@ -502,7 +516,8 @@ class BatchProblem:
 def _stats_list(st):
     return [dict(lam=s.lambda_, objective=s.objective, kkt=s.kkt, time_ms=s.time_ms,
                  outer_iters=s.outer_iters, inner_iters=s.inner_iters, fp64_passes=s.fp64_passes,
-                 armijo_backtracks=s.armijo_backtracks, nnz=s.nnz, status=s.status) for s in st]
+                 armijo_backtracks=s.armijo_backtracks, nnz=s.nnz, status=s.status,
+                 inner_restarts=s.inner_restarts) for s in st]
 
 
 def glam_fit_path_batched(problems: Sequence[BatchProblem], opts: Optional[GlamOpts] = None,

@@ -180,21 +180,8 @@ adjprox_kernel(APShape sh, const __grid_constant__ CUtensorMap mapS, const __gri
     is_last = (atomicAdd(&ctl->counter, 1u) == gridDim.x - 1);
   }
   __syncthreads();
-  if (is_last && tid == 0) {
-    const double cv = __longlong_as_double((long long)atomicAdd(&ctl->crit_bits, 0ull));
-    ctl->crit = cv;
-    ctl->iters_run += 1;
-    if (cv <= ctl->stop_abs) {
-      ctl->done = 1;
-      ctl->stop_reason = 1;
-    } else if (ctl->l >= ctl->max_iter) {
-      ctl->done = 1;
-      ctl->stop_reason = 2;
-    }
-    ctl->l += 1;
-    ctl->crit_bits = 0ull;
-    ctl->counter = 0u;
-  }
+  if (is_last && tid == 0)
+    ctl_finish_iteration(ctl, __longlong_as_double((long long)atomicAdd(&ctl->crit_bits, 0ull)));
   if (timed_out && tid == 0)  // copies still in flight land before the CTA leaves
     for (int b = 0; b < nfirst; ++b) mbar_wait_bounded(&mbar[b], 0u);
 }

@@ -79,6 +79,7 @@ struct glam_plan {
   double* kgram = nullptr;         // the FP64 weighted Gram matrices, p1^2 + p2^2 + p3^2
   double* pen_base = nullptr;      // the caller's penalty weights during a SCAD fit (p)
   unsigned long long* kcheck = nullptr;
+  double* geo = nullptr;           // scratch of the geometric-mean weight factors
   std::vector<void*> allocs;
 };
 
@@ -387,6 +388,7 @@ int glam_opts_default(glam_opts* o) {
   o->penalty = GLAM_PENALTY_LASSO;
   o->steps = 1;
   o->wait_limit_s = 2.0;
+  o->nu = 1.0;
   return GLAM_OK;
 }
 
@@ -750,10 +752,17 @@ int glam_prox_step(glam_plan* pl, const void* const X[3], const glam_quad* q, co
 // correction and the iteration converges to FP64 accuracy in theta and in the KKT residual.
 namespace {
 
+// Step 3 of Alg. 1 and the package's nu (Sec. 6.4): delta = 1 / L_hat for nu = 1, 1 / (nu L_hat)
+// for nu in (0, 1), 1 for nu = 0; delta_cap > 0 (a restart after divergence) caps it, but not
+// below 1 / L_hat.  Steps larger than 1 / L_hat arm the divergence test of the prox kernels.
 __global__ void ctl_init_kernel(InnerCtl* ctl, const DevScalars* sc, double lambda, double stop_rel,
-                                int max_iter, double l1, double l2) {
+                                int max_iter, double l1, double l2, double nu, double delta_cap) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const double delta = 1.0 / sc->Lhat;  // step 3 of Alg. 1: delta = 1 / L_hat (nu = 1)
+  const double safe = 1.0 / sc->Lhat;
+  double delta = nu >= 1.0 ? safe : (nu > 0.0 ? 1.0 / (nu * sc->Lhat) : 1.0);
+  if (delta_cap > 0.0 && delta > delta_cap) delta = delta_cap > safe ? delta_cap : safe;
+  ctl->div_factor = delta > safe ? kInnerDivFactor : 0.0;
+  ctl->crit_first = 0.0;
   ctl->l = 1;
   ctl->done = 0;
   ctl->max_iter = max_iter;
@@ -773,6 +782,10 @@ __global__ void objective_kernel(DevScalars* sc, double lambda) {
   if (threadIdx.x == 0 && blockIdx.x == 0) sc->F = sc->loss + lambda * sc->pen;
 }
 
+__global__ void set_lhat_kernel(DevScalars* sc, double L) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) sc->Lhat = L;
+}
+
 template <typename T>
 struct Fit {
   glam_plan* pl = nullptr;
@@ -787,6 +800,8 @@ struct Fit {
   cudaGraphExec_t graph = nullptr;
   int64_t graph_kernels = 0;
   bool kron = false;  // inner loop on the tensor-product form H(<M_j>, .) (Sec. 6.2)
+  bool kron_geo = false;  // ... with the M_j of the geometric-mean approximation of V, per pass
+  int restarts = 0;       // inner solves restarted with a halved step (nu < 1), this lambda
   double l1 = 1.0, l2 = 0.0;  // penalty J = sum_m w_m (l1 |theta_m| + l2 theta_m^2) (Sec. 6.3)
   // eta, U, V, the loss and g_k in the plan describe the current theta: set by a full FP64 pass,
   // cleared whenever theta moves (a new lambda starts where the last one stopped, so its first
@@ -799,6 +814,9 @@ struct Fit {
 };
 
 // The FP64 pass at theta (see above).  Fills r (scaled KKT residual), F, nnz.
+template <typename T>
+int kron_refresh_geo(Fit<T>& f);
+
 template <typename T>
 int fp64_pass(Fit<T>& f, double lambda, double& r, double& F, int& nnz, bool& nonfinite) {
   glam_plan* pl = f.pl;
@@ -814,6 +832,7 @@ int fp64_pass(Fit<T>& f, double lambda, double& r, double& F, int& nnz, bool& no
                                   f.rho_prod, pl->sc, pl->red, f.s));
     CKS(op.G(pl->wd.U, pl->gk));
     CK(launch_scale<double>(pl->p, pl->gk, pl->gk, -1.0 / (double)pl->n, f.s));
+    if (f.kron_geo) CKS(kron_refresh_geo<T>(f));
   }
   CK(launch_kkt<double>(pl->p, pl->gk, pl->th, pl->pen, lambda, pl->sc, pl->red, f.s, f.l1, f.l2));
   objective_kernel<<<1, 32, 0, f.s>>>(pl->sc, lambda);
@@ -933,14 +952,14 @@ int capture_chunk(Fit<T>& f) {
 
 // Inner PG loop of Sec. 3.2 from x(0) = x(1) = theta_k; *xout receives the last iterate.
 template <typename T>
-int run_inner(Fit<T>& f, double lambda, double stop_rel, int max_iter, double** xout, int& iters,
-              int& reason) {
+int run_inner_once(Fit<T>& f, double lambda, double stop_rel, int max_iter, double** xout, int& iters,
+                   int& reason, double delta_cap) {
   glam_plan* pl = f.pl;
   CK(cudaMemcpyAsync(pl->x0, pl->th, sizeof(double) * pl->p, cudaMemcpyDeviceToDevice, f.s));
   CK(cudaMemcpyAsync(pl->x1, pl->th, sizeof(double) * pl->p, cudaMemcpyDeviceToDevice, f.s));
   CK(cudaMemsetAsync(work_of<T>(pl).dn, 0, sizeof(T) * pl->p, f.s));  // y(1) - theta_k = 0
   CK(cudaMemsetAsync(&pl->sc->timeout, 0, sizeof(int), f.s));
-  ctl_init_kernel<<<1, 32, 0, f.s>>>(pl->ctl, pl->sc, lambda, stop_rel, max_iter, f.l1, f.l2);
+  ctl_init_kernel<<<1, 32, 0, f.s>>>(pl->ctl, pl->sc, lambda, stop_rel, max_iter, f.l1, f.l2, f.o.nu, delta_cap);
   CK(cudaGetLastError());
   count_launches(1);
   if (f.graph == nullptr) CKS(capture_chunk<T>(f));
@@ -963,6 +982,25 @@ int run_inner(Fit<T>& f, double lambda, double stop_rel, int max_iter, double** 
   iters = pl->h_ctl->iters_run;
   reason = pl->h_ctl->stop_reason;
   *xout = (iters % 2 == 1) ? pl->x1 : pl->x0;
+  return GLAM_OK;
+}
+
+// With nu < 1 a solve that diverges (stop reason 3) starts again from theta_k with the step
+// halved, until it reaches 1 / L_hat (where the test is off); the iterations of the abandoned
+// solves count in iters.
+template <typename T>
+int run_inner(Fit<T>& f, double lambda, double stop_rel, int max_iter, double** xout, int& iters,
+              int& reason) {
+  double cap = 0.0;
+  int total = 0;
+  for (;;) {
+    CKS(run_inner_once<T>(f, lambda, stop_rel, max_iter, xout, iters, reason, cap));
+    total += iters;
+    if (reason != 3) break;
+    f.restarts += 1;
+    cap = 0.5 * f.pl->h_ctl->delta;
+  }
+  iters = total;
   return GLAM_OK;
 }
 
@@ -1024,18 +1062,10 @@ int solve_lambda(Fit<T>& f, double lambda, LamOut& lo) {
   }
 }
 
-// Set-up of the tensor-product form (Sec. 6.2): checks that the weight array of the inner problem
-// is a tensor product (for the Gaussian family it is W itself), forms M_j = X_j^T diag(w_j) X_j in
-// FP64 and in the working precision, and returns prod_j varrho(M_j), which times 1/n is the exact
-// Lipschitz constant of the inner problem (Sec. 5, the case of tensor-product weights).
+// Buffers of the tensor-product form: the factors w_j, the FP64 and working-precision M_j, the
+// p-sized intermediates of H(<M_j>, d), and the scratch of the geometric-mean factors.
 template <typename T>
-int kron_setup(Fit<T>& f, const T* W, double& rho_kron, double& wmax) {
-  glam_plan* pl = f.pl;
-  // the IRLS weight is the observation weight itself for the Gaussian family and for the Gamma
-  // family with log link; for the others it varies with eta and is not a tensor product
-  if (pl->family != GLAM_GAUSSIAN_IDENTITY && pl->family != GLAM_GAMMA_LOG)
-    return fail(pl, GLAM_EINVAL,
-                "iwls = GLAM_IWLS_KRON needs tensor-product IRLS weights: the Gaussian or Gamma family");
+int kron_alloc(glam_plan* pl) {
   Work<T>& w = work_of<T>(pl);
   const int64_t pj[3] = {pl->p1, pl->p2, pl->p3};
   const int64_t nj[3] = {pl->n1, pl->n2, pl->n3};
@@ -1044,25 +1074,24 @@ int kron_setup(Fit<T>& f, const T* W, double& rho_kron, double& wmax) {
     CKS(dalloc(pl, &pl->kgram, pj[0] * pj[0] + pj[1] * pj[1] + pj[2] * pj[2]));
     CKS(dalloc(pl, &pl->kcheck, 2));
   }
+  if (pl->geo == nullptr) CKS(dalloc(pl, &pl->geo, geo_scratch_doubles(nj[0], nj[1], nj[2])));
   if (w.kQ == nullptr) {
     for (int j = 0; j < 3; ++j) CKS(dalloc(pl, &w.Mk[j], pj[j] * pj[j]));
     CKS(dalloc(pl, &w.kTa, pl->p));
     CKS(dalloc(pl, &w.kTb, pl->p));
     CKS(dalloc(pl, &w.kQ, pl->p));
   }
-  CK(launch_kron_factors<T>(pl->n1, pl->n2, pl->n3, W, pl->kfac[0], pl->kfac[1], pl->kfac[2],
-                            pl->kcheck, f.s));
-  unsigned long long chk[2] = {0ull, 0ull};
-  double w000 = 0.0;
-  CK(cudaMemcpyAsync(chk, pl->kcheck, sizeof(chk), cudaMemcpyDeviceToHost, f.s));
-  CK(cudaMemcpyAsync(&w000, f.W64, sizeof(double), cudaMemcpyDeviceToHost, f.s));
-  CK(cudaStreamSynchronize(f.s));
-  double dev_max, w_max;
-  std::memcpy(&dev_max, &chk[0], sizeof(double));
-  std::memcpy(&w_max, &chk[1], sizeof(double));
-  if (!(w000 > 0.0) || !(dev_max <= 1e-6 * w_max))
-    return fail(pl, GLAM_EINVAL, "iwls = GLAM_IWLS_KRON needs W = w1 (x) w2 (x) w3 with W(0,0,0) > 0");
-  wmax = w_max;
+  return GLAM_OK;
+}
+
+// M_j = X_j^T diag(kfac_j) X_j in FP64 and in the working precision, and prod_j varrho(M_j)
+// (host Jacobi on the FP64 matrices; p_j <= 64).
+template <typename T>
+int kron_grams(Fit<T>& f, double& rho_kron) {
+  glam_plan* pl = f.pl;
+  Work<T>& w = work_of<T>(pl);
+  const int64_t pj[3] = {pl->p1, pl->p2, pl->p3};
+  const int64_t nj[3] = {pl->n1, pl->n2, pl->n3};
   rho_kron = 1.0;
   if (kron_product_supported<T>((int)pl->p1, (int)pl->p2, (int)pl->p3))
     CK(kron_product_prepare<T>((int)pl->p1, (int)pl->p2, (int)pl->p3));
@@ -1078,6 +1107,60 @@ int kron_setup(Fit<T>& f, const T* W, double& rho_kron, double& wmax) {
     rho_kron *= jacobi_spectral_radius(M, (int)pj[j]);
     off += pj[j] * pj[j];
   }
+  return GLAM_OK;
+}
+
+// Set-up of the tensor-product form (Sec. 6.2): checks that the weight array of the inner problem
+// is a tensor product (for the Gaussian family it is W itself), forms M_j = X_j^T diag(w_j) X_j in
+// FP64 and in the working precision, and returns prod_j varrho(M_j), which times 1/n is the exact
+// Lipschitz constant of the inner problem (Sec. 5, the case of tensor-product weights).
+template <typename T>
+int kron_setup(Fit<T>& f, const T* W, double& rho_kron, double& wmax) {
+  glam_plan* pl = f.pl;
+  // the IRLS weight is the observation weight itself for the Gaussian family and for the Gamma
+  // family with log link; for the others it varies with eta and is not a tensor product
+  if (pl->family != GLAM_GAUSSIAN_IDENTITY && pl->family != GLAM_GAMMA_LOG)
+    return fail(pl, GLAM_EINVAL,
+                "iwls = GLAM_IWLS_KRON needs tensor-product IRLS weights: the Gaussian or Gamma family");
+  Work<T>& w = work_of<T>(pl);
+  const int64_t nj[3] = {pl->n1, pl->n2, pl->n3};
+  CKS(kron_alloc<T>(pl));
+  CK(launch_kron_factors<T>(pl->n1, pl->n2, pl->n3, W, pl->kfac[0], pl->kfac[1], pl->kfac[2],
+                            pl->kcheck, f.s));
+  unsigned long long chk[2] = {0ull, 0ull};
+  double w000 = 0.0;
+  CK(cudaMemcpyAsync(chk, pl->kcheck, sizeof(chk), cudaMemcpyDeviceToHost, f.s));
+  CK(cudaMemcpyAsync(&w000, f.W64, sizeof(double), cudaMemcpyDeviceToHost, f.s));
+  CK(cudaStreamSynchronize(f.s));
+  double dev_max, w_max;
+  std::memcpy(&dev_max, &chk[0], sizeof(double));
+  std::memcpy(&w_max, &chk[1], sizeof(double));
+  if (!(w000 > 0.0) || !(dev_max <= 1e-6 * w_max))
+    return fail(pl, GLAM_EINVAL, "iwls = GLAM_IWLS_KRON needs W = w1 (x) w2 (x) w3 with W(0,0,0) > 0");
+  wmax = w_max;
+  return kron_grams<T>(f, rho_kron);
+}
+
+// The geometric-mean tensor approximation of this outer iteration's weights V (Sec. 6.2, the
+// iwls options kron1 / kron2): factors v_j from V, M_j = X_j^T diag(v_j) X_j, and the exact
+// Lipschitz constant prod_j varrho(M_j) / n of the approximated problem in place of Prop. 1's
+// bound (the family pass has just written V and L_hat).
+template <typename T>
+int kron_refresh_geo(Fit<T>& f) {
+  glam_plan* pl = f.pl;
+  Work<T>& w = work_of<T>(pl);
+  const int scaled = f.o.iwls == GLAM_IWLS_KRON2 ? 1 : 0;
+  if (pl->Vb != nullptr)
+    CK(launch_geo_factors<__nv_bfloat16>((int)pl->n1, (int)pl->n2, (int)pl->n3, pl->Vb, scaled, pl->geo,
+                                         pl->kfac[0], pl->kfac[1], pl->kfac[2], f.s));
+  else
+    CK(launch_geo_factors<T>((int)pl->n1, (int)pl->n2, (int)pl->n3, w.V, scaled, pl->geo, pl->kfac[0],
+                             pl->kfac[1], pl->kfac[2], f.s));
+  double rho_kron = 1.0;
+  CKS(kron_grams<T>(f, rho_kron));
+  set_lhat_kernel<<<1, 1, 0, f.s>>>(pl->sc, rho_kron / (double)pl->n);
+  CK(cudaGetLastError());
+  count_launches(1);
   return GLAM_OK;
 }
 
@@ -1144,6 +1227,12 @@ int fit_impl(glam_plan* pl, const void* const X[3], const T* Y, const T* W, cons
     if (Xd[2] == nullptr) Xd[2] = pl->wd.one;
     CKS(rho_product_from<double>(pl, Xd, f.s, f.rho_prod));
   }
+  if (o.iwls == GLAM_IWLS_KRON1 || o.iwls == GLAM_IWLS_KRON2) {
+    // the factors, the M_j and L are formed from V in every full FP64 pass
+    CKS(kron_alloc<T>(pl));
+    f.kron = true;
+    f.kron_geo = true;
+  }
   if (o.iwls == GLAM_IWLS_KRON) {
     // the family pass sets L_hat = max(w)/n * rho_prod with w = W here; with rho_prod =
     // prod_j varrho(M_j) / max(W) it is the exact constant prod_j varrho(M_j) / n of
@@ -1185,6 +1274,7 @@ int fit_impl(glam_plan* pl, const void* const X[3], const T* Y, const T* W, cons
   for (int k = 0; k < nlambda; ++k) {
     const auto t0 = std::chrono::steady_clock::now();
     LamOut lo;
+    f.restarts = 0;
     CK(cudaMemsetAsync(&pl->sc->nonfinite, 0, sizeof(int), f.s));
     const int nsteps = scad ? o.steps : 1;
     for (int st = 0; st < nsteps; ++st) {
@@ -1223,6 +1313,8 @@ int fit_impl(glam_plan* pl, const void* const X[3], const T* Y, const T* W, cons
       s.armijo_backtracks = lo.backtracks;
       s.nnz = lo.nnz;
       s.status = lam_status;
+      s.inner_restarts = f.restarts;
+      s.reserved0 = 0;
     }
     if (lam_status != GLAM_OK) {
       status = lam_status;
@@ -1240,6 +1332,15 @@ int fit_impl(glam_plan* pl, const void* const X[3], const T* Y, const T* W, cons
 }
 
 }  // namespace
+
+int glam_kron_weights(glam_plan* pl, const double* V, int scaled, double* v1, double* v2, double* v3) {
+  CKS(check_plan(pl));
+  if (!V || !v1 || !v2 || !v3) return fail(pl, GLAM_EINVAL, "glam_kron_weights: NULL argument");
+  if (pl->geo == nullptr) CKS(dalloc(pl, &pl->geo, geo_scratch_doubles(pl->n1, pl->n2, pl->n3)));
+  CK(launch_geo_factors<double>((int)pl->n1, (int)pl->n2, (int)pl->n3, V, scaled ? 1 : 0, pl->geo, v1, v2, v3,
+                                pl->stream));
+  return GLAM_OK;
+}
 
 int glam_fit_path(glam_plan* pl, const void* const X[3], const void* Y, const void* W,
                   const void* pen_w, int nlambda, double* lambda, const glam_opts* opts,
@@ -1259,7 +1360,7 @@ int glam_fit_path(glam_plan* pl, const void* const X[3], const void* Y, const vo
   if (o.max_inner < 1 || o.max_outer < 1 || o.max_linesearch < 1 || !(o.tol > 0) ||
       !(o.inner_forcing > 0) || !(o.inner_floor > 0) || !(o.armijo_b > 0 && o.armijo_b < 1) ||
       !(o.armijo_v > 0 && o.armijo_v < 1) || !(o.armijo_alpha0 > 0) ||
-      !(o.iwls == GLAM_IWLS_EXACT || o.iwls == GLAM_IWLS_KRON) ||
+      !(o.iwls >= GLAM_IWLS_EXACT && o.iwls <= GLAM_IWLS_KRON2) || !(o.nu >= 0.0 && o.nu <= 1.0) ||
       !(o.penalty >= GLAM_PENALTY_LASSO && o.penalty <= GLAM_PENALTY_RIDGE) || o.steps < 1 ||
       !(o.enet_alpha >= 0.0 && std::isfinite(o.enet_alpha)) ||
       !(o.wait_limit_s >= 0.0 && o.wait_limit_s <= 3600.0))

@@ -411,21 +411,8 @@ prox_kernel(int64_t p, int ksplit, const Tq* __restrict__ Qpart, const TP* __res
   const double bm = block_max(crit);
   if (threadIdx.x == 0) atomicMax(&ctl->crit_bits, (unsigned long long)__double_as_longlong(bm));
   if (last_block(&ctl->counter)) {
-    if (threadIdx.x == 0) {
-      const double c = __longlong_as_double((long long)atomicAdd(&ctl->crit_bits, 0ull));
-      ctl->crit = c;
-      ctl->iters_run += 1;
-      if (c <= ctl->stop_abs) {
-        ctl->done = 1;
-        ctl->stop_reason = 1;
-      } else if (ctl->l >= ctl->max_iter) {
-        ctl->done = 1;
-        ctl->stop_reason = 2;
-      }
-      ctl->l += 1;
-      ctl->crit_bits = 0ull;
-      ctl->counter = 0u;
-    }
+    if (threadIdx.x == 0)
+      ctl_finish_iteration(ctl, __longlong_as_double((long long)atomicAdd(&ctl->crit_bits, 0ull)));
   }
 }
 

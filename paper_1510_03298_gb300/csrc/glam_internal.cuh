@@ -69,7 +69,36 @@ struct InnerCtl {
   double stop_abs;             // stop when max_m |x+_m - y_m| <= stop_abs
   double crit;                 // last criterion value
   double pen_l1, pen_l2;       // penalty J = sum_m w_m (pen_l1 |theta_m| + pen_l2 theta_m^2)
+  double crit_first;           // criterion of the first iteration
+  double div_factor;           // > 0: stop as diverged when crit > div_factor * crit_first
 };
+
+// A step larger than 1 / L_hat (opts.nu < 1) is given up when the step max_m |x+_m - y_m| grows
+// past this multiple of its first value, or is not finite.
+constexpr double kInnerDivFactor = 10.0;
+
+#ifdef __CUDACC__
+// End of an inner iteration, run once by the last block of the prox kernel: the stop criterion
+// (1 converged, 2 iteration cap, 3 diverged) and the advance of the loop state.
+__device__ __forceinline__ void ctl_finish_iteration(InnerCtl* ctl, double c) {
+  ctl->crit = c;
+  ctl->iters_run += 1;
+  if (ctl->l == 1) ctl->crit_first = c;
+  if (c <= ctl->stop_abs) {
+    ctl->done = 1;
+    ctl->stop_reason = 1;
+  } else if (ctl->div_factor > 0.0 && !(c <= ctl->div_factor * ctl->crit_first)) {
+    ctl->done = 1;
+    ctl->stop_reason = 3;
+  } else if (ctl->l >= ctl->max_iter) {
+    ctl->done = 1;
+    ctl->stop_reason = 2;
+  }
+  ctl->l += 1;
+  ctl->crit_bits = 0ull;
+  ctl->counter = 0u;
+}
+#endif
 
 // Scalars produced by reductions and consumed by later kernels (all device-resident).
 struct DevScalars {
@@ -204,6 +233,14 @@ cudaError_t launch_kron_factors(int64_t n1, int64_t n2, int64_t n3, const T* W, 
                                 double* w3, unsigned long long* check, cudaStream_t s);
 cudaError_t launch_weighted_gram(int nj, int pj, const double* XT, const double* w, double* M,
                                  cudaStream_t s);
+// The geometric-mean tensor approximation of a weight array V (C-order (n3, n2, n1), Sec. 6.2):
+// v_j(i) = exp(mean of log V over slice i of mode j - mean of log V over all cells), the means
+// over the cells with V > 0 (1 for a slice with none), summed in a fixed order; scaled != 0
+// multiplies v_1 by the overall geometric mean.  scratch holds geo_scratch_doubles(n1, n2, n3).
+template <typename TV>
+cudaError_t launch_geo_factors(int n1, int n2, int n3, const TV* V, int scaled, double* scratch, double* v1,
+                               double* v2, double* v3, cudaStream_t s);
+int64_t geo_scratch_doubles(int64_t n1, int64_t n2, int64_t n3);
 // Q = H(<M_j>, d) on p-sized arrays in one launch (one CTA per slab j3, d staged in shared memory);
 // supported when d and the M_j fit in shared memory; kron_product_prepare sets the kernel's
 // shared-memory limit (call it outside any stream capture, before the first launch).

@@ -3,6 +3,8 @@
 // only the p_j x p_j matrices M_j = X_j^T diag(w_j) X_j and p-sized arrays.  These kernels find
 // the factors of W (and check that W is one), form the M_j in FP64, and apply H(<M_j>, d) to the
 // correction of every inner iteration in one launch.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 
 #include "glam_internal.cuh"
@@ -125,6 +127,92 @@ size_t kron_product_smem(int p1, int p2, int p3) {
   return sizeof(T) * (size_t)((P + 3) / 4 * 4 + 2 * P21 + (int64_t)p1 * p1 + (int64_t)p2 * p2 + p3);
 }
 
+// ---- geometric-mean tensor approximation of a weight array V (Sec. 6.2, "tensor approximation")
+// v_j(i) = exp(mean of log V over the cells of slice i of mode j - mean of log V over all cells),
+// the means taken over the cells with V > 0 (a masked cell carries no weight to approximate).
+// Pass 1: CTA i3 sums log V over its slab per i1 (over i2) and per i2 (over i1), with counts, in
+// a fixed order.  V is C-order (n3, n2, n1).
+template <typename TV>
+__device__ __forceinline__ double geo_log(TV v, int& cnt) {
+  const double x = (double)v;
+  if (x > 0.0) {
+    ++cnt;
+    return log(x);
+  }
+  return 0.0;
+}
+template <typename TV>
+__global__ void geo_slab_kernel(int n1, int n2, const TV* __restrict__ V, double* __restrict__ s1p,
+                                int* __restrict__ c1p, double* __restrict__ s2p, int* __restrict__ c2p) {
+  const int i3 = blockIdx.x;
+  const TV* Vs = V + (int64_t)i3 * n1 * n2;
+  for (int i1 = threadIdx.x; i1 < n1; i1 += blockDim.x) {  // per i1: over i2 in order
+    double s = 0.0;
+    int c = 0;
+    for (int i2 = 0; i2 < n2; ++i2) s += geo_log(Vs[(int64_t)i2 * n1 + i1], c);
+    s1p[(int64_t)i3 * n1 + i1] = s;
+    c1p[(int64_t)i3 * n1 + i1] = c;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i2 = warp; i2 < n2; i2 += nw) {  // per i2: lane-strided over i1, then a fixed tree
+    double s = 0.0;
+    int c = 0;
+    for (int i1 = lane; i1 < n1; i1 += 32) s += geo_log(Vs[(int64_t)i2 * n1 + i1], c);
+    for (int o = 16; o > 0; o >>= 1) {
+      s += __shfl_xor_sync(0xffffffffu, s, o);
+      c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if (lane == 0) {
+      s2p[(int64_t)i3 * n2 + i2] = s;
+      c2p[(int64_t)i3 * n2 + i2] = c;
+    }
+  }
+}
+// Pass 2: per index of each mode, the sum of the slab partials in slab order (mode 3: of its own
+// slab's per-i2 partials in i2 order); sums go to s[n1 + n2 + n3], counts to c[...].
+__global__ void geo_mode_kernel(int n1, int n2, int n3, const double* __restrict__ s1p, const int* __restrict__ c1p,
+                                const double* __restrict__ s2p, const int* __restrict__ c2p,
+                                double* __restrict__ s, int* __restrict__ c) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  double a = 0.0;
+  int k = 0;
+  if (t < n1) {
+    for (int i3 = 0; i3 < n3; ++i3) a += s1p[(int64_t)i3 * n1 + t], k += c1p[(int64_t)i3 * n1 + t];
+  } else if (t < n1 + n2) {
+    const int i2 = t - n1;
+    for (int i3 = 0; i3 < n3; ++i3) a += s2p[(int64_t)i3 * n2 + i2], k += c2p[(int64_t)i3 * n2 + i2];
+  } else if (t < n1 + n2 + n3) {
+    const int i3 = t - n1 - n2;
+    for (int i2 = 0; i2 < n2; ++i2) a += s2p[(int64_t)i3 * n2 + i2], k += c2p[(int64_t)i3 * n2 + i2];
+  } else {
+    return;
+  }
+  s[t] = a;
+  c[t] = k;
+}
+// Pass 3 (one CTA): the overall mean of log V (the slab sums in slab order), then the factors;
+// a slice without a positive cell gets the neutral factor 1.  scaled multiplies v_1 by the
+// overall geometric mean, so that the product reproduces a tensor-product V exactly.
+__global__ void geo_factor_kernel(int n1, int n2, int n3, const double* __restrict__ s, const int* __restrict__ c,
+                                  int scaled, double* __restrict__ v1, double* __restrict__ v2,
+                                  double* __restrict__ v3) {
+  __shared__ double mean_all;
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    long long k = 0;
+    for (int i3 = 0; i3 < n3; ++i3) a += s[n1 + n2 + i3], k += c[n1 + n2 + i3];
+    mean_all = k > 0 ? a / (double)k : 0.0;
+  }
+  __syncthreads();
+  const double lm = mean_all;
+  for (int t = threadIdx.x; t < n1 + n2 + n3; t += blockDim.x) {
+    const double f = c[t] > 0 ? exp(s[t] / (double)c[t] - lm) : 1.0;
+    if (t < n1) v1[t] = scaled ? f * exp(lm) : f;
+    else if (t < n1 + n2) v2[t - n1] = f;
+    else v3[t - n1 - n2] = f;
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -183,6 +271,33 @@ cudaError_t launch_weighted_gram(int nj, int pj, const double* XT, const double*
   count_launches(1);
   return cudaGetLastError();
 }
+
+template <typename TV>
+cudaError_t launch_geo_factors(int n1, int n2, int n3, const TV* V, int scaled, double* scratch, double* v1,
+                               double* v2, double* v3, cudaStream_t s) {
+  // scratch: (n1 + n2) n3 doubles and as many ints, then n1 + n2 + n3 doubles and ints
+  double* s1p = scratch;
+  double* s2p = s1p + (int64_t)n1 * n3;
+  int* c1p = reinterpret_cast<int*>(s2p + (int64_t)n2 * n3);
+  int* c2p = c1p + (int64_t)n1 * n3;
+  double* sm = reinterpret_cast<double*>(c2p + (int64_t)n2 * n3 + ((int64_t)(n1 + n2) * n3 % 2));
+  int* cm = reinterpret_cast<int*>(sm + n1 + n2 + n3);
+  geo_slab_kernel<TV><<<n3, 256, 0, s>>>(n1, n2, V, s1p, c1p, s2p, c2p);
+  const int m = n1 + n2 + n3;
+  geo_mode_kernel<<<(m + 127) / 128, 128, 0, s>>>(n1, n2, n3, s1p, c1p, s2p, c2p, sm, cm);
+  geo_factor_kernel<<<1, 256, 0, s>>>(n1, n2, n3, sm, cm, scaled, v1, v2, v3);
+  count_launches(3);
+  return cudaGetLastError();
+}
+int64_t geo_scratch_doubles(int64_t n1, int64_t n2, int64_t n3) {
+  return (n1 + n2) * n3 * 2 + 1 + (n1 + n2 + n3) * 2;
+}
+template cudaError_t launch_geo_factors<float>(int, int, int, const float*, int, double*, double*, double*,
+                                               double*, cudaStream_t);
+template cudaError_t launch_geo_factors<double>(int, int, int, const double*, int, double*, double*, double*,
+                                                double*, cudaStream_t);
+template cudaError_t launch_geo_factors<__nv_bfloat16>(int, int, int, const __nv_bfloat16*, int, double*,
+                                                       double*, double*, double*, cudaStream_t);
 
 template cudaError_t launch_kron_factors<float>(int64_t, int64_t, int64_t, const float*, double*, double*,
                                                 double*, unsigned long long*, cudaStream_t);
