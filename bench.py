@@ -335,7 +335,7 @@ def run_ours(args):
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of each fused slab kernel on this
 # workload, from an ncu capture (cold cache) of the current kernels (None: not captured since the
 # kernel last changed)
-NCU_TRAFFIC_BYTES = {"3xtf32": None, "tf32": None, "bf16": None}
+NCU_TRAFFIC_BYTES = {"3xtf32": 39764736, "tf32": 39698432, "bf16": 20022272}
 
 
 def measure_details(g, torch, pr, plan, X, Y, W, pen, opts, dev, flush, last):
@@ -673,7 +673,7 @@ def run_kernels(reps, precision="fp32"):
         gb.build()
     pr = gen.make_workload(1)
     f32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
-    plan = g.Plan(pr.n, pr.p, pr.family, g.GLAM_TF32 if precision == "tf32" else g.GLAM_FP32)
+    plan = g.Plan(pr.n, pr.p, pr.family, {"tf32": g.GLAM_TF32, "bf16": g.GLAM_BF16}.get(precision, g.GLAM_FP32))
     X = [f32(x) for x in pr.XT]
     theta = f32(0.01 * np.random.default_rng(0).standard_normal((pr.p[2], pr.p[1], pr.p[0])))
     q = g.glam_quad_build(plan, X, theta, f32(pr.Y), f32(pr.W))
@@ -728,7 +728,7 @@ def main():
                     help="fits of its sequential plain-FP32-path baseline")
     ap.add_argument("--kernels", type=int, default=0, metavar="REPS",
                     help="diagnostic: launch the inner-iteration kernels REPS times for a profiler")
-    ap.add_argument("--kernels-precision", choices=["fp32", "tf32"], default="fp32",
+    ap.add_argument("--kernels-precision", choices=["fp32", "tf32", "bf16"], default="fp32",
                     help="plan precision of the --kernels diagnostic")
     ap.add_argument("--predict", type=int, default=0, metavar="REPS",
                     help="diagnostic: run glam_predict REPS times for a profiler")
