@@ -207,6 +207,24 @@ int glam_opts_default(glam_opts* opts);
  * current device.  *out receives the plan.  Allocates the workspace on the current device. */
 int glam_plan_create(const glam_dims* dims, int family, int precision, void* stream, glam_plan** out);
 
+/* Create a plan for the model with c components (Sec. 2, Eq. fivenew: X = [X_1 | ... | X_c], each
+ * X_r = X_r3 (x) X_r2 (x) X_r1 with its own marginal designs and parameter array Theta_r):
+ *   eta = sum_r H(<X_rj>, Theta_r)          (Sec. 6.1, Eq. eighteen with r = 1..c),
+ *   G(U) = (G(<X_1j>, U), ..., G(<X_cj>, U))  (Eq. nineteen),
+ * and, in glam_fit_path, the Prop. 1 bound L_hat = max(w)/n sum_r prod_j varrho(X_rj^T X_rj)
+ * (Eq. nineteennew).  d: 2 or 3; n: the shared grid (n3 = 1 when d = 2); c in [1, 8]; p: HOST array
+ * of 3c sizes, (p_r1, p_r2, p_r3) of component r at 3r (p_r3 = 1 when d = 2).  The coefficient
+ * vector of such a plan is the concatenation (vec Theta_1, ..., vec Theta_c) of p = sum_r p_r1 p_r2
+ * p_r3 entries, each vec in the layout of a one-component plan (p_r1 fastest), and every X
+ * argument is a HOST array of 3c device pointers, X_r1, X_r2, X_r3 of component r at 3r.  Such a
+ * plan serves glam_predict, glam_gradient, glam_loss and glam_fit_path (iwls GLAM_IWLS_EXACT; the
+ * inner-loop product then runs as the sum of the components' mode products in the plan's
+ * precision, not the fused kernels); glam_quad_build, glam_prox_step, glam_penalized_nll,
+ * glam_time_inner_kernels and glam_fit_path_batched return GLAM_EINVAL for it.  c = 1 gives
+ * the plan of glam_plan_create.  The other arguments and errors are those of glam_plan_create. */
+int glam_plan_create_components(int d, const int64_t n[3], int c, const int64_t* p, int family, int precision,
+                                void* stream, glam_plan** out);
+
 /* Release the plan and its workspace (synchronizes its stream first).  NULL is a no-op. */
 int glam_plan_destroy(glam_plan* plan);
 

@@ -9,7 +9,9 @@ It is plain, slow, obviously-correct float64 numpy, written in the paper's notat
 models"):
   * arrays are indexed as in the paper, A[i1, i2, ..., id], and flattened by `vec`
     (App. A, Eq. index: column-major, i1 fastest);
-  * rho, H and G follow App. A and Eqs. (eighteen)/(nineteen) of Sec. 6.1, with c = 1;
+  * rho, H and G follow App. A and Eqs. (eighteen)/(nineteen) of Sec. 6.1, for one component or
+    c > 1 components (GlamData.comps: eta = sum_r H(<X_rj>, Theta_r), theta the concatenation of
+    the vec Theta_r, Prop. 1 with the sum over r);
   * the family quantities follow App. B, Eqs. (four), (weights)/(nine) and (tennew);
   * the inner PG (FISTA) loop follows Sec. 3.2 with h and grad h of Eqs.
     (twentyfour)/(twentyfive); the step size is Prop. 1 (Eq. nineteennew);
@@ -371,13 +373,54 @@ class GlamData:
     l1: float = 1.0   # penalty J = sum omega (l1 |theta| + l2 theta^2), see `penalty`
     l2: float = 0.0
 
+    comps: Optional[List[List[np.ndarray]]] = None  # c > 1: the c marginal design lists (Xs unused)
+
     @property
     def n(self) -> int:
         return int(self.Y.size)
 
     @property
     def pshape(self):
+        if self.comps is not None:
+            return (sum(math.prod(X.shape[1] for X in Xr) for Xr in self.comps),)
         return tuple(X.shape[1] for X in self.Xs)
+
+    def H(self, theta) -> np.ndarray:
+        """The linear predictor: H(<X_j>, Theta) (Eq. eighteen); with c > 1 components
+        sum_r H(<X_rj>, Theta_r), theta the concatenation (vec Theta_1, ..., vec Theta_c)."""
+        if self.comps is None:
+            return H(self.Xs, theta)
+        eta = np.zeros(self.Y.shape)
+        off = 0
+        for Xr in self.comps:
+            pr = tuple(X.shape[1] for X in Xr)
+            k = math.prod(pr)
+            eta = eta + H(Xr, unvec(theta[off:off + k], pr))
+            off += k
+        return eta
+
+    def G(self, U) -> np.ndarray:
+        """X^T U: G(<X_j>, U) (Eq. nineteen); with c > 1 components the concatenation of the
+        components' vec G(<X_rj>, U)."""
+        if self.comps is None:
+            return G(self.Xs, U)
+        return np.concatenate([vec(G(Xr, U)) for Xr in self.comps])
+
+    def rho_sum(self) -> float:
+        """sum over the components of prod_j varrho(X_rj^T X_rj), the factor of Prop. 1 (Eq.
+        nineteennew)."""
+        comps = self.comps if self.comps is not None else [self.Xs]
+        return float(sum(math.prod(spectral_radius_gram(X) for X in Xr) for Xr in comps))
+
+    @classmethod
+    def from_c_components(cls, family, XTs, Y, W, pen_w):
+        """The model with c components from the library's layout: XTs[r][j] is (p_rj, n_j), Y/W
+        (n3, n2, n1), pen_w the flat concatenation of the components' (p_r3, p_r2, p_r1) arrays."""
+        comps = [[np.asarray(x, dtype=np.float64).T for x in XT] for XT in XTs]
+        return cls(int(family), comps[0], paper_array(Y), paper_array(W),
+                   np.concatenate([vec(paper_array(np.asarray(pw, dtype=np.float64))) for pw in pen_w])
+                   if isinstance(pen_w, (list, tuple)) else np.asarray(pen_w, dtype=np.float64),
+                   comps=comps)
 
     @classmethod
     def from_c(cls, family, XT, Y, W, pen_w):
@@ -389,15 +432,15 @@ class GlamData:
 
 def objective(data: GlamData, theta, lam) -> float:
     """F(theta) = f(eta(theta)) + lambda J(theta), Eq. (five) with the 1/n scaling of R1."""
-    eta = H(data.Xs, theta)
+    eta = data.H(theta)
     return loss(data.family, eta, data.Y, data.a) + lam * penalty(theta, data.pen_w, data.l1, data.l2)
 
 
 def gradient(data: GlamData, theta) -> np.ndarray:
     """grad f(theta) = -(1/n) X^T u(eta(theta)) (Eq. three), via G (Eq. nineteen)."""
-    eta = H(data.Xs, theta)
+    eta = data.H(theta)
     u = score(data.family, eta, data.Y, data.a)
-    return -G(data.Xs, u) / data.n
+    return -data.G(u) / data.n
 
 
 def penalized_gradient(data: GlamData, theta, lam) -> np.ndarray:
@@ -454,7 +497,7 @@ def inner_pg(data: GlamData, V, Z, theta0, delta, lam, tol=1e-12, max_iter=10000
     x(l+1) = prox_{delta lambda}(y - delta grad h(y)) with grad h(y) = (1/n) X^T W (X y - z),
     evaluated as (G(V (.) H(y)) - G(V (.) Z)) / n (Eqs. twentyeight and twentysixnew)."""
     n = data.n
-    b = G(data.Xs, V * Z)
+    b = data.G(V * Z)
     x_prev = np.array(theta0, dtype=np.float64)
     x = x_prev.copy()
     hist = [x.copy()] if keep_history else None
@@ -464,7 +507,7 @@ def inner_pg(data: GlamData, V, Z, theta0, delta, lam, tol=1e-12, max_iter=10000
         it = l
         omega = (l - 1.0) / (l + 2.0)
         y = x + omega * (x - x_prev)
-        grad_h = (G(data.Xs, V * H(data.Xs, y)) - b) / n
+        grad_h = (data.G(V * data.H(y)) - b) / n
         x_new = penalty_prox(y - delta * grad_h, gam, data.l1, data.l2)
         step = float(np.max(np.abs(x_new - x))) if x.size else 0.0
         scale = max(1.0, float(np.max(np.abs(x))) if x.size else 0.0)
@@ -500,10 +543,10 @@ def gdpg(data: GlamData, lam, theta0, lmax, tol=1e-9, tol_inner=1e-12, max_outer
     and the exact Lipschitz constant of tensor-product weights.  Returns (theta, FitStats)."""
     fam = data.family
     n = data.n
-    rho_prod = math.prod(spectral_radius_gram(X) for X in data.Xs)
+    rho_prod = data.rho_sum()
     theta = np.array(theta0, dtype=np.float64)
     st = FitStats()
-    eta = H(data.Xs, theta)
+    eta = data.H(theta)
     J = lambda t: penalty(t, data.pen_w, data.l1, data.l2)
     F = loss(fam, eta, data.Y, data.a) + lam * J(theta)
     st.objective_trace.append(F)
@@ -534,13 +577,13 @@ def gdpg(data: GlamData, lam, theta0, lmax, tol=1e-9, tol_inner=1e-12, max_outer
         theta_t = inner.x
         # Step 5: Armijo line search along d = theta~ - theta
         d = theta_t - theta
-        eta_t = H(data.Xs, theta_t)
+        eta_t = data.H(theta_t)
         Delta = -float(np.sum(u * (eta_t - eta))) / n + lam * (J(theta_t) - J(theta))
         alpha = alpha0
         accepted = False
         for j in range(max_ls):
             th = theta + alpha * d
-            eta_j = H(data.Xs, th)
+            eta_j = data.H(th)
             F_j = loss(fam, eta_j, data.Y, data.a) + lam * J(th)
             if F_j <= F + alpha * v * Delta:
                 accepted = True
@@ -591,7 +634,7 @@ def msa_scad(data: GlamData, lam, theta0, lmax, steps, a=SCAD_A, **kw):
     for s in range(steps):
         if s > 0:
             w = data.pen_w * scad_derivative(theta, lam, a) / lam
-        ds = GlamData(data.family, data.Xs, data.Y, data.a, w)
+        ds = GlamData(data.family, data.Xs, data.Y, data.a, w, comps=data.comps)
         theta, st = gdpg(ds, lam, theta, lmax, **kw)
     return theta, st, w
 

@@ -108,6 +108,7 @@ def library_path() -> str:
 _LIB = None
 _VP = C.c_void_p
 _X3 = C.c_void_p * 3
+_XP = C.POINTER(C.c_void_p)  # 3 design pointers per component
 
 
 def load_library():
@@ -122,24 +123,26 @@ def load_library():
     sig = {
         "glam_opts_default": (C.c_int, [C.POINTER(GlamOpts)]),
         "glam_plan_create": (C.c_int, [C.POINTER(GlamDims), C.c_int, C.c_int, _VP, C.POINTER(_VP)]),
+        "glam_plan_create_components": (C.c_int, [C.c_int, C.POINTER(C.c_int64), C.c_int, C.POINTER(C.c_int64),
+                                                  C.c_int, C.c_int, _VP, C.POINTER(_VP)]),
         "glam_plan_destroy": (C.c_int, [_VP]),
         "glam_plan_set_stream": (C.c_int, [_VP, _VP]),
         "glam_last_error": (C.c_char_p, [_VP]),
-        "glam_predict": (C.c_int, [_VP, _X3, _VP, _VP]),
-        "glam_gradient": (C.c_int, [_VP, _X3, _VP, _VP, _VP, _VP, _VP]),
-        "glam_loss": (C.c_int, [_VP, _X3, _VP, _VP, _VP, _VP]),
-        "glam_quad_build": (C.c_int, [_VP, _X3, _VP, _VP, _VP, C.POINTER(GlamQuadC)]),
-        "glam_prox_step": (C.c_int, [_VP, _X3, C.POINTER(GlamQuadC), _VP, _VP, C.c_double, C.c_double,
+        "glam_predict": (C.c_int, [_VP, _XP, _VP, _VP]),
+        "glam_gradient": (C.c_int, [_VP, _XP, _VP, _VP, _VP, _VP, _VP]),
+        "glam_loss": (C.c_int, [_VP, _XP, _VP, _VP, _VP, _VP]),
+        "glam_quad_build": (C.c_int, [_VP, _XP, _VP, _VP, _VP, C.POINTER(GlamQuadC)]),
+        "glam_prox_step": (C.c_int, [_VP, _XP, C.POINTER(GlamQuadC), _VP, _VP, C.c_double, C.c_double,
                                      C.c_double, _VP, _VP]),
-        "glam_fit_path": (C.c_int, [_VP, _X3, _VP, _VP, _VP, C.c_int, C.POINTER(C.c_double),
+        "glam_fit_path": (C.c_int, [_VP, _XP, _VP, _VP, _VP, C.c_int, C.POINTER(C.c_double),
                                     C.POINTER(GlamOpts), _VP, _VP, C.POINTER(GlamStats),
                                     C.POINTER(C.c_int)]),
-        "glam_penalized_nll": (C.c_int, [_VP, _X3, _VP, _VP, _VP, C.c_double, _VP, _VP, _VP, _VP, _VP]),
+        "glam_penalized_nll": (C.c_int, [_VP, _XP, _VP, _VP, _VP, C.c_double, _VP, _VP, _VP, _VP, _VP]),
         "glam_fit_path_batched": (C.c_int, [C.c_int, C.POINTER(_VP), C.POINTER(GlamBatchItem),
                                             C.POINTER(GlamOpts), C.c_int]),
         "glam_launch_count": (C.c_int64, []),
         "glam_kron_weights": (C.c_int, [_VP, _VP, C.c_int, _VP, _VP, _VP]),
-        "glam_time_inner_kernels": (C.c_int, [_VP, _X3, C.POINTER(GlamQuadC), C.c_int,
+        "glam_time_inner_kernels": (C.c_int, [_VP, _XP, C.POINTER(GlamQuadC), C.c_int,
                                               C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
@@ -258,6 +261,56 @@ class Plan:
 
     def coef_shape(self):
         return (self.p[2], self.p[1], self.p[0])
+
+
+class PlanC(Plan):
+    """A plan for the model with c components (Sec. 2, Eq. fivenew): eta = sum_r H(<X_rj>, Theta_r).
+    ps lists the c parameter shapes (p_r1, p_r2, p_r3) (two entries each for a 2-D GLAM).  The
+    coefficients are the concatenation (vec Theta_1, ..., vec Theta_c), a 1-D tensor of
+    sum_r p_r1 p_r2 p_r3 entries, and X is a sequence of c design triples."""
+
+    def __init__(self, n: Sequence[int], ps: Sequence[Sequence[int]], family: int, precision: int,
+                 stream: Optional[torch.cuda.Stream] = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libglam needs a CUDA device; no CPU fallback exists")
+        lib = load_library()
+        n = tuple(int(v) for v in n)
+        ps = [tuple(int(v) for v in p) for p in ps]
+        d = 3
+        if len(n) == 2:
+            n, ps, d = n + (1,), [p + (1,) for p in ps], 2
+        self.n, self.ps, self.p = n, ps, ps[0]
+        self.family, self.precision = family, precision
+        self.dtype = torch.float64 if precision == GLAM_FP64 else torch.float32
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        flat = (C.c_int64 * (3 * len(ps)))(*[v for p in ps for v in p])
+        h = _VP()
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        _check(lib.glam_plan_create_components(d, (C.c_int64 * 3)(*n), len(ps), flat, family, precision, _VP(s),
+                                               C.byref(h)), None)
+        self._h = h
+
+    @property
+    def ncoef(self) -> int:
+        return sum(p[0] * p[1] * p[2] for p in self.ps)
+
+    def coef_shape(self):
+        return (self.ncoef,)
+
+    def _X(self, X):
+        if len(X) != len(self.ps):
+            raise ValueError(f"X must hold {len(self.ps)} design triples")
+        ptrs = []
+        for r, Xr in enumerate(X):
+            if len(Xr) != 3:
+                raise ValueError("each component needs three marginal designs (the third may be None for d = 2)")
+            for j in range(3):
+                if Xr[j] is None:
+                    ptrs.append(None)
+                    continue
+                self._arr(Xr[j], (self.ps[r][j], self.n[j]), f"X[{r}][{j}]")
+                ptrs.append(Xr[j].data_ptr())
+        return (C.c_void_p * len(ptrs))(*ptrs)
 
 
 def glam_plan_create(n, p, family, precision=GLAM_FP32, stream=None) -> Plan:

@@ -43,8 +43,16 @@ struct Work {
 
 }  // namespace
 
+constexpr int kMaxComp = 8;  // components of a plan of the model with c > 1 (Eq. fivenew), at most
+
 struct glam_plan {
   int device = 0;
+  // c > 1 components: the transforms of component r run on the single-component plan sub[r]
+  // (its own workspace); this plan holds the n-space arrays and the concatenated p-space state,
+  // component r's coefficients at [poff[r], poff[r + 1])
+  int nc = 1;
+  glam_plan* sub[kMaxComp] = {};
+  int64_t poff[kMaxComp + 1] = {};
   cudaStream_t stream = nullptr;   // caller's stream
   cudaStream_t work = nullptr;     // private stream (graph capture needs a capturable stream)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -190,16 +198,30 @@ struct Ops {
   glam_plan* pl;
   Work<T>& w;
   cudaStream_t s;
-  const T* X[3];
+  const T* X[3 * kMaxComp];  // 3 designs per component
 
   Ops(glam_plan* p, cudaStream_t st, const void* const Xin[3])
       : pl(p), w(work_of<T>(p)), s(st) {
-    for (int j = 0; j < 3; ++j) X[j] = static_cast<const T*>(Xin[j]);
-    if (X[2] == nullptr) X[2] = w.one;
+    for (int r = 0; r < pl->nc; ++r) {
+      for (int j = 0; j < 3; ++j) X[3 * r + j] = static_cast<const T*>(Xin[3 * r + j]);
+      if (X[3 * r + 2] == nullptr) X[3 * r + 2] = pl->nc > 1 ? work_of<T>(pl->sub[r]).one : w.one;
+    }
   }
+  // the transforms of component r (c > 1): its own plan, designs and workspace
+  Ops sub(int r) const { return Ops(pl->sub[r], s, reinterpret_cast<const void* const*>(X + 3 * r)); }
 
-  // eta = H(<X_j>, Theta)   (Sec. 6.1, Eq. eighteen)
+  // eta = H(<X_j>, Theta)   (Sec. 6.1, Eq. eighteen); c > 1: the sum over the components, each
+  // component's term formed in its own plan's n-array and added
   int H(const T* theta, T* eta) {
+    if (pl->nc > 1) {
+      for (int r = 0; r < pl->nc; ++r) {
+        Ops o = sub(r);
+        T* dst = r == 0 ? eta : o.w.eta;
+        CKS(o.H(theta + pl->poff[r], dst));
+        if (r > 0) CK(launch_add<T>(pl->n, dst, eta, nullptr, s));
+      }
+      return GLAM_OK;
+    }
     if constexpr (sizeof(T) == 4) {
       if (predict_tiles_supported((int)pl->p1, (int)pl->p2) && mode3_rows_supported((int)pl->p3)) {
         CK(launch_mode3_rows((int)pl->n3, (int)pl->p3, (int)(pl->p2 * pl->p1), X[2], theta, w.Ta, s));
@@ -213,8 +235,12 @@ struct Ops {
     CK(launch_gemm<T, T>(d_mode2_fwd(pl), X[1], w.Tb, eta, s));
     return GLAM_OK;
   }
-  // out = G(<X_j>, U)   (Sec. 6.1, Eq. nineteen)
+  // out = G(<X_j>, U)   (Sec. 6.1, Eq. nineteen); c > 1: component r's block at poff[r]
   int G(const T* U, T* out) {
+    if (pl->nc > 1) {
+      for (int r = 0; r < pl->nc; ++r) CKS(sub(r).G(U, out + pl->poff[r]));
+      return GLAM_OK;
+    }
     CK(launch_gemm<T, T>(d_mode2_adj(pl), X[1], U, w.Tb, s));
     CK(launch_gemm<T, T>(d_mode1_adj(pl), w.Tb, X[0], w.Sb, s));
     if (pl->ksplit > 1) {
@@ -228,6 +254,15 @@ struct Ops {
   // eta = H(<X_j>, x - sub) for a parameter array held in TB (the correction of a refinement)
   template <typename TB>
   int H_diff(const TB* x, const TB* sub, T* eta) {
+    if (pl->nc > 1) {
+      for (int r = 0; r < pl->nc; ++r) {
+        Ops o = this->sub(r);
+        T* dst = r == 0 ? eta : o.w.eta;
+        CKS(o.H_diff(x + pl->poff[r], sub + pl->poff[r], dst));
+        if (r > 0) CK(launch_add<T>(pl->n, dst, eta, nullptr, s));
+      }
+      return GLAM_OK;
+    }
     CK(launch_gemm<T, TB>(d_mode3_fwd(pl), X[2], x, w.Ta, s, nullptr, sub, nullptr, 0.0, nullptr));
     CK(launch_gemm<T, T>(d_mode1_fwd(pl), w.Ta, X[0], w.Tb, s));
     CK(launch_gemm<T, T>(d_mode2_fwd(pl), X[1], w.Tb, eta, s));
@@ -238,6 +273,33 @@ struct Ops {
   template <typename TB>
   int XtWX(const TB* x, const TB* xp, const TB* sub, const T* V, const InnerCtl* ctl,
            double omega, const int* skip) {
+    if (pl->nc > 1) {
+      // c > 1 (Eq. twentysixnew with r = 1..c): eta = sum_r H_r(y_r - sub_r) in this plan's
+      // n-array, V (.) eta, then G_r of it into component r's block of Qpart (ksplit = 1)
+      T* acc = w.eta_bar;
+      for (int r = 0; r < pl->nc; ++r) {
+        Ops o = this->sub(r);
+        glam_plan* q = pl->sub[r];
+        const int64_t off = pl->poff[r];
+        T* dst = r == 0 ? acc : o.w.eta_bar;
+        CK(launch_gemm<T, TB>(d_mode3_fwd(q), o.X[2], x + off, o.w.Ta, s, xp ? xp + off : nullptr,
+                              sub ? sub + off : nullptr, ctl, omega, skip));
+        CK(launch_gemm<T, T>(d_mode1_fwd(q), o.w.Ta, o.X[0], o.w.Tb, s, nullptr, nullptr, nullptr, 0.0, skip));
+        CK(launch_gemm<T, T>(d_mode2_fwd(q), o.X[1], o.w.Tb, dst, s, nullptr, nullptr, nullptr, 0.0, skip));
+        if (r > 0) CK(launch_add<T>(pl->n, dst, acc, skip, s));
+      }
+      CK(launch_vmul<T>(pl->n, V, acc, skip, s));
+      for (int r = 0; r < pl->nc; ++r) {
+        Ops o = this->sub(r);
+        glam_plan* q = pl->sub[r];
+        CK(launch_gemm<T, T>(d_mode2_adj(q), o.X[1], acc, o.w.Tb, s, nullptr, nullptr, nullptr, 0.0, skip));
+        CK(launch_gemm<T, T>(d_mode1_adj(q), o.w.Tb, o.X[0], o.w.Sb, s, nullptr, nullptr, nullptr, 0.0, skip));
+        CK(launch_gemm<T, T>(d_mode3_adj(q, q->ksplit), o.X[2], o.w.Sb, o.w.Qpart, s, nullptr, nullptr,
+                             nullptr, 0.0, skip));
+        CK(launch_sum_splits<T>(q->p, q->ksplit, o.w.Qpart, w.Qpart + pl->poff[r], s));
+      }
+      return GLAM_OK;
+    }
     if constexpr (sizeof(T) == 4 && sizeof(TB) == 4) {
       if (pl->um_form && sub == nullptr && ctl == nullptr && fused_tc_pointers_ok((const float*)pl->um_cst, w.yx, V)) {
         // tcgen05 kernel: it forms T_a = X_3 y from the extrapolated point itself
@@ -348,10 +410,20 @@ double jacobi_spectral_radius(std::vector<double> A, int m) {
   return r;
 }
 
+// X holds 3 design pointers per component (X_r1, X_r2, X_r3 of component r at 3r .. 3r + 2)
 int validate_X(glam_plan* pl, const void* const X[3]) {
-  if (X == nullptr || X[0] == nullptr || X[1] == nullptr)
-    return fail(pl, GLAM_EINVAL, "X: NULL design pointer");
-  if (pl->dims.d == 3 && X[2] == nullptr) return fail(pl, GLAM_EINVAL, "X[2] is NULL with d = 3");
+  if (X == nullptr) return fail(pl, GLAM_EINVAL, "X: NULL design pointer");
+  for (int r = 0; r < pl->nc; ++r) {
+    if (X[3 * r] == nullptr || X[3 * r + 1] == nullptr) return fail(pl, GLAM_EINVAL, "X: NULL design pointer");
+    if (pl->dims.d == 3 && X[3 * r + 2] == nullptr) return fail(pl, GLAM_EINVAL, "X: NULL X_3 with d = 3");
+  }
+  return GLAM_OK;
+}
+
+// entry points that take one component only
+int single_component(glam_plan* pl, const char* what) {
+  if (pl->nc > 1)
+    return fail(pl, GLAM_EINVAL, std::string(what) + ": not available for a plan with c > 1 components");
   return GLAM_OK;
 }
 
@@ -365,6 +437,7 @@ int check_plan(glam_plan* pl) {
 
 namespace glam {
 int thread_fail(int code, const std::string& msg) { return fail(nullptr, code, msg); }
+int plan_components(const glam_plan* pl) { return pl->nc; }
 }  // namespace glam
 
 // ======================================================================== ABI
@@ -528,6 +601,8 @@ int glam_plan_create(const glam_dims* dims, int family, int precision, void* str
 
 int glam_plan_destroy(glam_plan* pl) {
   if (pl == nullptr) return GLAM_OK;
+  for (int r = 0; r < kMaxComp; ++r)
+    if (pl->sub[r] != nullptr) glam_plan_destroy(pl->sub[r]);
   if (pl->stream) cudaStreamSynchronize(pl->stream);
   if (pl->work) cudaStreamSynchronize(pl->work);
   for (void* p : pl->allocs) cudaFree(p);
@@ -544,6 +619,56 @@ int glam_plan_destroy(glam_plan* pl) {
 int glam_plan_set_stream(glam_plan* pl, void* stream) {
   CKS(check_plan(pl));
   pl->stream = static_cast<cudaStream_t>(stream);
+  for (int r = 0; r < kMaxComp; ++r)
+    if (pl->sub[r] != nullptr) pl->sub[r]->stream = pl->stream;
+  return GLAM_OK;
+}
+
+int glam_plan_create_components(int d, const int64_t n[3], int c, const int64_t* p, int family, int precision,
+                                void* stream, glam_plan** out) {
+  if (out == nullptr || n == nullptr || p == nullptr)
+    return fail(nullptr, GLAM_EINVAL, "glam_plan_create_components: NULL argument");
+  *out = nullptr;
+  if (c < 1 || c > kMaxComp) return fail(nullptr, GLAM_EINVAL, "c must be in [1, 8]");
+  glam_dims dr{};
+  dr.d = d;
+  for (int j = 0; j < 3; ++j) dr.n[j] = n[j];
+  if (c == 1) {
+    for (int j = 0; j < 3; ++j) dr.p[j] = p[j];
+    return glam_plan_create(&dr, family, precision, stream, out);
+  }
+  int64_t ptot = 0;
+  for (int r = 0; r < c; ++r) {
+    if (p[3 * r] < 1 || p[3 * r + 1] < 1 || p[3 * r + 2] < 1)
+      return fail(nullptr, GLAM_EINVAL, "every p_rj must be >= 1");
+    ptot += p[3 * r] * p[3 * r + 1] * p[3 * r + 2];
+  }
+  // this plan: the grid's n-space arrays and the concatenated p-space state (its own transforms
+  // are never used: the components' plans do them)
+  glam_dims dp = dr;
+  dp.p[0] = ptot;
+  dp.p[1] = 1;
+  dp.p[2] = 1;
+  glam_plan* pl = nullptr;
+  CKS(glam_plan_create(&dp, family, precision, stream, &pl));
+  pl->nc = c;
+  pl->ksplit = 1;
+  pl->fused[0] = pl->fused[1] = false;
+  pl->um_form = 0;
+  pl->tc_split = 0;
+  pl->Vb = nullptr;  // the generic inner product reads the weights in the working precision
+  pl->poff[0] = 0;
+  for (int r = 0; r < c; ++r) {
+    for (int j = 0; j < 3; ++j) dr.p[j] = p[3 * r + j];
+    const int st = glam_plan_create(&dr, family, precision, stream, &pl->sub[r]);
+    if (st != GLAM_OK) {
+      const std::string m = g_thread_err;
+      glam_plan_destroy(pl);
+      return fail(nullptr, st, "component " + std::to_string(r) + ": " + m);
+    }
+    pl->poff[r + 1] = pl->poff[r] + pl->sub[r]->p;
+  }
+  *out = pl;
   return GLAM_OK;
 }
 
@@ -632,6 +757,7 @@ int glam_penalized_nll(glam_plan* pl, const void* const X[3], const void* Theta,
                        const void* W, double lambda, const void* pen_w, const double* gout,
                        double* F, void* grad_Theta, void* grad_Y) {
   CKS(check_plan(pl));
+  CKS(single_component(pl, "glam_penalized_nll"));
   CKS(validate_X(pl, X));
   if (!Theta || !Y || !W || !pen_w) return fail(pl, GLAM_EINVAL, "glam_penalized_nll: NULL array");
   if (!F && !grad_Theta && !grad_Y)
@@ -691,6 +817,7 @@ int rho_product_from(glam_plan* pl, const T* const X[3], cudaStream_t s, double&
 int glam_quad_build(glam_plan* pl, const void* const X[3], const void* Theta_k, const void* Y,
                     const void* W, const glam_quad* q) {
   CKS(check_plan(pl));
+  CKS(single_component(pl, "glam_quad_build"));
   CKS(validate_X(pl, X));
   if (!Theta_k || !Y || !W || !q || !q->V || !q->VZ || !q->b || !q->Lhat)
     return fail(pl, GLAM_EINVAL, "glam_quad_build: NULL argument");
@@ -724,6 +851,7 @@ int glam_prox_step(glam_plan* pl, const void* const X[3], const glam_quad* q, co
                    const void* x_prev, double omega, double delta, double lambda, const void* pen_w,
                    void* x_next) {
   CKS(check_plan(pl));
+  CKS(single_component(pl, "glam_prox_step"));
   CKS(validate_X(pl, X));
   if (!q || !q->V || !q->b || !q->Lhat || !x || !x_prev || !pen_w || !x_next)
     return fail(pl, GLAM_EINVAL, "glam_prox_step: NULL argument");
@@ -793,8 +921,8 @@ struct Fit {
   cudaStream_t s = nullptr;
   double rho_prod = 1.0;
   double lmax = 0.0;
-  const void* Xw[3] = {nullptr, nullptr, nullptr};   // designs in the working precision
-  const void* X64[3] = {nullptr, nullptr, nullptr};  // designs in FP64
+  const void* Xw[3 * kMaxComp] = {};   // designs in the working precision (3 per component)
+  const void* X64[3 * kMaxComp] = {};  // designs in FP64
   const double* Y64 = nullptr;
   const double* W64 = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -889,8 +1017,8 @@ int capture_chunk(Fit<T>& f) {
     if constexpr (sizeof(T) == 4) {
       use_um = pl->um_form && fused_tc_pointers_ok((const float*)pl->um_cst, op.w.dn, (const float*)Vin);
       use_tc = !use_um && pl->tc_split && fused_tc_pointers_ok(pl->tc_cst, op.w.dn, op.w.V);
-      use_ap = adjprox_supported((int)pl->n3, (int)pl->p3, (int)(pl->p2 * pl->p1),
-                                 (const float*)op.X[2], (const float*)op.w.Sb) != 0;
+      use_ap = pl->nc == 1 && adjprox_supported((int)pl->n3, (int)pl->p3, (int)(pl->p2 * pl->p1),
+                                                (const float*)op.X[2], (const float*)op.w.Sb) != 0;
     }
     const bool fused = pl->fused[sizeof(T) == 8 ? 1 : 0] || use_tc || use_um;
     if (fused) {
@@ -1176,7 +1304,8 @@ int fit_impl(glam_plan* pl, const void* const X[3], const T* Y, const T* W, cons
   f.s = pl->work;
   CK(cudaEventRecord(pl->ev_in, pl->stream));
   CK(cudaStreamWaitEvent(f.s, pl->ev_in, 0));
-  for (int j = 0; j < 3; ++j) f.Xw[j] = X[j];
+  const int nx = 3 * pl->nc;
+  for (int j = 0; j < nx; ++j) f.Xw[j] = X[j];
   f.wait_ns = (uint64_t)(o.wait_limit_s * 1e9);
   if (sizeof(T) == 4 && pl->um_form)  // the tcgen05 kernel's constant block, once per fit
     CK(launch_fused_umma_const((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2, (int)pl->p3,
@@ -1185,14 +1314,17 @@ int fit_impl(glam_plan* pl, const void* const X[3], const T* Y, const T* W, cons
     CK(launch_fused_tc_const((int)pl->n1, (int)pl->n2, (int)pl->p1, (int)pl->p2, (const float*)X[0],
                              (const float*)X[1], pl->tc_cst, pl->tc_split, f.s));
   if (sizeof(T) == 8) {
-    for (int j = 0; j < 3; ++j) f.X64[j] = X[j];
+    for (int j = 0; j < nx; ++j) f.X64[j] = X[j];
     f.Y64 = (const double*)Y;
     f.W64 = (const double*)W;
   } else {
-    for (int j = 0; j < 3; ++j) {
-      if (X[j] == nullptr) continue;
-      CK(launch_convert<float, double>(pl->dims.n[j] * pl->dims.p[j], (const float*)X[j], pl->wd.Xc[j], f.s));
-      f.X64[j] = pl->wd.Xc[j];
+    for (int r = 0; r < pl->nc; ++r) {
+      glam_plan* q = pl->nc > 1 ? pl->sub[r] : pl;  // the FP64 copies live in each component's plan
+      for (int j = 0; j < 3; ++j) {
+        if (X[3 * r + j] == nullptr) continue;
+        CK(launch_convert<float, double>(q->dims.n[j] * q->dims.p[j], (const float*)X[3 * r + j], q->wd.Xc[j], f.s));
+        f.X64[3 * r + j] = q->wd.Xc[j];
+      }
     }
     CK(launch_convert<float, double>(pl->n, (const float*)Y, pl->wd.Yc, f.s));
     CK(launch_convert<float, double>(pl->n, (const float*)W, pl->wd.Wc, f.s));
@@ -1221,12 +1353,19 @@ int fit_impl(glam_plan* pl, const void* const X[3], const T* Y, const T* W, cons
   CK(cudaMemcpyAsync(pl->h_sc, pl->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, f.s));
   CK(cudaStreamSynchronize(f.s));
   if (pl->h_sc->nonfinite) return fail(pl, GLAM_ENONFINITE, "non-finite value in Y, W, pen_w or Theta0");
-  // Prop. 1: prod_j varrho(X_j^T X_j)
-  {
-    const double* Xd[3] = {(const double*)f.X64[0], (const double*)f.X64[1], (const double*)f.X64[2]};
-    if (Xd[2] == nullptr) Xd[2] = pl->wd.one;
-    CKS(rho_product_from<double>(pl, Xd, f.s, f.rho_prod));
+  // Prop. 1: sum over the components of prod_j varrho(X_rj^T X_rj) (Eq. nineteennew)
+  f.rho_prod = 0.0;
+  for (int r = 0; r < pl->nc; ++r) {
+    glam_plan* q = pl->nc > 1 ? pl->sub[r] : pl;
+    const double* Xd[3] = {(const double*)f.X64[3 * r], (const double*)f.X64[3 * r + 1],
+                           (const double*)f.X64[3 * r + 2]};
+    if (Xd[2] == nullptr) Xd[2] = q->wd.one;
+    double rr = 1.0;
+    CKS(rho_product_from<double>(q, Xd, f.s, rr));
+    f.rho_prod += rr;
   }
+  if (pl->nc > 1 && o.iwls != GLAM_IWLS_EXACT)
+    return fail(pl, GLAM_EINVAL, "iwls: the tensor-product forms take one component (c = 1)");
   if (o.iwls == GLAM_IWLS_KRON1 || o.iwls == GLAM_IWLS_KRON2) {
     // the factors, the M_j and L are formed from V in every full FP64 pass
     CKS(kron_alloc<T>(pl));
@@ -1486,6 +1625,7 @@ int time_inner_impl(glam_plan* pl, const void* const X[3], const glam_quad* q, i
 int glam_time_inner_kernels(glam_plan* pl, const void* const X[3], const glam_quad* q, int reps,
                             double* ms) {
   CKS(check_plan(pl));
+  CKS(single_component(pl, "glam_time_inner_kernels"));
   CKS(validate_X(pl, X));
   if (!q || !q->V || !ms || reps < 1) return fail(pl, GLAM_EINVAL, "glam_time_inner_kernels: bad argument");
   if (pl->precision == GLAM_FP64) return time_inner_impl<double>(pl, X, q, reps, ms);

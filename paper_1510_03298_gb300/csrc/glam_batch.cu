@@ -28,6 +28,9 @@ int glam_fit_path_batched(int nitems, glam_plan* const* plans, glam_batch_item* 
       if (!seen.insert(plans[i]).second)
         return thread_fail(GLAM_EINVAL, "glam_fit_path_batched: a plan appears twice");
     }
+    for (int i = 0; i < nitems; ++i)
+      if (plan_components(plans[i]) != 1)  // an item holds the three designs of one component
+        return thread_fail(GLAM_EINVAL, "glam_fit_path_batched: plans with c > 1 components are not batched");
   }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess)

@@ -152,7 +152,7 @@ family_kernel(int family, int64_t n, const T* __restrict__ eta, const T* __restr
       }
       sc->loss = s / (double)n;
       sc->maxw = mx;
-      sc->Lhat = mx / (double)n * rho_prod;  // Prop. 1, Eq. (nineteennew), c = 1
+      sc->Lhat = mx / (double)n * rho_prod;  // Prop. 1, Eq. (nineteennew); rho_prod sums over the components
       *red.counter = 0u;
     }
   }
@@ -321,6 +321,15 @@ __global__ void vmul_kernel(int64_t n, const T* __restrict__ V, T* x, const int*
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     x[i] = V[i] * x[i];
+}
+
+// y += x (the sum over the components of a model with c > 1, Eq. eighteen)
+template <typename T>
+__global__ void add_kernel(int64_t n, const T* __restrict__ x, T* y, const int* skip) {
+  if (skip != nullptr && *skip) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += x[i];
 }
 
 template <typename T>
@@ -780,6 +789,13 @@ cudaError_t launch_vmul(int64_t n, const T* V, T* x, const int* skip, cudaStream
 }
 
 template <typename T>
+cudaError_t launch_add(int64_t n, const T* x, T* y, const int* skip, cudaStream_t s) {
+  add_kernel<T><<<grid_for(n), kThreads, 0, s>>>(n, x, y, skip);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_check_finite(int64_t n, const T* x, DevScalars* sc, cudaStream_t s) {
   finite_kernel<T><<<grid_for(n), kThreads, 0, s>>>(n, x, sc);
   count_launches(1);
@@ -889,6 +905,7 @@ cudaError_t launch_gram(int nj, int pj, const double* XT, double* gram, cudaStre
                                           cudaStream_t);                                           \
   template cudaError_t launch_check_finite<T>(int64_t, const T*, DevScalars*, cudaStream_t);      \
   template cudaError_t launch_vmul<T>(int64_t, const T*, T*, const int*, cudaStream_t);           \
+  template cudaError_t launch_add<T>(int64_t, const T*, T*, const int*, cudaStream_t);            \
   template cudaError_t launch_sum_splits<T>(int64_t, int, const T*, T*, cudaStream_t);            \
   template cudaError_t launch_armijo_penalty<T>(int64_t, const T*, const T*, const T*, double,    \
                                                 double, int, DevScalars*, RedScratch,             \

@@ -317,6 +317,8 @@ cudaError_t launch_sum_splits(int64_t p, int ksplit, const T* part, T* out, cuda
 
 template <typename T>
 cudaError_t launch_vmul(int64_t n, const T* V, T* x, const int* skip, cudaStream_t s);
+template <typename T>
+cudaError_t launch_add(int64_t n, const T* x, T* y, const int* skip, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_check_finite(int64_t n, const T* x, DevScalars* sc, cudaStream_t s);
@@ -341,6 +343,8 @@ int num_sms();
 
 // Record msg as the calling thread's last error (read by glam_last_error(NULL)); returns code.
 int thread_fail(int code, const std::string& msg);
+// Number of model components c of a plan (1, or c > 1 for glam_plan_create_components).
+int plan_components(const glam_plan* pl);
 
 // Process-wide count of kernels launched by the library (graph replays add their kernel nodes).
 void count_launches(int64_t k);
