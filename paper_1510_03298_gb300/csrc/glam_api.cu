@@ -223,6 +223,11 @@ struct Ops {
       return GLAM_OK;
     }
     if constexpr (sizeof(T) == 4) {
+      if (predict_umma_supported((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2, (int)pl->p3)) {
+        CK(launch_predict_umma((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2, (int)pl->p3, X[0],
+                               X[1], X[2], theta, eta, &pl->sc->timeout, s));
+        return GLAM_OK;
+      }
       if (predict_tiles_supported((int)pl->p1, (int)pl->p2) && mode3_rows_supported((int)pl->p3)) {
         CK(launch_mode3_rows((int)pl->n3, (int)pl->p3, (int)(pl->p2 * pl->p1), X[2], theta, w.Ta, s));
         CK(launch_predict_tiles((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2,

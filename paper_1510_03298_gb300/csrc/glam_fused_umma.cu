@@ -898,6 +898,303 @@ bool um_configure(int n1, int n2, int n3, int p1, int p2, int p3, int grid, int 
   return (size_t)(s.total + 1024) <= g_um_budget;
 }
 
+// ---------------------------------------------------------------- the H-transform on tcgen05
+// eta = H(<X_j>, Theta) (Sec. 6.1, Eq. eighteen) for glam_predict and the other single-precision
+// products of the linear predictor, one CTA per SM over the slabs i3 it owns:
+//   first H stage  T_a = X_3 Theta for the CTA's slabs (FP32; zero rows of X_3 skipped), Theta
+//                  staged in shared memory in rounds of rows j3
+//   MMA0 (SIMT)    T_b^T (c x j2) = X_1 (c x j1) T_a^T, exact FP32 FMAs, split hi/lo into TMEM
+//   MMA1 (tcgen05) eta^T (c x i2) = T_b^T X_2^T in the 3xTF32 form (about FP32 accuracy), A from
+//                  TMEM, B = X_2 (hi and lo tiles formed in shared memory by the CTA), D in one of
+//                  two TMEM buffers
+//   write-out      the compute warps read eta^T from TMEM (lane = i1) and store it with
+//                  coalesced global stores while MMA1 of the next slab fills the other buffer.
+// Warps 0-7 compute (two warpgroups split the i2 columns of the write-out), warp 8 issues MMA1
+// and owns the TMEM.  Every wait is bounded; a wait that runs out sets *err and the CTA drains and
+// exits (eta is then incomplete).
+constexpr int kPuThreads = 288;
+constexpr int kPuIssuer = 8;
+
+struct PuShape {
+  int n1, n2, n3, p1, p2, p3;
+  int K1, P1P, kmax, R;  // K of MMA1 (p2 padded to 8), p1 padded to 4, slabs per CTA, rows j3 per round
+  int64_t o_x2t, x2t_part, o_tas, o_x3r, o_rows, o_stage, stage_floats, total;
+  uint32_t c_eta, c_tb, c_tblo;  // TMEM: two eta buffers of n2 columns, T_b^T hi and lo
+};
+
+bool pu_configure(int n1, int n2, int n3, int p1, int p2, int p3, int grid, PuShape& s) {
+  if (n1 < 4 || n1 > 128 || n1 % 4 != 0 || n2 < 32 || n2 % 32 != 0 || n2 > 224 || n3 < 1 || p1 < 1 ||
+      p1 > 32 || p2 < 1 || p2 > 32 || p3 < 1 || grid < 1)
+    return false;
+  s.n1 = n1; s.n2 = n2; s.n3 = n3; s.p1 = p1; s.p2 = p2; s.p3 = p3;
+  s.K1 = (int)up(p2, 8);
+  s.P1P = (int)up(p1, 4);
+  s.kmax = (n3 + grid - 1) / grid;
+  const int KQ = (s.kmax + 3) / 4 * 4;
+  int64_t o = 0;
+  s.o_x2t = o;
+  s.x2t_part = (int64_t)n2 * 128;  // rows i2 of 128 bytes (K = j2 <= 32 TF32 values), 1 KB groups
+  o += 2 * s.x2t_part;
+  s.o_tas = o;
+  o += up(((int64_t)s.kmax * s.P1P * s.K1 + 16) * 4, 16);
+  s.o_x3r = o;
+  o += up((int64_t)p3 * KQ * 4, 16);
+  s.o_rows = o;
+  o += up((int64_t)p3 * 4, 16);
+  s.o_stage = o;
+  const int64_t P21 = (int64_t)p1 * p2;
+  const int64_t room = (int64_t)g_um_budget - 1024 - o;
+  int64_t R = room / (P21 * 4);
+  if (R > p3) R = p3;
+  if (R < 1) return false;
+  s.R = (int)R;
+  s.stage_floats = R * P21;
+  o += up(s.stage_floats * 4, 16);
+  s.total = up(o, 16);
+  s.c_eta = 0;
+  s.c_tb = (uint32_t)(2 * n2);
+  s.c_tblo = s.c_tb + 32;
+  if (s.c_tblo + 32 > kUmTmemCols) return false;
+  return (size_t)(s.total + 1024) <= g_um_budget;
+}
+
+__global__ void __launch_bounds__(kPuThreads, 1)
+predict_umma_kernel(PuShape sh, const float* __restrict__ X1T, const float* __restrict__ X2T,
+                    const float* __restrict__ X3T, const float* __restrict__ Theta, float* __restrict__ eta,
+                    int* __restrict__ err, uint64_t wait_ns) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ uint64_t tb_ready, eta_ready[2], eta_free[2];
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int timed_out, nrows_s;
+  const int n1 = sh.n1, n2 = sh.n2, n3 = sh.n3, p1 = sh.p1, p2 = sh.p2, p3 = sh.p3;
+  const int P21 = p1 * p2, K1 = sh.K1, P1P = sh.P1P;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int kcta = (n3 - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  unsigned char* const base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  const uint32_t sbase = smem_u32(base);
+  float* const TaS = reinterpret_cast<float*>(base + sh.o_tas);
+  float* const X3r = reinterpret_cast<float*>(base + sh.o_x3r);
+  int* const rowlist = reinterpret_cast<int*>(base + sh.o_rows);
+  float* const stage = reinterpret_cast<float*>(base + sh.o_stage);
+  const int KQ = (sh.kmax + 3) / 4 * 4;
+  const uint64_t drain_ns = wait_ns > kDrainNs ? wait_ns : kDrainNs;
+  if (tid == 0) {
+    timed_out = 0;
+    mbar_init(&tb_ready, 8);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&eta_ready[b], 1);
+      mbar_init(&eta_free[b], 8);
+    }
+    fence_mbar_init();
+  }
+  if (warp == kPuIssuer) {
+    umma::tmem_alloc(&tmem_base_s, kUmTmemCols);
+    umma::tmem_relinquish();
+  }
+  // X_2 as MMA1's B operand (rows i2, K = j2, 128-byte swizzle), hi and lo TF32 parts; each
+  // thread loads 8 entries before it stores any
+  for (int e0 = 0; e0 < n2 * 32; e0 += 8 * kPuThreads) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * kPuThreads + tid, i2 = e >> 5, j2 = e & 31;
+      v[u] = (e < n2 * 32 && j2 < p2) ? X2T[(int64_t)j2 * n2 + i2] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * kPuThreads + tid, i2 = e >> 5, j2 = e & 31;
+      if (e >= n2 * 32) break;
+      const uint32_t h = rna_tf32(v[u]);
+      const uint32_t off = umma::sw128_k4((uint32_t)i2, (uint32_t)j2);
+      *reinterpret_cast<uint32_t*>(base + sh.o_x2t + off) = h;
+      *reinterpret_cast<uint32_t*>(base + sh.o_x2t + sh.x2t_part + off) = rna_tf32(v[u] - __uint_as_float(h));
+    }
+  }
+  // X_3 entries of this CTA's slabs, [j3][k]; T_a starts at zero (rows j1 >= p1 stay zero)
+  for (int idx = tid; idx < p3 * KQ; idx += kPuThreads) {
+    const int j3 = idx / KQ, kk = idx - j3 * KQ;
+    X3r[idx] = kk < kcta ? X3T[(int64_t)j3 * n3 + blockIdx.x + (int64_t)kk * gridDim.x] : 0.f;
+  }
+  for (int idx = tid; idx < sh.kmax * P1P * K1 + 16; idx += kPuThreads) TaS[idx] = 0.f;
+  fence_proxy_async();  // the B tiles were written by plain stores; MMA1 reads them
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tb = tmem_base_s;
+  if (warp == 0) {  // rows j3 with a nonzero X_3 entry for this CTA's slabs, in increasing order
+    int cnt = 0;
+    for (int j0 = 0; j0 < p3; j0 += 32) {
+      const int j3 = j0 + lane;
+      bool nz = false;
+      if (j3 < p3)
+        for (int kk = 0; kk < kcta; ++kk) nz |= X3r[j3 * KQ + kk] != 0.f;
+      const unsigned m = __ballot_sync(0xffffffffu, nz);
+      if (nz) rowlist[cnt + __popc(m & ((1u << lane) - 1u))] = j3;
+      cnt += __popc(m);
+    }
+    if (lane == 0) nrows_s = cnt;
+  }
+  __syncthreads();
+  // first H stage: T_a(s_k, j2, j1) = sum_j3 X_3(s_k, j3) Theta(j3, j2, j1) over the listed rows,
+  // in j3 order, Theta staged R rows at a time (only the listed rows are copied)
+  const int nr = nrows_s;
+  for (int rl = 0; rl < nr;) {
+    int re = rl;
+    while (re < nr && rowlist[re] - rowlist[rl] < sh.R) ++re;
+    const int j0 = rowlist[rl];
+    // the round's listed rows of Theta by asynchronous 4-byte copies, all in flight at once
+    for (int idx = tid; idx < (re - rl) * P21; idx += kPuThreads) {
+      const int t = idx / P21, i = idx - t * P21;
+      const int j3 = rowlist[rl + t];
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(stage + (j3 - j0) * P21 + i)),
+                   "l"(Theta + (int64_t)j3 * P21 + i)
+                   : "memory");
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    const int nkg = (kcta + 3) / 4;
+    for (int task = tid; task < P21 * nkg; task += kPuThreads) {
+      const int nn = task % P21, k0 = 4 * (task / P21);
+      const int j2 = nn / p1, j1 = nn - j2 * p1;
+      float a[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = (k0 + r < kcta) ? TaS[((k0 + r) * P1P + j1) * K1 + j2] : 0.f;
+      for (int t0 = rl; t0 < re; t0 += 8) {
+        int jr[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) jr[u] = rowlist[t0 + u < re ? t0 + u : re - 1];
+        float dv[8];
+        float4 xv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          dv[u] = t0 + u < re ? stage[(jr[u] - j0) * P21 + nn] : 0.f;
+          xv[u] = *reinterpret_cast<const float4*>(X3r + jr[u] * KQ + k0);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          a[0] = fmaf(xv[u].x, dv[u], a[0]);
+          a[1] = fmaf(xv[u].y, dv[u], a[1]);
+          a[2] = fmaf(xv[u].z, dv[u], a[2]);
+          a[3] = fmaf(xv[u].w, dv[u], a[3]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (k0 + r < kcta) TaS[((k0 + r) * P1P + j1) * K1 + j2] = a[r];
+    }
+    __syncthreads();
+    rl = re;
+  }
+  if (warp == kPuIssuer) {
+    // ---------------------------------------------------------------- MMA1 issue (warp 8)
+    if (lane == 0) {
+      const uint32_t id1 = umma::idesc(128, (uint32_t)n2, umma::kTypeTF32, umma::kTypeTF32, 0, 0);
+      const uint64_t bh = umma::sdesc(sbase + (uint32_t)sh.o_x2t, 16, 1024, umma::kSwizzle128B);
+      const uint64_t bl = umma::sdesc(sbase + (uint32_t)(sh.o_x2t + sh.x2t_part), 16, 1024, umma::kSwizzle128B);
+      int ne0 = 0, ne1 = 0;  // commits on eta_ready[0] and [1]
+      bool ok = true;
+      for (int k = 0; k < kcta && ok; ++k) {
+        const int b = k & 1;
+        ok = wait_for(&tb_ready, (uint32_t)(k & 1), wait_ns);
+        if (ok && k >= 2) ok = wait_for(&eta_free[b], (uint32_t)(((k - 2) >> 1) & 1), wait_ns);
+        if (!ok) break;
+        umma::fence_after_sync();
+        const uint32_t d = tb + sh.c_eta + (uint32_t)(b * n2);
+        for (int s = 0; s < K1 / 8; ++s) {
+          const uint64_t off = (uint64_t)(2 * s);  // 32 bytes of K
+          umma::mma_tf32_ts(d, tb + sh.c_tb + 8u * s, bh + off, id1, s != 0);
+          umma::mma_tf32_ts(d, tb + sh.c_tb + 8u * s, bl + off, id1, 1u);
+          umma::mma_tf32_ts(d, tb + sh.c_tblo + 8u * s, bh + off, id1, 1u);
+        }
+        umma::commit(&eta_ready[b]);
+        if (b == 0) ++ne0;
+        else ++ne1;
+      }
+      if (!ok) atomicOr(&timed_out, 1);
+      // every MMA has completed before the TMEM is released
+      if (ne0 > 0) wait_for(&eta_ready[0], (uint32_t)((ne0 - 1) & 1), drain_ns);
+      if (ne1 > 0) wait_for(&eta_ready[1], (uint32_t)((ne1 - 1) & 1), drain_ns);
+    }
+    __syncwarp();
+  } else {
+    // ---------------------------------------------------------------- compute warps 0-7
+    const int q = warp & 3, wg = warp >> 2;
+    const int c = 32 * q + lane;  // TMEM lane = row i1
+    const bool rowok = c < n1;
+    const uint32_t lq = (uint32_t)(32 * q) << 16;
+    const int hw = K1 / 2;
+    const float* const x1c = X1T + (rowok ? c : 0);
+    auto mma0 = [&](int kk) {  // T_b^T(c, j2) for this warpgroup's columns j2, hi and lo parts
+      const float* tk = TaS + (int64_t)kk * P1P * K1 + wg * hw;
+      float acc[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) acc[u] = 0.f;
+      switch (hw >> 2) {
+        case 1: mma0_fma<1>(tk, K1, p1, x1c, n1, rowok, acc); break;
+        case 2: mma0_fma<2>(tk, K1, p1, x1c, n1, rowok, acc); break;
+        case 3: mma0_fma<3>(tk, K1, p1, x1c, n1, rowok, acc); break;
+        default: mma0_fma<4>(tk, K1, p1, x1c, n1, rowok, acc); break;
+      }
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        if (4 * v < hw) {
+          uint32_t hi[4], lo[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            hi[u] = rna_tf32(acc[4 * v + u]);
+            lo[u] = rna_tf32(acc[4 * v + u] - __uint_as_float(hi[u]));
+          }
+          umma::st_x4(tb + lq + sh.c_tb + (uint32_t)(wg * hw + 4 * v), hi);
+          umma::st_x4(tb + lq + sh.c_tblo + (uint32_t)(wg * hw + 4 * v), lo);
+        }
+      umma::wait_st();
+      umma::fence_before_sync();
+      warp_arrive(&tb_ready);
+    };
+    bool ok = __all_sync(0xffffffffu, !*(volatile int*)&timed_out) != 0;
+    if (ok) mma0(0);
+    const int half = n2 / 32;  // 16-column chunks of this warpgroup
+    for (int k = 0; k < kcta && ok; ++k) {
+      const int b = k & 1;
+      ok = warp_wait(&eta_ready[b], (uint32_t)((k >> 1) & 1), wait_ns);
+      if (!ok) break;
+      umma::fence_after_sync();
+      // T_b^T is free once MMA1 of slab k has completed: the next slab's goes in now, so that its
+      // MMA1 runs while this slab is written out
+      if (k + 1 < kcta) mma0(k + 1);
+      float* out = eta + (int64_t)((int)blockIdx.x + k * (int)gridDim.x) * n2 * n1 + c;
+      const uint32_t src = tb + lq + sh.c_eta + (uint32_t)(b * n2);
+      for (int i = 0; i < half; i += 2) {  // two chunks per load round
+        const int ch = wg * half + i;
+        const bool two = i + 1 < half;
+        uint32_t e0[16], e1[16];
+        umma::ld_x16(src + (uint32_t)(16 * ch), e0);
+        if (two) umma::ld_x16(src + (uint32_t)(16 * (ch + 1)), e1);
+        umma::wait_ld();
+        umma::ld_done(e0);
+        umma::ld_done(e1);
+        if (rowok) {
+#pragma unroll
+          for (int u = 0; u < 16; ++u) __stcs(out + (int64_t)(16 * ch + u) * n1, __uint_as_float(e0[u]));
+          if (two) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) __stcs(out + (int64_t)(16 * (ch + 1) + u) * n1, __uint_as_float(e1[u]));
+          }
+        }
+      }
+      umma::fence_before_sync();
+      warp_arrive(&eta_free[b]);
+    }
+    if (!ok) atomicOr(&timed_out, 1);
+  }
+  __syncthreads();
+  if (timed_out && tid == 0) atomicOr(err, 1);
+  if (warp == kPuIssuer) {
+    umma::fence_after_sync();
+    umma::tmem_dealloc(tb, kUmTmemCols);
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 um_encode() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static bool done = false;
@@ -947,6 +1244,8 @@ cudaError_t fused_umma_prepare() {
   if (e == cudaSuccess) e = um_prepare_one<kForm3x, float>();
   if (e == cudaSuccess) e = um_prepare_one<kFormBF16, float>();
   if (e == cudaSuccess) e = um_prepare_one<kFormBF16, __nv_bfloat16>();
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(predict_umma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g_um_budget);
   return e;
 }
 
@@ -1007,6 +1306,24 @@ cudaError_t launch_fused_umma(int n1, int n2, int n3, int p1, int p2, int p3, in
     e = launch_pdl(fused_slab_umma_kernel<kFormBF16, float>, g, b, smem, st, pdl, s, c, D, X1T, X3T, tmapV, Sb,
                    skip, err, wait_ns);
   if (e != cudaSuccess) return e;
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+int predict_umma_supported(int n1, int n2, int n3, int p1, int p2, int p3) {
+  PuShape s;
+  return pu_configure(n1, n2, n3, p1, p2, p3, um_grid(n3), s) ? 1 : 0;
+}
+
+cudaError_t launch_predict_umma(int n1, int n2, int n3, int p1, int p2, int p3, const float* X1T, const float* X2T,
+                                const float* X3T, const float* Theta, float* eta, int* err, cudaStream_t st) {
+  PuShape s;
+  const int grid = um_grid(n3);
+  if (!pu_configure(n1, n2, n3, p1, p2, p3, grid, s)) return cudaErrorInvalidValue;
+  // at least half of the shared memory of an SM: one CTA per SM (the TMEM allocation is 512 columns)
+  size_t smem = (size_t)s.total + 1024;
+  if (smem < g_um_budget / 2 + 1024) smem = g_um_budget / 2 + 1024;
+  predict_umma_kernel<<<grid, kPuThreads, smem, st>>>(s, X1T, X2T, X3T, Theta, eta, err, kDrainNs);
   count_launches(1);
   return cudaGetLastError();
 }

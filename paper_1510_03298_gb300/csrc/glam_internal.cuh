@@ -186,6 +186,13 @@ cudaError_t fused_tc_prepare();
 // the shape is in the kernel's domain (n1 <= 128, n1 a multiple of 4 (8 for BF16), n2 a multiple
 // of 32 up to 128 (3xTF32) or 256, p1, p2 <= 32).
 cudaError_t fused_umma_prepare();
+// eta = H(<X_j>, Theta) for single-precision plans on the tcgen05 kernel (first H stage and MMA0
+// in FP32 FMAs, MMA1 in 3xTF32), one CTA per SM, eta written with coalesced stores; after
+// fused_umma_prepare.  Domain: n1 <= 128, n1 % 4 == 0, n2 % 32 == 0, n2 <= 224, p1, p2 <= 32.  A
+// device wait that runs out (bounded by 2 s) sets *err.
+int predict_umma_supported(int n1, int n2, int n3, int p1, int p2, int p3);
+cudaError_t launch_predict_umma(int n1, int n2, int n3, int p1, int p2, int p3, const float* X1T, const float* X2T,
+                                const float* X3T, const float* Theta, float* eta, int* err, cudaStream_t st);
 int fused_umma_supported(int n1, int n2, int n3, int p1, int p2, int p3, int form);
 int64_t fused_umma_const_bytes(int n1, int n2, int n3, int p1, int p2, int p3, int form);
 cudaError_t launch_fused_umma_const(int n1, int n2, int n3, int p1, int p2, int p3, int form,
