@@ -135,7 +135,14 @@ typedef struct {
                               stats of a lambda then sum the steps' iterations and report the
                               objective and KKT residual of the last weighted problem */
   int32_t steps;           /* MSA steps per lambda for GLAM_PENALTY_SCAD (default 1, >= 1) */
-  int32_t reserved[3];
+  int32_t exploit_bands;   /* nonzero: the FP64 gradient passes use banded mode products, for marginal
+                              designs with at most 4 consecutive nonzeros per row and nondecreasing
+                              first columns (cubic B-spline bases); a specialisation, not the paper's
+                              general method (which takes dense designs, Sec. 6.1).  The FP64 sums
+                              skip only exact zeros, so the path is the same up to summation order.
+                              glam_fit_path returns GLAM_EINVAL when a design is not banded or the
+                              plan has c > 1 components (default 0) */
+  int32_t reserved[2];
   double enet_alpha;       /* GLAM_PENALTY_ENET: J = sum_m w_m (|theta_m| + enet_alpha theta_m^2),
                               the elastic net of Sec. 6.3 (default 0, >= 0) */
   double wait_limit_s;     /* limit, in seconds, of every bounded device-side wait of the inner

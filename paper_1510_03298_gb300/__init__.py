@@ -83,7 +83,7 @@ class GlamOpts(C.Structure):
                 ("inner_floor", C.c_double), ("armijo_alpha0", C.c_double), ("armijo_b", C.c_double),
                 ("armijo_v", C.c_double), ("max_inner", C.c_int32), ("max_outer", C.c_int32),
                 ("max_linesearch", C.c_int32), ("check_every", C.c_int32), ("iwls", C.c_int32),
-                ("penalty", C.c_int32), ("steps", C.c_int32), ("reserved", C.c_int32 * 3),
+                ("penalty", C.c_int32), ("steps", C.c_int32), ("exploit_bands", C.c_int32), ("reserved", C.c_int32 * 2),
                 ("enet_alpha", C.c_double), ("wait_limit_s", C.c_double), ("nu", C.c_double)]
 
 

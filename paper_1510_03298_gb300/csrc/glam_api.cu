@@ -88,6 +88,10 @@ struct glam_plan {
   double* pen_base = nullptr;      // the caller's penalty weights during a SCAD fit (p)
   unsigned long long* kcheck = nullptr;
   double* geo = nullptr;           // scratch of the geometric-mean weight factors
+  // banded form of the marginal designs, used by the FP64 transforms while a fit that asked for it
+  // (glam_opts.exploit_bands) runs
+  bool band_on = false;
+  BandDesign band[3];
   std::vector<void*> allocs;
 };
 
@@ -213,6 +217,15 @@ struct Ops {
   // eta = H(<X_j>, Theta)   (Sec. 6.1, Eq. eighteen); c > 1: the sum over the components, each
   // component's term formed in its own plan's n-array and added
   int H(const T* theta, T* eta) {
+    if constexpr (sizeof(T) == 8) {
+      if (pl->band_on) {  // modes 3, 1, 2 as banded products (4 terms per output)
+        const int64_t P21 = pl->p2 * pl->p1;
+        CK(launch_band_fwd(1, (int)pl->p3, (int)pl->n3, P21, pl->band[2], theta, w.Ta, s));
+        CK(launch_band_fwd(pl->n3 * pl->p2, (int)pl->p1, (int)pl->n1, 1, pl->band[0], w.Ta, w.Tb, s));
+        CK(launch_band_fwd(pl->n3, (int)pl->p2, (int)pl->n2, pl->n1, pl->band[1], w.Tb, eta, s));
+        return GLAM_OK;
+      }
+    }
     if (pl->nc > 1) {
       for (int r = 0; r < pl->nc; ++r) {
         Ops o = sub(r);
@@ -242,6 +255,15 @@ struct Ops {
   }
   // out = G(<X_j>, U)   (Sec. 6.1, Eq. nineteen); c > 1: component r's block at poff[r]
   int G(const T* U, T* out) {
+    if constexpr (sizeof(T) == 8) {
+      if (pl->band_on) {  // modes 2, 1, 3 as banded adjoint products
+        const int64_t P21 = pl->p2 * pl->p1;
+        CK(launch_band_adj(pl->n3, (int)pl->n2, (int)pl->p2, pl->n1, pl->band[1], U, w.Tb, s));
+        CK(launch_band_adj(pl->n3 * pl->p2, (int)pl->n1, (int)pl->p1, 1, pl->band[0], w.Tb, w.Sb, s));
+        CK(launch_band_adj(1, (int)pl->n3, (int)pl->p3, P21, pl->band[2], w.Sb, out, s));
+        return GLAM_OK;
+      }
+    }
     if (pl->nc > 1) {
       for (int r = 0; r < pl->nc; ++r) CKS(sub(r).G(U, out + pl->poff[r]));
       return GLAM_OK;
@@ -1195,6 +1217,42 @@ int solve_lambda(Fit<T>& f, double lambda, LamOut& lo) {
   }
 }
 
+// The banded form of the FP64 marginal designs of this fit (glam_opts.exploit_bands): every X_j
+// must have at most kBand consecutive nonzeros per row with nondecreasing first columns.
+template <typename T>
+int band_setup(Fit<T>& f) {
+  glam_plan* pl = f.pl;
+  if (pl->nc > 1) return fail(pl, GLAM_EINVAL, "exploit_bands: takes one component (c = 1)");
+  const int64_t nj[3] = {pl->n1, pl->n2, pl->n3}, pj[3] = {pl->p1, pl->p2, pl->p3};
+  for (int j = 0; j < 3; ++j) {
+    const double* Xd = (const double*)f.X64[j];
+    if (Xd == nullptr) Xd = pl->wd.one;  // d = 2: the 1 x 1 design
+    std::vector<double> XT((size_t)(nj[j] * pj[j]));
+    CK(cudaMemcpyAsync(XT.data(), Xd, sizeof(double) * XT.size(), cudaMemcpyDeviceToHost, f.s));
+    CK(cudaStreamSynchronize(f.s));
+    std::vector<int> st, lo, hi;
+    std::vector<double> val;
+    if (!band_form(XT.data(), (int)nj[j], (int)pj[j], st, val, lo, hi))
+      return fail(pl, GLAM_EINVAL,
+                  "exploit_bands: X_" + std::to_string(j + 1) + " has a row with more than 4 consecutive nonzeros "
+                  "or first columns that decrease");
+    BandDesign& b = pl->band[j];
+    if (b.start == nullptr) {
+      CKS(dalloc(pl, &b.start, nj[j]));
+      CKS(dalloc(pl, &b.val, nj[j] * kBand));
+      CKS(dalloc(pl, &b.lo, pj[j]));
+      CKS(dalloc(pl, &b.hi, pj[j]));
+    }
+    CK(cudaMemcpyAsync(b.start, st.data(), sizeof(int) * st.size(), cudaMemcpyHostToDevice, f.s));
+    CK(cudaMemcpyAsync(b.val, val.data(), sizeof(double) * val.size(), cudaMemcpyHostToDevice, f.s));
+    CK(cudaMemcpyAsync(b.lo, lo.data(), sizeof(int) * lo.size(), cudaMemcpyHostToDevice, f.s));
+    CK(cudaMemcpyAsync(b.hi, hi.data(), sizeof(int) * hi.size(), cudaMemcpyHostToDevice, f.s));
+    CK(cudaStreamSynchronize(f.s));  // the host vectors go out of scope
+  }
+  pl->band_on = true;
+  return GLAM_OK;
+}
+
 // Buffers of the tensor-product form: the factors w_j, the FP64 and working-precision M_j, the
 // p-sized intermediates of H(<M_j>, d), and the scratch of the geometric-mean factors.
 template <typename T>
@@ -1371,6 +1429,11 @@ int fit_impl(glam_plan* pl, const void* const X[3], const T* Y, const T* W, cons
   }
   if (pl->nc > 1 && o.iwls != GLAM_IWLS_EXACT)
     return fail(pl, GLAM_EINVAL, "iwls: the tensor-product forms take one component (c = 1)");
+  struct BandOff {  // the banded form serves this fit only
+    glam_plan* p;
+    ~BandOff() { p->band_on = false; }
+  } band_off{pl};
+  if (o.exploit_bands) CKS(band_setup<T>(f));
   if (o.iwls == GLAM_IWLS_KRON1 || o.iwls == GLAM_IWLS_KRON2) {
     // the factors, the M_j and L are formed from V in every full FP64 pass
     CKS(kron_alloc<T>(pl));

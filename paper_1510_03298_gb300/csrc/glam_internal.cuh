@@ -10,6 +10,7 @@
 
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "glam.h"
 
@@ -350,6 +351,21 @@ int num_sms();
 
 // Record msg as the calling thread's last error (read by glam_last_error(NULL)); returns code.
 int thread_fail(int code, const std::string& msg);
+// ---- banded marginal designs (glam_band.cu): at most kBand consecutive nonzeros per row
+constexpr int kBand = 4;
+struct BandDesign {
+  int* start = nullptr;   // n: first column of row i
+  double* val = nullptr;  // n x kBand: X(i, start(i) + t)
+  int* lo = nullptr;      // p: the rows touching column j are [lo(j), hi(j))
+  int* hi = nullptr;
+};
+cudaError_t launch_band_fwd(int64_t A, int Cin, int Cout, int64_t B, const BandDesign& X, const double* In,
+                            double* Out, cudaStream_t s);
+cudaError_t launch_band_adj(int64_t A, int Cin, int Cout, int64_t B, const BandDesign& X, const double* In,
+                            double* Out, cudaStream_t s);
+bool band_form(const double* XT, int n, int p, std::vector<int>& start, std::vector<double>& val,
+               std::vector<int>& lo, std::vector<int>& hi);
+
 // Number of model components c of a plan (1, or c > 1 for glam_plan_create_components).
 int plan_components(const glam_plan* pl);
 
