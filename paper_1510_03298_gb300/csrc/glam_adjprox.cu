@@ -57,7 +57,8 @@ __global__ void __launch_bounds__(kAPThreads)
 adjprox_kernel(APShape sh, const __grid_constant__ CUtensorMap mapS, const __grid_constant__ CUtensorMap mapX,
                const double* __restrict__ gk, const double* __restrict__ x, const double* xp,
                const double* __restrict__ pen, double* out, float* __restrict__ dnext,
-               const double* __restrict__ anchor, double inv_n, InnerCtl* ctl, int* err) {
+               const double* __restrict__ anchor, double inv_n, InnerCtl* ctl, int* err,
+               const int* __restrict__ rows) {
   // with a programmatic dependent launch this kernel may start before the preceding one ends:
   // nothing is read or written before it has
   griddep_wait();
@@ -73,9 +74,24 @@ adjprox_kernel(APShape sh, const __grid_constant__ CUtensorMap mapS, const __gri
   __shared__ bool is_last;
   float* const base = reinterpret_cast<float*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int KC = sh.KC, nchunk = sh.nchunk, P21 = sh.P21;
+  const int KC = sh.KC, P21 = sh.P21;
   const int tn = blockIdx.x % sh.nx, tj = blockIdx.x / sh.nx;
   const int n0 = 32 * tn, j0 = TJ * tj;
+  // the rows i3 where this tile's rows of X_3 have nonzero entries (from rows[]: per j3 the first
+  // and one past the last nonzero i3), the start rounded down to 4 (16-byte copy coordinates);
+  // the other rows add exact zeros
+  int i_lo = 0, i_hi = sh.n3;
+  if (rows != nullptr) {
+    i_lo = sh.n3;
+    i_hi = 0;
+    for (int j = j0; j < j0 + TJ && j < sh.p3; ++j) {
+      i_lo = min(i_lo, rows[2 * j]);
+      i_hi = max(i_hi, rows[2 * j + 1]);
+    }
+    i_lo &= ~3;
+    if (i_hi < i_lo) i_hi = i_lo;
+  }
+  const int nchunk = (i_hi - i_lo + KC - 1) / KC;
   const int stage = KC * 32 + KC * TJ;  // floats per buffer: S chunk [KC][32], X chunk [TJ][KC]
   const uint32_t bytes = (uint32_t)stage * 4u;
   if (tid == 0) {
@@ -91,12 +107,12 @@ adjprox_kernel(APShape sh, const __grid_constant__ CUtensorMap mapS, const __gri
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
         "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(&mapS)), "r"(n0), "r"(c * KC), "r"(smem_u32(&mbar[b]))
+        "l"(reinterpret_cast<uint64_t>(&mapS)), "r"(n0), "r"(i_lo + c * KC), "r"(smem_u32(&mbar[b]))
         : "memory");
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
         "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst + KC * 32)),
-        "l"(reinterpret_cast<uint64_t>(&mapX)), "r"(c * KC), "r"(j0), "r"(smem_u32(&mbar[b]))
+        "l"(reinterpret_cast<uint64_t>(&mapX)), "r"(i_lo + c * KC), "r"(j0), "r"(smem_u32(&mbar[b]))
         : "memory");
   };
   const int nfirst = nchunk < kAPBufs ? nchunk : kAPBufs;
@@ -155,18 +171,26 @@ adjprox_kernel(APShape sh, const __grid_constant__ CUtensorMap mapS, const __gri
   float* red = base;  // [warp][TJ][32], over buffer 0 (free after the loop's last barrier)
 #pragma unroll
   for (int j = 0; j < TJ; ++j) red[(warp * TJ + j) * 32 + lane] = acc[j];
+  __shared__ double om_s[2];  // the extrapolation weights, divided once per CTA (FP64 is slow here)
+  if (tid == 0) {
+    om_s[0] = double(l - 1) / double(l + 2);
+    om_s[1] = double(l) / double(l + 3);
+  }
   __syncthreads();
-  const double omega = double(l - 1) / double(l + 2), omega_next = double(l) / double(l + 3);
+  const double omega = om_s[0], omega_next = om_s[1];
   double crit = 0.0;
   if (!timed_out && mine) {
-    double q = 0.0;
-    for (int w = 0; w < kAPWarps; ++w) q += (double)red[(w * TJ + jo) * 32 + co];
+    // the warp partials (FP32 sums themselves) added in warp order in FP32: FP64 is slow here
+    float qs = 0.f;
+    for (int w = 0; w < kAPWarps; ++w) qs += red[(w * TJ + jo) * 32 + co];
+    const double q = (double)qs;
     const double g = gm + q * inv_n;            // gradient of the quadratic model
     const double y = xm + omega * (xm - xpm);   // extrapolation, Sec. 3.2
     const double z = y - delta * g;
     const double gam = delta * lam * pm;
     const double az = fabs(z) - gam * pl1;  // soft threshold, Sec. 6.3, then the ridge shrinkage
-    const double xn = (az > 0.0 ? copysign(az, z) : 0.0) / (1.0 + 2.0 * gam * pl2);
+    double xn = az > 0.0 ? copysign(az, z) : 0.0;
+    if (pl2 != 0.0) xn /= 1.0 + 2.0 * gam * pl2;  // the ridge part (no division for the lasso)
     out[mo] = xn;
     dnext[mo] = (float)(xn + omega_next * (xn - xm) - am);
     crit = fabs(xn - y);
@@ -186,13 +210,37 @@ adjprox_kernel(APShape sh, const __grid_constant__ CUtensorMap mapS, const __gri
     for (int b = 0; b < nfirst; ++b) mbar_wait_bounded(&mbar[b], 0u);
 }
 
+// rows[2 j3] = the first i3 with X_3(i3, j3) != 0 (n3 if none), rows[2 j3 + 1] = one past the last
+__global__ void x3_rows_kernel(int n3, const float* __restrict__ X3T, int* __restrict__ rows) {
+  __shared__ int lo, hi;
+  if (threadIdx.x == 0) {
+    lo = n3;
+    hi = 0;
+  }
+  __syncthreads();
+  const float* r = X3T + (int64_t)blockIdx.x * n3;
+  int a = n3, b = 0;
+  for (int i = threadIdx.x; i < n3; i += blockDim.x)
+    if (r[i] != 0.f) {
+      a = min(a, i);
+      b = max(b, i + 1);
+    }
+  atomicMin(&lo, a);
+  atomicMax(&hi, b);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    rows[2 * blockIdx.x] = lo;
+    rows[2 * blockIdx.x + 1] = hi;
+  }
+}
+
 bool ap_configure(int n3, int p3, int P21, APShape& sh, size_t& smem) {
   if (n3 < 1 || p3 < 1 || P21 < 1 || P21 % 4 != 0 || n3 % 4 != 0) return false;
   sh.n3 = n3;
   sh.p3 = p3;
   sh.P21 = P21;
   sh.nx = (P21 + 31) / 32;
-  int gy = (num_sms() + sh.nx - 1) / sh.nx;  // about one tile per SM
+  int gy = num_sms() / sh.nx;  // at most one tile per SM: a second CTA on an SM ends last
   if (gy > p3) gy = p3;
   if (gy < 1) gy = 1;
   sh.TJ = (p3 + gy - 1) / gy;
@@ -232,7 +280,7 @@ int adjprox_supported(int n3, int p3, int P21, const float* X3T, const float* Sb
 cudaError_t launch_adjprox(int n3, int p3, int P21, const float* X3T, const float* Sb, const double* gk,
                            const double* x, const double* xp, const double* pen, double* out,
                            float* dnext, const double* anchor, double inv_n, InnerCtl* ctl, int* err,
-                           cudaStream_t s, bool pdl) {
+                           cudaStream_t s, bool pdl, const int* x3_rows) {
   APShape sh;
   size_t smem;
   if (!adjprox_supported(n3, p3, P21, X3T, Sb) || !ap_configure(n3, p3, P21, sh, smem))
@@ -262,7 +310,7 @@ cudaError_t launch_adjprox(int n3, int p3, int P21, const float* X3T, const floa
 #define GLAM_AP(tj)                                                                                  \
   case tj:                                                                                           \
     e = launch_pdl(adjprox_kernel<tj>, dim3(blocks), dim3(kAPThreads), smem, s, pdl, sh, mapS, mapX, gk, \
-                   x, xp, pen, out, dnext, anchor, inv_n, ctl, err);                                 \
+                   x, xp, pen, out, dnext, anchor, inv_n, ctl, err, x3_rows);                        \
     break;
     GLAM_AP(1) GLAM_AP(2) GLAM_AP(3) GLAM_AP(4) GLAM_AP(5) GLAM_AP(6) GLAM_AP(7) GLAM_AP(8)
 #undef GLAM_AP
@@ -270,6 +318,12 @@ cudaError_t launch_adjprox(int n3, int p3, int P21, const float* X3T, const floa
   }
   count_launches(1);
   return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_x3_rows(int n3, int p3, const float* X3T, int* rows, cudaStream_t s) {
+  x3_rows_kernel<<<p3, 256, 0, s>>>(n3, X3T, rows);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 }  // namespace glam

@@ -92,6 +92,7 @@ struct glam_plan {
   // (glam_opts.exploit_bands) runs
   bool band_on = false;
   BandDesign band[3];
+  int* x3rows = nullptr;           // per row j3 of X_3^T the range of its nonzero entries (2 p3)
   std::vector<void*> allocs;
 };
 
@@ -1073,7 +1074,7 @@ int capture_chunk(Fit<T>& f) {
         if (e == cudaSuccess && use_ap)  // mode-3 adjoint and prox step in one kernel
           e = launch_adjprox((int)pl->n3, (int)pl->p3, (int)(pl->p2 * pl->p1), op.X[2], op.w.Sb, pl->gk,
                              x, xp, pl->pen, xp, op.w.dn, pl->th, 1.0 / (double)pl->n, pl->ctl,
-                             &pl->sc->timeout, f.s, pdl);
+                             &pl->sc->timeout, f.s, pdl, pl->x3rows);
       }
       if (e == cudaSuccess && !use_ap)
         e = launch_gemm<T, T>(d_mode3_adj(pl, pl->ksplit), op.X[2], op.w.Sb, op.w.Qpart, f.s, nullptr,
@@ -1215,6 +1216,13 @@ int solve_lambda(Fit<T>& f, double lambda, LamOut& lo) {
     CK(launch_armijo_update<double>(pl->p, pl->th, xt, pl->sc, f.s));
     f.grad_fresh = false;
   }
+}
+
+// The range of the nonzero entries of each row j3 of X_3^T, read by the adjoint + prox kernel.
+int x3_rows_setup(glam_plan* pl, const float* X3T, cudaStream_t s) {
+  if (pl->x3rows == nullptr) CKS(dalloc(pl, &pl->x3rows, 2 * pl->p3));
+  CK(launch_x3_rows((int)pl->n3, (int)pl->p3, X3T, pl->x3rows, s));
+  return GLAM_OK;
 }
 
 // The banded form of the FP64 marginal designs of this fit (glam_opts.exploit_bands): every X_j
@@ -1373,6 +1381,8 @@ int fit_impl(glam_plan* pl, const void* const X[3], const T* Y, const T* W, cons
   if (sizeof(T) == 4 && pl->um_form)  // the tcgen05 kernel's constant block, once per fit
     CK(launch_fused_umma_const((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2, (int)pl->p3,
                                pl->um_form, (const float*)X[0], (const float*)X[1], pl->um_cst, f.s));
+  if (sizeof(T) == 4 && pl->nc == 1)  // the nonzero range of each row of X_3, once per fit
+    CKS(x3_rows_setup(pl, X[2] != nullptr ? (const float*)X[2] : pl->wf.one, f.s));
   if (sizeof(T) == 4 && pl->tc_split)  // the tensor-core kernel's constant block, once per fit
     CK(launch_fused_tc_const((int)pl->n1, (int)pl->n2, (int)pl->p1, (int)pl->p2, (const float*)X[0],
                              (const float*)X[1], pl->tc_cst, pl->tc_split, f.s));
@@ -1609,6 +1619,7 @@ int time_inner_impl(glam_plan* pl, const void* const X[3], const glam_quad* q, i
   if constexpr (sizeof(T) == 4) {
     use_ap = adjprox_supported((int)pl->n3, (int)pl->p3, (int)(pl->p2 * pl->p1), op.X[2], op.w.Sb) != 0;
     if (use_ap) {
+      CKS(x3_rows_setup(pl, op.X[2], pl->stream));
       CK(cudaMalloc(&tctl, sizeof(InnerCtl)));
       InnerCtl h{};
       h.l = 1;
@@ -1662,7 +1673,7 @@ int time_inner_impl(glam_plan* pl, const void* const X[3], const glam_quad* q, i
             if (fused && use_ap) {
               CK(launch_adjprox((int)pl->n3, (int)pl->p3, (int)(pl->p2 * pl->p1), op.X[2], op.w.Sb,
                                 pl->gk, pl->x0, pl->x1, pl->pen, pl->ptmp, op.w.grad, pl->th,
-                                1.0 / (double)pl->n, tctl, &pl->sc->timeout, pl->stream));
+                                1.0 / (double)pl->n, tctl, &pl->sc->timeout, pl->stream, false, pl->x3rows));
               break;
             }
           }

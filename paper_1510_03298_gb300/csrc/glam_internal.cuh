@@ -231,7 +231,10 @@ int adjprox_supported(int n3, int p3, int P21, const float* X3T, const float* Sb
 cudaError_t launch_adjprox(int n3, int p3, int P21, const float* X3T, const float* Sb, const double* gk,
                            const double* x, const double* xp, const double* pen, double* out,
                            float* dnext, const double* anchor, double inv_n, InnerCtl* ctl, int* err,
-                           cudaStream_t s, bool pdl = false);
+                           cudaStream_t s, bool pdl = false, const int* x3_rows = nullptr);
+// For each row j3 of X_3^T (p3 x n3), the range [first, last + 1) of its nonzero entries (n3, 0 when
+// none): with it launch_adjprox reads only the rows i3 of S_b that meet a nonzero entry.
+cudaError_t launch_x3_rows(int n3, int p3, const float* X3T, int* rows, cudaStream_t s);
 
 // Tensor-product weights (Sec. 6.2, Eq. kronweight): the factors w1 (n1), w2 (n2), w3 (n3) of W
 // read off its first row, column and tube, and check[0] = max |W - w1 w2 w3|, check[1] = max |W|
