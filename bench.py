@@ -374,7 +374,7 @@ def measure_details(g, torch, pr, plan, X, Y, W, pen, opts, dev, flush, last):
                           "frac_hbm": h_bytes / t_h / 1e9 / peaks["hbm_gbs"], "peak_src": src,
                           "tflops": h_flops / t_h / 1e12, "calls_per_region": K,
                           "first_call_after_flush_ms": statistics.median(cold),
-                          "kernels": "mode3_rows_kernel + predict_tile_kernel<1> (FP32 SIMT)"}
+                          "kernels": "predict_umma_kernel (tcgen05: FP32 first H stage and MMA0, 3xTF32 MMA1)"}
     del etas
     # dominant kernel of the inner iteration: the fused slab kernel G(V (.) H(.)), which a GLAM_FP32
     # plan runs on the tensor cores in the 3xTF32 form (FP32-level accuracy)

@@ -11,6 +11,7 @@ This file is collected last on purpose, so that a run stopping at the first fail
 every other test before it; it also passes on its own in a fresh process.
 """
 import ctypes as C
+import gc
 
 import numpy as np
 import pytest
@@ -124,14 +125,23 @@ def test_noalloc_calls_leave_device_memory_unchanged():
     stream = torch.cuda.current_stream().cuda_stream
     assert fn(gen.POISSON, g.GLAM_FP32, n, x.data_ptr(), y.data_ptr(), y.data_ptr(), out.data_ptr(), stream) == g.GLAM_OK
     torch.cuda.synchronize()
-    free0, _ = torch.cuda.mem_get_info()
-    alloc0 = torch.cuda.memory_allocated()
-    for _ in range(3):
-        assert fn(gen.POISSON, g.GLAM_FP32, n, x.data_ptr(), y.data_ptr(), y.data_ptr(), out.data_ptr(),
-                  stream) == g.GLAM_OK
+    # objects of earlier tests (plans, cached tensor blocks) are released first, and the collector
+    # stays off while the calls run, so that nothing else frees device memory in between
+    gc.collect()
+    torch.cuda.empty_cache()
     torch.cuda.synchronize()
-    free1, _ = torch.cuda.mem_get_info()
-    assert free1 == free0 and torch.cuda.memory_allocated() == alloc0
+    gc.disable()
+    try:
+        free0, _ = torch.cuda.mem_get_info()
+        alloc0 = torch.cuda.memory_allocated()
+        for _ in range(3):
+            assert fn(gen.POISSON, g.GLAM_FP32, n, x.data_ptr(), y.data_ptr(), y.data_ptr(), out.data_ptr(),
+                      stream) == g.GLAM_OK
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+    finally:
+        gc.enable()
+    assert free1 == free0 and torch.cuda.memory_allocated() == alloc0, (free0, free1)
 
 
 def test_noalloc_rejects_bad_sizes():
