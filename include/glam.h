@@ -392,7 +392,9 @@ int64_t glam_launch_count(void);
  * mode-3 adjoint product: the split GEMM, or, where the fit path fuses it with the proximal step
  * (FP32 and TF32 plans whose p2 p1 and n3 are multiples of 4), that one kernel; ms[3] the
  * proximal step (0 when it is part of ms[2]).  Each kernel runs 2 + reps times back to
- * back; ms (HOST, 4 doubles) receives the mean of the last reps launches in milliseconds.  Uses
+ * back (the tcgen05 kernel as programmatic dependent launches, as the fit path launches it, so
+ * that a launch's start overlaps the end of the one before); ms (HOST, 4 doubles) receives the
+ * mean of the last reps launches in milliseconds.  Uses
  * q->V as the weights and the plan's FP64 state of the last fit (values do not change the work).
  * Synchronizes the plan's stream. */
 int glam_time_inner_kernels(glam_plan* plan, const void* const X[3], const glam_quad* q, int reps,

@@ -1649,7 +1649,8 @@ int time_inner_impl(glam_plan* pl, const void* const X[3], const glam_quad* q, i
             if (use_um) {
               CK(launch_fused_umma((int)pl->n1, (int)pl->n2, (int)pl->n3, (int)pl->p1, (int)pl->p2, (int)pl->p3,
                                    pl->um_form, pl->Vb != nullptr, pl->um_cst, op.w.dn, op.X[0], op.X[2], Vin,
-                                   op.w.Sb, pl->stream, nullptr, &pl->sc->timeout, kDefaultWaitNs));
+                                   op.w.Sb, pl->stream, nullptr, &pl->sc->timeout, kDefaultWaitNs,
+                                   r > -2));  // programmatic dependent launches, as in the fit path
               break;
             }
             if (use_tc) {
