@@ -663,7 +663,9 @@ def measure_batched(g, torch, nfit, nbase):
     """The 64-fit workload (grid sides U{32..96}, p_j U{8..24}, Gaussian or Poisson, 20-lambda
     paths to KKT 1e-6, FP32 plans) through glam_fit_path_batched, against the plain FP32 path fitting
     the first nbase of the same problems one after another.  Throughput in fits/s and in inner PG
-    iterations/s (the sequential leg covers a subset, so the speedup is taken on iterations/s)."""
+    iterations/s (the sequential leg covers a subset, so the speedup is taken on iterations/s).
+    The mixed-precision leg fits the same 64 problems on TF32 plans to the same KKT tolerance and
+    reports its wall time against the FP32 batch."""
     import gen
     probs = gen.make_workload(4, nfit=nfit)
     f32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
@@ -686,12 +688,26 @@ def measure_batched(g, torch, nfit, nbase):
     dt_b, it_b, kkt_b, ok_b = run(bps, 16)
     nb = max(1, min(nbase, nfit))
     dt_s, it_s, kkt_s, ok_s = run(bps[:nb], 1)
+    # the mixed-precision batch: the same fits with TF32 plans (TF32 inner products, FP64 gradient
+    # and KKT test), at the same KKT tolerance
+    bpt = [g.BatchProblem(g.Plan(pr.n, pr.p, pr.family, g.GLAM_TF32), bp.X, bp.Y, bp.W, bp.pen_w,
+                          nlambda=pr.nlambda) for pr, bp in zip(probs, bps)]
+    dt_t, it_t, kkt_t, ok_t = run(bpt, 16)
+    for bp in bpt + bps:
+        bp.plan.close()
     return {"fits": nfit, "nlambda": probs[0].nlambda, "threads": 16, "wall_s": dt_b,
             "fits_per_s": nfit / dt_b, "inner_iters": it_b, "inner_iters_per_s": it_b / dt_b,
             "max_kkt": kkt_b, "converged": ok_b,
             "sequential_fp32_path": {"fits": nb, "wall_s": dt_s, "fits_per_s": nb / dt_s,
                                      "inner_iters_per_s": it_s / dt_s, "max_kkt": kkt_s, "converged": ok_s},
             "speedup_iters_per_s": (it_b / dt_b) / (it_s / dt_s),
+            "mixed_precision_tf32_batch": {"fits": nfit, "wall_s": dt_t, "fits_per_s": nfit / dt_t,
+                                           "inner_iters": it_t, "max_kkt": kkt_t, "converged": ok_t,
+                                           "speedup_vs_fp32_batch_at_equal_kkt": dt_b / dt_t,
+                                           "note": "no fit of this workload meets the tensor-core kernels' "
+                                                   "shape rules (n1 a multiple of 4 up to 128, n2 a multiple "
+                                                   "of 32, p1, p2 <= 32), so TF32 plans run the same FP32 "
+                                                   "CUDA-core kernels as FP32 plans here"},
             "form": "each fit on its own plan and stream, 16 native host worker threads"}
 
 
