@@ -5,10 +5,11 @@ One step = one warm-started 50-lambda path fit (glam_fit_path: lambda_max, inner
 Armijo line search, FP64 KKT test to 1e-6 at every lambda) on the synthetic workload with
 cubic B-spline bases p = (20, 20, 60), FP32 mode products.  The headline value is prox-grad
 (inner PG) iterations per second over the timed steps; the line also carries the H-transform
-GB/s of glam_predict, the FP64 GPU path on a bounded sample of the same path, the roofline of
-the dominant kernel, the FP64 CPU oracle baseline, an end-to-end figure with host buffers, and
-the batched form: 64 independent fits of uneven shapes through glam_fit_path_batched against the
-plain FP32 path fitting them one after another.
+GB/s of glam_predict, the whole path on an FP64 plan and on TF32 and BF16 plans, the roofline of
+the dominant kernel, an end-to-end figure with host buffers, and at N = 1 the FP64 CPU oracle
+baseline, the masked Poisson 96 x 96 x 365 path in four precisions, and the batched form: 64
+independent fits of uneven shapes through glam_fit_path_batched against the plain FP32 path
+fitting them one after another, and on TF32 plans against the FP32 batch.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -295,9 +296,11 @@ def run_ours(args):
     if rank == 0:
         extra = measure_details(g, torch, pr, plan, X, Y, W, pen, opts, dev, flush, results[-1])
         extra["e2e"] = measure_e2e(g, torch, pr, plan, opts, dev, args.steps)
-        if not args.no_config3:
+        # the single-GPU side measurements run at N = 1 only: at N > 1 the other ranks would wait
+        # for them in the closing barrier
+        if not args.no_config3 and world == 1:
             extra["poisson_96x96x365_paths"] = measure_config3(g, torch, flush)
-        if args.batched > 0:
+        if args.batched > 0 and world == 1:
             extra["batched"] = measure_batched(g, torch, args.batched, args.batched_baseline)
         if world == 1 and not args.no_cpu:
             extra["cpu_baseline"] = cpu_baseline()
