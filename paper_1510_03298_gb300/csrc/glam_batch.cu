@@ -6,6 +6,7 @@
 // device work.
 #include <algorithm>
 #include <atomic>
+#include <exception>
 #include <string>
 #include <thread>
 #include <unordered_set>
@@ -58,8 +59,14 @@ int glam_fit_path_batched(int nitems, glam_plan* const* plans, glam_batch_item* 
     worker();
   } else {
     std::vector<std::thread> pool;
-    pool.reserve(nt);
-    for (int t = 0; t < nt; ++t) pool.emplace_back(worker);
+    try {
+      pool.reserve(nt);
+      for (int t = 0; t < nt; ++t) pool.emplace_back(worker);
+    } catch (const std::exception&) {
+      // the system gave fewer threads than asked for (no exception may leave this C entry
+      // point): the caller's thread takes fits too
+      worker();
+    }
     for (auto& th : pool) th.join();
   }
   for (int i = 0; i < nitems; ++i)
