@@ -68,13 +68,15 @@ class Clocks:
 
     def start(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        self.f = open(self.path, "w")
         try:
-            self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
-        except Exception:
+        except OSError:
             self.proc = None
+            self.f.close()
+            os.remove(self.path)
 
     def stop(self):
         if self.proc is None:
