@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "glam_host_math.h"
 #include "glam_internal.cuh"
 
 using namespace glam;
@@ -401,41 +402,6 @@ int alloc_work(glam_plan* pl, Work<T>& w, bool full) {
   }
   w.ready = true;
   return GLAM_OK;
-}
-
-// Largest eigenvalue magnitude of a symmetric matrix by the cyclic Jacobi method.
-double jacobi_spectral_radius(std::vector<double> A, int m) {
-  auto at = [&](int i, int j) -> double& { return A[(size_t)i * m + j]; };
-  for (int sweep = 0; sweep < 100; ++sweep) {
-    double off = 0.0, diag = 0.0;
-    for (int i = 0; i < m; ++i) {
-      diag += at(i, i) * at(i, i);
-      for (int j = i + 1; j < m; ++j) off += at(i, j) * at(i, j);
-    }
-    if (off <= 1e-30 * (diag + 1e-300)) break;
-    for (int p = 0; p < m - 1; ++p) {
-      for (int q = p + 1; q < m; ++q) {
-        const double apq = at(p, q);
-        if (apq == 0.0) continue;
-        const double theta = (at(q, q) - at(p, p)) / (2.0 * apq);
-        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
-        for (int k = 0; k < m; ++k) {
-          const double akp = at(k, p), akq = at(k, q);
-          at(k, p) = c * akp - s * akq;
-          at(k, q) = s * akp + c * akq;
-        }
-        for (int k = 0; k < m; ++k) {
-          const double apk = at(p, k), aqk = at(q, k);
-          at(p, k) = c * apk - s * aqk;
-          at(q, k) = s * apk + c * aqk;
-        }
-      }
-    }
-  }
-  double r = 0.0;
-  for (int i = 0; i < m; ++i) r = std::fmax(r, std::fabs(at(i, i)));
-  return r;
 }
 
 // X holds 3 design pointers per component (X_r1, X_r2, X_r3 of component r at 3r .. 3r + 2)
