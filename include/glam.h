@@ -371,8 +371,10 @@ int glam_fit_path_batched(int nitems, glam_plan* const* plans, glam_batch_item* 
  * before the exponential (at 80 in FP32, 700 in FP64), so that a large eta gives a finite term
  * and a masked cell (a_i = 0) contributes zero; a NaN or infinite input gives a NaN result.
  * Every term is added in FP64, with a fixed summation order (same bits on every call).
- * Asynchronous on `stream`.  The first call on a device looks up the scratch address
- * (cudaGetSymbolAddress), so make that first call before any stream capture.  All calls share
+ * Asynchronous on `stream`.  The first call on a device looks up the scratch address with
+ * cudaGetSymbolAddress (a runtime query, not an allocation) and keeps it; every call clears the
+ * counter with cudaMemsetAsync on `stream`.
+ * All calls share
  * the one scratch array: calls whose kernels overlap on the GPU race on it and must be
  * serialized (one stream).
  * Errors: GLAM_EINVAL (message from glam_last_error(NULL)), GLAM_ECUDA. */
