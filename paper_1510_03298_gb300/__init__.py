@@ -236,6 +236,8 @@ class Plan:
             raise TypeError(f"{name} must be a torch.Tensor")
         if t.device.type != "cuda":
             raise ValueError(f"{name} must be a CUDA tensor")
+        if t.device != self.device:
+            raise ValueError(f"{name} is on {t.device}, the plan on {self.device}")
         if t.dtype != self.dtype:
             raise TypeError(f"{name} must be {self.dtype}, got {t.dtype}")
         if tuple(t.shape) != tuple(shape):
