@@ -205,13 +205,17 @@ int glam_opts_default(glam_opts* opts);
  * BF16), n2 % 32 == 0, n2 <= 128 (GLAM_FP32) or 256, p1, p2 <= 32; outside that domain a
  * warp-level tensor-core kernel serves shapes with n1 % 32 == 0, n2 % 8 == 0, n2 <= 256,
  * p1, p2 <= 32 and 4 n1 n2 < 2^20 bytes (3xTF32 for GLAM_FP32, TF32 for GLAM_TF32 and GLAM_BF16
- * plans), and FP32 SIMT kernels every other shape.  Every other product (glam_predict,
- * glam_gradient, glam_loss, glam_quad_build, the FP64 passes of glam_fit_path) uses the FP32
- * kernels in every single-precision plan: each outer iteration of glam_fit_path recomputes the
- * gradient and the KKT residual in FP64, so the product precision changes iteration counts,
- * not the accuracy of the accepted solutions.
+ * plans), and FP32 SIMT kernels every other shape.  In the single-precision plans,
+ * glam_predict, glam_gradient, glam_loss and glam_quad_build take their H-transform from a
+ * tcgen05 kernel in the 3xTF32 form (about FP32 accuracy) on the 5th-generation domain above
+ * with n2 <= 224, from FP32 SIMT kernels elsewhere, and their G from FP32 SIMT kernels.  The
+ * gradient, line-search and KKT passes of glam_fit_path run in FP64 in every plan, so the
+ * product precision changes iteration counts, not the accuracy of the accepted solutions.
  * stream: a cudaStream_t (NULL = legacy default stream) on the
- * current device.  *out receives the plan.  Allocates the workspace on the current device. */
+ * current device.  *out receives the plan.  Allocates the workspace on the current device.
+ * Errors: GLAM_EINVAL (NULL argument; d not 2 or 3; an n_j or p_j below 1; d = 2 with n3 or p3
+ * not 1; unknown family or precision; n1 n2 n3 or p1 p2 p3 above 2^40; n3 above 65535 or
+ * n3 p2 above 65535 * 64), GLAM_ENOMEM, GLAM_ECUDA. */
 int glam_plan_create(const glam_dims* dims, int family, int precision, void* stream, glam_plan** out);
 
 /* Create a plan for the model with c components (Sec. 2, Eq. fivenew: X = [X_1 | ... | X_c], each

@@ -475,9 +475,17 @@ int glam_plan_create(const glam_dims* dims, int family, int precision, void* str
     return fail(nullptr, GLAM_EINVAL, "unknown family");
   if (precision != GLAM_FP64 && precision != GLAM_FP32 && precision != GLAM_TF32 && precision != GLAM_BF16)
     return fail(nullptr, GLAM_EINVAL, "precision: GLAM_FP64, GLAM_FP32, GLAM_TF32 or GLAM_BF16");
-  const int64_t n = dims->n[0] * dims->n[1] * dims->n[2];
-  const int64_t p = dims->p[0] * dims->p[1] * dims->p[2];
-  if (n > (int64_t)1 << 40 || dims->n[2] * dims->p[1] > 65535LL * 64 || dims->n[2] > 65535)
+  // the products are formed only once each factor is known to keep them below 2^40 (no int64
+  // overflow can slip a huge shape past the limit)
+  const int64_t kLim = (int64_t)1 << 40;
+  int64_t n = 1, p = 1;
+  for (int j = 0; j < 3; ++j) {
+    if (dims->n[j] > kLim / n || dims->p[j] > kLim / p)
+      return fail(nullptr, GLAM_EINVAL, "dims too large: n1 n2 n3 and p1 p2 p3 must not exceed 2^40");
+    n *= dims->n[j];
+    p *= dims->p[j];
+  }
+  if (dims->n[2] > 65535 || dims->n[2] * dims->p[1] > 65535LL * 64)
     return fail(nullptr, GLAM_EINVAL, "dims too large");
   pl = new (std::nothrow) glam_plan();
   if (pl == nullptr) return fail(nullptr, GLAM_ENOMEM, "host allocation failed");
@@ -632,10 +640,17 @@ int glam_plan_create_components(int d, const int64_t n[3], int c, const int64_t*
     return glam_plan_create(&dr, family, precision, stream, out);
   }
   int64_t ptot = 0;
+  const int64_t kLim = (int64_t)1 << 40;
   for (int r = 0; r < c; ++r) {
     if (p[3 * r] < 1 || p[3 * r + 1] < 1 || p[3 * r + 2] < 1)
       return fail(nullptr, GLAM_EINVAL, "every p_rj must be >= 1");
-    ptot += p[3 * r] * p[3 * r + 1] * p[3 * r + 2];
+    int64_t pr = 1;
+    for (int j = 0; j < 3; ++j) {
+      if (p[3 * r + j] > kLim / pr) return fail(nullptr, GLAM_EINVAL, "component coefficients too many");
+      pr *= p[3 * r + j];
+    }
+    if (pr > kLim - ptot) return fail(nullptr, GLAM_EINVAL, "component coefficients too many");
+    ptot += pr;
   }
   // this plan: the grid's n-space arrays and the concatenated p-space state (its own transforms
   // are never used: the components' plans do them)

@@ -65,6 +65,27 @@ def test_plan_create_rejects_bad_arguments(lib):
     assert lib.glam_plan_create(None, 0, 0, None, C.byref(h)) == g.GLAM_EINVAL
 
 
+def test_plan_create_rejects_shapes_past_the_cell_limit(lib):
+    """n1 n2 n3 and p1 p2 p3 may not exceed 2^40, including shapes whose int64 product would
+    wrap around (2^32 x 2^32 = 2^64 -> 0); the refusal comes before any CUDA call."""
+    import paper_1510_03298_gb300 as g
+    h = C.c_void_p()
+    big = [((1 << 32, 1 << 32, 1), (4, 4, 1)), ((1 << 21, 1 << 20, 1), (4, 4, 1)),
+           ((5, 5, 5), (1 << 32, 1 << 32, 2)), ((5, 5, 5), (1 << 41, 1, 1)),
+           ((1 << 62, 4, 4), (4, 4, 4))]
+    for n, p in big:
+        dims = g.GlamDims(3, (C.c_int64 * 3)(*n), (C.c_int64 * 3)(*p))
+        assert lib.glam_plan_create(C.byref(dims), g.GLAM_GAUSSIAN_IDENTITY, g.GLAM_FP32, None,
+                                    C.byref(h)) == g.GLAM_EINVAL, (n, p)
+        assert h.value is None
+        assert b"too large" in lib.glam_last_error(None)
+    n = (C.c_int64 * 3)(5, 5, 5)
+    ps = (C.c_int64 * 6)(1 << 30, 1 << 10, 1, 1 << 30, 1 << 10, 1)  # 2^40 + 2^40 coefficients
+    assert lib.glam_plan_create_components(3, n, 2, ps, g.GLAM_GAUSSIAN_IDENTITY, g.GLAM_FP32, None,
+                                           C.byref(h)) == g.GLAM_EINVAL
+    assert b"too many" in lib.glam_last_error(None)
+
+
 def test_null_plan_is_an_error_not_a_crash(lib):
     import paper_1510_03298_gb300 as g
     X = (C.c_void_p * 3)(None, None, None)
