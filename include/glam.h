@@ -93,7 +93,7 @@ typedef struct {
 /* Options of glam_fit_path.  glam_opts_default fills the defaults given below. */
 typedef struct {
   double tol;              /* KKT residual target per lambda (default 1e-6), see glam_stats.kkt */
-  double lambda_min_ratio; /* auto path: lambda_min = ratio * lambda_max (default 1e-3) */
+  double lambda_min_ratio; /* auto path: lambda_min = ratio * lambda_max, in (0, 1] (default 1e-3) */
   double inner_forcing;    /* inner PG stop: max_m |x+_m - y_m| / delta <= s * lambda_max with
                               s = max(inner_floor * tol, inner_forcing * r_k), r_k the KKT residual
                               at the outer iterate (defaults 1e-2 and 0.1) */
@@ -105,7 +105,8 @@ typedef struct {
   int32_t max_outer;       /* outer GD iterations per lambda (default 50) */
   int32_t max_linesearch;  /* Armijo trials per outer iteration (default 30) */
   int32_t check_every;     /* inner iterations per captured CUDA graph chunk, i.e. between host
-                              reads of the device stop flag (default 32, rounded up to even) */
+                              reads of the device stop flag (default 32, rounded up to even;
+                              at most 4096) */
   int32_t iwls;            /* weights of the inner problem (the package's iwls option, Sec. 6.4):
                               GLAM_IWLS_EXACT (default) uses the IRLS weights of App. B as they are;
                               GLAM_IWLS_KRON uses their tensor-product form (Sec. 6.2, Eq.
@@ -293,7 +294,8 @@ int glam_prox_step(glam_plan* plan, const void* const X[3], const glam_quad* q, 
  * Each lambda stops when its FP64 KKT residual is <= opts->tol.  Returns GLAM_ENOCONV (with
  * *nfit = the number of lambdas that met the tolerance, and rows up to the failing one written)
  * when an iteration cap is hit, as the paper's package does; GLAM_ENONFINITE on non-finite
- * input or a non-finite iterate. */
+ * input or a non-finite iterate; GLAM_EINVAL for a NULL argument, nlambda < 1, a NaN lambda[0],
+ * a negative given lambda, or options out of range. */
 int glam_fit_path(glam_plan* plan, const void* const X[3], const void* Y, const void* W,
                   const void* pen_w, int nlambda, double* lambda, const glam_opts* opts,
                   const double* Theta0, double* Theta_path, glam_stats* stats, int* nfit);

@@ -1540,6 +1540,9 @@ int glam_kron_weights(glam_plan* pl, const double* V, int scaled, double* v1, do
   return GLAM_OK;
 }
 
+// longest captured chunk of inner iterations (each iteration adds two to four kernel nodes)
+constexpr int kMaxCheckEvery = 4096;
+
 int glam_fit_path(glam_plan* pl, const void* const X[3], const void* Y, const void* W,
                   const void* pen_w, int nlambda, double* lambda, const glam_opts* opts,
                   const double* Theta0, double* Theta_path, glam_stats* stats, int* nfit) {
@@ -1553,6 +1556,8 @@ int glam_fit_path(glam_plan* pl, const void* const X[3], const void* Y, const vo
     o = *opts;
   else
     glam_opts_default(&o);
+  if (o.check_every > kMaxCheckEvery)
+    return fail(pl, GLAM_EINVAL, "glam_fit_path: check_every above 4096 (the captured chunk holds that many iterations)");
   if (o.check_every < 2) o.check_every = 2;
   if (o.check_every % 2) o.check_every += 1;
   if (o.max_inner < 1 || o.max_outer < 1 || o.max_linesearch < 1 || !(o.tol > 0) ||
@@ -1563,9 +1568,13 @@ int glam_fit_path(glam_plan* pl, const void* const X[3], const void* Y, const vo
       !(o.enet_alpha >= 0.0 && std::isfinite(o.enet_alpha)) ||
       !(o.wait_limit_s >= 0.0 && o.wait_limit_s <= 3600.0))
     return fail(pl, GLAM_EINVAL, "glam_fit_path: bad options");
-  if (lambda[0] >= 0)
+  if (std::isnan(lambda[0])) return fail(pl, GLAM_EINVAL, "glam_fit_path: lambda[0] is NaN");
+  if (lambda[0] >= 0) {
     for (int k = 0; k < nlambda; ++k)
       if (!(lambda[k] >= 0)) return fail(pl, GLAM_EINVAL, "glam_fit_path: negative lambda");
+  } else if (!(o.lambda_min_ratio > 0.0 && o.lambda_min_ratio <= 1.0)) {
+    return fail(pl, GLAM_EINVAL, "glam_fit_path: lambda_min_ratio must be in (0, 1]");
+  }
   if (pl->precision == GLAM_FP64)
     return fit_impl<double>(pl, X, (const double*)Y, (const double*)W, (const double*)pen_w, nlambda,
                             lambda, o, Theta0, Theta_path, stats, nfit);
